@@ -1,0 +1,385 @@
+#!/usr/bin/env python3
+"""Throughput of the active-Brownian-particle ensemble integrator on GB300.
+
+Workload (default): the D x q parameter sweep -- 64 values of D log-spaced in [1e-3, 1]
+times 32 values of q log-spaced in [0.1, 10], 1,024 trajectories per point (2,097,152
+trajectories), 10^5 Euler-Maruyama steps at dt = 1e-3, FP32 state with FP64
+accumulation, v0 ~ N(0, sqrt(D)), Philox seed 1.  One step of the benchmark is one pass
+of the whole path: initial condition, integration with noise generation, the final
+histogram of x mod L and the FP64 ensemble reduction.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s on 1 GB300 (and % FP32-pipe roofline) at oracle-matched accuracy"
+UNIT = "particle-steps/s"
+# Algorithmic FP32/INT32 lane operations per particle-step: drift, depot, position and
+# wrap ~16, Philox4x32-10 amortised over its four steps 15, Box-Muller ~4.
+N_ALG = 35
+LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--ppt", type=int, default=0, help="particles per thread (0 = library default)")
+    ap.add_argument("--steps-per-launch", type=int, default=10_000)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--small", action="store_true", help="reduced sweep (for quick checks, not a bench line)")
+    return ap.parse_args()
+
+
+def workload(args):
+    from paper_1104_2499_gb300 import workloads as W
+
+    if args.small:
+        return W.sweep_grid(n_D=16, n_q=8, traj_per_set=1024, n_steps=10_000)
+    return W.sweep_grid()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"sm_max_mhz": 2070.0}, "fallback"
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.gpu_id:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, power, reasons = [], [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "power_w_max": max(power),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- oracle legs
+
+def oracle_sample(w, budget_s: float, gpu_moments=None):
+    """Time the FP64 oracle on whole parameter sets of the workload (all their trajectories,
+    all their steps), evenly spread over the grid, until about budget_s seconds are used.
+    Returns (rate, cores, sample description, parity summary)."""
+    from oracle import oracle as O
+
+    O.build()
+    cores = os.cpu_count() or 1
+    base = w.traj_base()
+    order = [int(round(i * (w.n_sets - 1) / 15)) for i in range(16)] if w.n_sets > 16 else list(range(w.n_sets))
+    done_ps, t_used, used, z = 0, 0.0, [], []
+    for i in order:
+        t0 = time.perf_counter()
+        r = O.run_set(w.sets[i], seed=w.seed, dt=w.dt, n_traj=w.n_traj[i], n_steps=w.n_steps[i], traj_base=base[i],
+                      v0_mode=w.v0_mode, n_threads=cores)
+        t_used += time.perf_counter() - t0
+        done_ps += w.n_traj[i] * w.n_steps[i]
+        used.append(i)
+        if gpu_moments is not None:
+            se = max(r["se_v"], 1e-300)
+            z.append(abs(float(gpu_moments[i][0]) - r["mean_v"]) / se)
+        if t_used >= budget_s:
+            break
+    desc = "%d whole parameter sets (%d trajectories x %d steps each, %.3g particle-steps) of the sweep" % (
+        len(used), w.n_traj[used[0]], w.n_steps[used[0]], done_ps)
+    parity = None
+    if z:
+        parity = {"sets_checked": len(z), "max_abs_dmean_over_se": max(z), "bar": 3.0, "pass": max(z) <= 3.0}
+    return done_ps / t_used, cores, desc, parity
+
+
+def run_reference(args, rank, world):
+    """The reference arm: the FP64 CPU oracle, timed on the host cores."""
+    from paper_1104_2499_gb300 import workloads as W
+
+    w = workload(args)
+    if rank != 0:
+        return
+    from oracle import oracle as O
+
+    O.build()
+    cores = os.cpu_count() or 1
+    base = w.traj_base()
+    # one step = one bounded sample of the workload: a slice of trajectories of sets spread over
+    # the grid, all 10^5 steps, sized so that warm-up + timed steps take about two minutes
+    total_steps = args.steps + args.warmup
+    per_step_budget = max(2.0, 120.0 / max(total_steps, 1))
+    t0 = time.perf_counter()
+    O.run_set(w.sets[0], seed=w.seed, dt=w.dt, n_traj=16, n_steps=2000, traj_base=base[0], v0_mode=w.v0_mode,
+              n_threads=cores)
+    rate_probe = 16 * 2000 / max(time.perf_counter() - t0, 1e-6)
+    ps_target = rate_probe * per_step_budget
+    n_sets_s = 8
+    m = max(1, int(ps_target / (n_sets_s * w.n_steps[0])))
+    m = min(m, w.n_traj[0])
+    idx = [int(round(i * (w.n_sets - 1) / (n_sets_s - 1))) for i in range(n_sets_s)]
+
+    def step():
+        for i in idx:
+            O.run_set(w.sets[i], seed=w.seed, dt=w.dt, n_traj=m, n_steps=w.n_steps[i], traj_base=base[i],
+                      v0_mode=w.v0_mode, n_threads=cores)
+
+    for _ in range(args.warmup):
+        step()
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        step()
+        times.append(time.perf_counter() - t0)
+    ps = n_sets_s * m * w.n_steps[0]
+    value = ps / statistics.mean(times)
+    sample = "%d sets spread over the %d-set sweep x %d trajectories x %d steps per step (%.3g particle-steps)" % (
+        n_sets_s, w.n_sets, m, w.n_steps[0], ps)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(w, args),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(w, args, extra=None):
+    d = {"workload": w.name, "parameter_sets": w.n_sets, "traj_per_set": int(w.n_traj[0]) if w.n_sets else 0,
+         "total_traj": w.total_traj, "steps": int(w.n_steps[0]) if w.n_sets else 0, "dt": w.dt, "seed": w.seed,
+         "particle_steps_per_step": w.particle_steps, "state": "fp32 (cell + fraction), fp64 accumulation",
+         "l2": "flushed (256 MiB write) between timed steps", "hist_x_bins": w.hist_x_bins}
+    if extra:
+        d.update(extra)
+    return d
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1104_2499_gb300 import abp as A
+    from paper_1104_2499_gb300 import build as B
+
+    if rank == 0 or world == 1:
+        B.build()
+    if dist is not None:
+        dist.barrier()
+        B.build()
+    A.lib()
+
+    w = workload(args)
+    stream = torch.cuda.Stream()
+    props = torch.cuda.get_device_properties(local)
+    n_sm = props.multi_processor_count
+    # weak scaling: every rank integrates its own copy of the sweep with distinct trajectory ids
+    ens = A.Ensemble(w, stream=stream, particles_per_thread=args.ppt, steps_per_launch=args.steps_per_launch,
+                     traj_base=rank * w.total_traj)
+    S = w.n_sets
+    spl = args.steps_per_launch
+    n_launch = math.ceil(w.n_steps[0] / spl)
+    mom = torch.empty((S, 8), dtype=torch.float64, device="cuda")
+    ns = 1
+    hx = torch.empty((ns, S, w.hist_x_bins), dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    with torch.cuda.stream(stream):
+        ens.set_params()
+
+    def gpu_step(ev_k=None):
+        ens.reset(w.seed)
+        for j in range(n_launch):
+            if ev_k is not None:
+                ev_k[j][0].record(stream)
+            ens.integrate(spl)
+            if ev_k is not None:
+                ev_k[j][1].record(stream)
+        A.abp_reduce(ens.ctx, mom, hx, None)
+        if dist is not None:
+            with torch.cuda.stream(stream):
+                dist.all_reduce(mom[:, 4:8])
+
+    for _ in range(args.warmup):
+        with torch.cuda.stream(stream):
+            gpu_step()
+    stream.synchronize()
+
+    ev_step = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev_kern = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_launch)]
+               for _ in range(args.steps)]
+    gpu_id = None
+    try:
+        gpu_id = "GPU-" + str(props.uuid) if getattr(props, "uuid", None) else None
+    except Exception:
+        gpu_id = None
+    launches0 = ens.launches()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(gpu_id) as clk:
+        wall0 = time.perf_counter()
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                ev_step[k][0].record(stream)
+                gpu_step(ev_kern[k])
+                ev_step[k][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    if dist is not None:
+        dist.barrier()
+    launches = ens.launches() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev_step]
+    total_ms = sum(step_ms)
+    kern_ms = [a.elapsed_time(b) for row in ev_kern for a, b in row]
+    t_max = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    total_ms = float(t_max.item())
+    ps_step = w.particle_steps
+    value = world * ps_step * args.steps / (total_ms * 1e-3)
+    moments = mom.cpu().numpy()
+    clocks = clk.summary()
+
+    # e2e: the same step through the C ABI with host buffers (params uploaded from host
+    # memory, moments and histograms read back into pinned host memory)
+    e2e = None
+    if not args.no_e2e:
+        mom_h = torch.empty((S, 8), dtype=torch.float64, pin_memory=True)
+        hx_h = torch.empty((ns, S, w.hist_x_bins), dtype=torch.int32, pin_memory=True)
+        n_tiles = sum(math.ceil(m / (256 * max(args.ppt, 1))) for m in w.n_traj)
+        h2d = S * (72 + 8) + 4 * (S + 1) + 16 * n_tiles
+        d2h = mom_h.numel() * 8 + hx_h.numel() * 4
+        times = []
+        with torch.cuda.stream(stream):
+            for k in range(max(1, args.steps)):
+                flush.zero_()
+                stream.synchronize()
+                t0 = time.perf_counter()
+                A.abp_set_params(ens.ctx, w.sets, w.n_traj, w.n_steps)
+                A.abp_integrate(ens.ctx, -1)
+                A.abp_reduce(ens.ctx, mom_h, hx_h, None)
+                times.append(time.perf_counter() - t0)
+        e2e = {"value": world * ps_step / statistics.mean(times), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    pk, pk_kind = peaks()
+    f_max = float(pk.get("sm_max_mhz", 2070.0)) * 1e6
+    peak = n_sm * LANES_PER_SM * f_max / 1e12  # T lane-ops/s
+    ps_launch = w.total_traj * spl
+    kern_avg = statistics.mean(kern_ms) * 1e-3
+    achieved = N_ALG * ps_launch / kern_avg / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T lane-op/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "integrate_kernel<float,PPT>", "n_alg_per_particle_step": N_ALG,
+            "peak_basis": "%d SMs x %d FP32 lanes x %.0f MHz (%s sm_max_mhz)" % (n_sm, LANES_PER_SM, f_max / 1e6,
+                                                                                pk_kind),
+            "launch_ms_avg": kern_avg * 1e3, "particle_steps_per_launch": ps_launch,
+            "particle_steps_per_s_in_kernel": ps_launch / kern_avg}
+    if clocks.get("sm_mhz"):
+        roof["frac_at_measured_clock"] = achieved / (n_sm * LANES_PER_SM * clocks["sm_mhz"] * 1e6 / 1e12)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, cores, desc, parity = oracle_sample(w, args.cpu_seconds, gpu_moments=moments)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+        if parity:
+            cpu["parity_mean_v"] = parity
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": config_dict(w, args, {"steps_per_launch": spl, "particles_per_thread": args.ppt or 1,
+                                                "launches_per_step": n_launch,
+                                                "parallelism": "dp%d (independent replicas)" % world}),
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+                "wall_s_timed": wall, "sm_count": n_sm, "device": props.name}
+        print(json.dumps(line), flush=True)
+    ens.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

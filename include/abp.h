@@ -1,0 +1,207 @@
+/*
+ * abp.h -- C ABI of the GB300 active-Brownian-particle ensemble integrator.
+ *
+ * The library integrates many independent trajectories of the energy-depot
+ * Langevin model of arXiv 1104.2499, Sec. 2 (Zabicki, "OpenCL/OpenGL approach
+ * for studying active Brownian motion"):
+ *
+ *   Eq. (ereservoir)  de/dt = q - c e - d e v^2
+ *   Eq. (velocity)    dv/dt = F0 + d e v - gamma0 v - U'(x) + sqrt(2 D) xi(t)
+ *   Eq. (pot)         U(x)  = h [0.499 - 0.453 (sin phi + a sin 2 phi)],
+ *                     phi = 2 pi (x / L + 0.1903)
+ *                     dx/dt = v
+ *
+ * across sets of parameters and initial conditions (Sec. 2: one work item per
+ * parameter value, results averaged over noise realisations and over time),
+ * with explicit Euler-Maruyama steps (Fig. 1: per iteration, draw uniforms,
+ * Box-Muller them into a Gaussian, update velocity and energy), and reduces
+ * the ensemble on the device to the mean velocity (ratchet current), the
+ * diffusion coefficient and position / velocity histograms.
+ *
+ * Noise.  Step n of global trajectory t under seed s uses the Philox4x32-10
+ * block with key (s_lo, s_hi) and counter (m_lo, m_hi, t_lo, t_hi), m = n >> 2
+ * (Salmon et al., SC'11).  Words (w0, w1) give steps 4m and 4m+1, (w2, w3)
+ * steps 4m+2 and 4m+3, through Box-Muller with u1 = (w_a + 1/2) 2^-32 and
+ * u2 = floor(w_b / 2^9) 2^-23: z_even = r cos(2 pi u2), z_odd = r sin(2 pi u2),
+ * r = sqrt(-2 ln u1).  The initial condition uses counter m = 2^63:
+ * x0 = L floor(w0 / 2^8) 2^-24, v0 = 0 or sqrt(D) r(w1) cos(2 pi u2(w2)), e0 = 0.
+ * Global trajectory ids number the sets' ensembles consecutively in set order.
+ *
+ * Arithmetic.  State is FP32.  The position is an integer cell index plus an
+ * FP32 fraction of the period, and the per-step increments v dt are summed in
+ * a separate small accumulator that is folded into the fraction every 64 steps
+ * with its rounding error kept (compensated FP32), so that long runs lose no
+ * precision (the paper's precision section warns against adding small
+ * increments to large values).  Because the scheme advances x by v_n dt, the
+ * time average of v over n steps is (x_n - x_0) / (n dt), taken from this
+ * compensated displacement in FP64.  All ensemble sums are FP64.
+ *
+ * Conventions for every entry point:
+ *   - Returns ABP_OK or an error code; the message of the last error of a
+ *     context is available from abp_last_error().  Nothing is printed.
+ *   - Work is enqueued asynchronously on the context's CUDA stream; a device
+ *     side failure recorded by a kernel (for example an expired bounded wait)
+ *     surfaces as ABP_ETIMEOUT / ABP_ESTATE from abp_synchronize() or from the
+ *     next call that synchronises.
+ *   - Output pointers documented as "host or device" may point to either; the
+ *     library inspects them with cudaPointerGetAttributes and copies device ->
+ *     host itself when they are host memory (pinned or pageable), in which case
+ *     the call returns after the copy has completed.
+ *   - The context owns every device buffer it allocates (state, histograms,
+ *     checkpoints, scratch); callers own the buffers they pass in.
+ *   - Calls on one context must not run concurrently from several host threads.
+ */
+#ifndef ABP_H
+#define ABP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define ABP_API __attribute__((visibility("default")))
+#else
+#define ABP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct abp_ctx abp_ctx;
+
+typedef enum {
+    ABP_OK = 0,
+    ABP_EINVAL = 1,   /* an argument is out of range, inconsistent or NULL */
+    ABP_ENOMEM = 2,   /* a device or host allocation failed */
+    ABP_ECUDA = 3,    /* a CUDA runtime call failed (message has the CUDA error) */
+    ABP_ETIMEOUT = 4, /* a bounded device-side wait expired; results are invalid */
+    ABP_ESTATE = 5    /* the call is out of order (e.g. abp_reduce before abp_set_params) */
+} abp_status;
+
+/* Parameters of one set, Sec. 2: Eqs. (ereservoir), (velocity), (pot).
+ * asym is the weight a of the second harmonic of Eq. (pot) (1/4 in the paper;
+ * a = 0 gives a symmetric potential).  Requirements: L > 0, D >= 0, finite. */
+typedef struct {
+    double q, c, d, gamma0, F0, D, h, L, asym;
+} abp_params;
+
+/* Context-wide configuration. */
+typedef struct {
+    uint64_t seed;               /* Philox key */
+    double dt;                   /* Euler-Maruyama time step, > 0 */
+    int32_t v0_mode;             /* 0: v0 = 0; 1: v0 ~ N(0, sqrt(D)) */
+    int32_t state_fp64;          /* 0: FP32 state (production path); 1: FP64 state and FP64
+                                    arithmetic throughout (precision reference; slow on GB300) */
+    int32_t hist_x_bins;         /* bins of x mod L over [0, L); 0 = no position histogram */
+    int32_t hist_v_bins;         /* bins of v over [v_lo, v_hi); 0 = none (+2 out-of-range counters) */
+    double v_lo, v_hi;           /* velocity histogram range, v_hi > v_lo */
+    int64_t snapshot_every;      /* S > 0: histograms of the state after steps S, 2S, ...;
+                                    0: one snapshot after each set's last step */
+    int64_t checkpoint_every;    /* K > 0: keep the state every K steps for abp_backward;
+                                    0: no checkpoints (abp_backward returns ABP_ESTATE) */
+    int32_t particles_per_thread;/* 1, 2 or 4 trajectories per CUDA thread; 0 = choose automatically */
+    int32_t reserved;            /* must be 0 */
+    int64_t steps_per_launch;    /* steps per integrator launch; 0 = choose automatically */
+    uint64_t traj_base;          /* added to every global trajectory id: a process that runs
+                                    one shard of a larger ensemble passes the id of its first
+                                    trajectory, so every trajectory keeps its own noise */
+} abp_config;
+
+/* Create a context on the current CUDA device.  cuda_stream is a cudaStream_t
+ * (NULL = the legacy default stream) on which all work of the context runs.
+ * The configuration is copied.  On success *out owns a context to be released
+ * with abp_destroy. */
+ABP_API abp_status abp_create(abp_ctx **out, const abp_config *cfg, void *cuda_stream);
+
+/* Define the batch: n_sets parameter sets (host array, copied), set i with
+ * n_traj[i] >= 0 trajectories of n_steps[i] >= 0 steps (host arrays, copied;
+ * n_steps[i] < 2^34).  Allocates the trajectory state (28 bytes per FP32
+ * trajectory, plus histograms and checkpoints), draws the initial condition on
+ * the device and zeroes all accumulators.  May be called again to start a new
+ * batch; the previous one is discarded. */
+ABP_API abp_status abp_set_params(abp_ctx *ctx, int32_t n_sets, const abp_params *sets, const int64_t *n_traj,
+                          const int64_t *n_steps);
+
+/* Start the current batch over: redraw the initial condition with the given
+ * seed (the parameters, sizes and device buffers are kept), zero the time sums
+ * and histograms and set every set back to step 0.  Only kernels and memsets
+ * are enqueued; nothing is copied from the host. */
+ABP_API abp_status abp_reset(abp_ctx *ctx, uint64_t seed);
+
+/* Advance every set by min(max_steps, remaining) Euler-Maruyama steps
+ * (max_steps < 0: to completion).  Steps run on the device, trajectory state
+ * stays resident in HBM between calls, and splitting a run into several calls
+ * gives bitwise the same result as one call.  Snapshot histograms are filled
+ * as their steps are reached; checkpoints are stored when checkpoint_every > 0. */
+ABP_API abp_status abp_integrate(abp_ctx *ctx, int64_t max_steps);
+
+/* Number of steps every set has completed so far (host output, n_sets values). */
+ABP_API abp_status abp_progress(const abp_ctx *ctx, int64_t *steps_done);
+
+/* Ensemble reduction (Sec. 2: results averaged over realisations and time).
+ * moments (host or device, may be NULL): [n_sets][8] doubles per set:
+ *   0 mean_v  = (1/M) sum_i vbar_i, vbar_i = (1/n) sum_{k<n} v_k = (x_n - x_0)/(n dt)
+ *             (n = steps done)
+ *   1 se_v    = sqrt(sum_i (vbar_i - mean_v)^2 / ((M-1) M))
+ *   2 msd     = (1/M) sum_i (x_n - x_0)^2
+ *   3 d_eff   = ((1/M) sum_i dx_i^2 - ((1/M) sum_i dx_i)^2) / (2 n dt)
+ *   4..7      = sum_i vbar_i, sum_i vbar_i^2, sum_i dx_i, sum_i dx_i^2
+ * hist_x (host or device, may be NULL): uint32 [n_snap][n_sets][hist_x_bins]
+ * hist_v (host or device, may be NULL): uint32 [n_snap][n_sets][hist_v_bins + 2],
+ *   the last two entries counting v < v_lo and v >= v_hi.
+ * n_snap = max over sets of (n_steps / snapshot_every), or 1 when
+ * snapshot_every == 0; snapshots not reached yet are zero.  The sums are taken
+ * in a fixed order, so results are bitwise reproducible. */
+ABP_API abp_status abp_reduce(abp_ctx *ctx, double *moments, uint32_t *hist_x, uint32_t *hist_v);
+
+/* Number of snapshot slots of the current batch (host output). */
+ABP_API abp_status abp_num_snapshots(const abp_ctx *ctx, int64_t *n_snap);
+
+/* Final (current) state of every trajectory, in global trajectory order
+ * (host or device outputs, each of sum(n_traj) doubles; any may be NULL):
+ * x = unwrapped position, x0 = initial position, v, e, vbar = time-averaged
+ * velocity so far. */
+ABP_API abp_status abp_get_state(abp_ctx *ctx, double *x, double *x0, double *v, double *e, double *vbar);
+
+/* Pathwise adjoint.  With the noise held fixed, returns for every set
+ * grad[s][j] = dJ/dtheta_j, J = sum_s dJ_dmean_v[s] * mean_v[s], theta =
+ * (D, q, c, d, gamma0, asym) of that set.  dJ_dmean_v: host or device, n_sets
+ * doubles (NULL = all ones); grad: host or device, [n_sets][6] doubles.
+ * Requires a completed abp_integrate with checkpoint_every > 0 (otherwise
+ * ABP_ESTATE); recomputes each checkpoint interval forward and sweeps it in
+ * reverse, accumulating in FP64. */
+ABP_API abp_status abp_backward(abp_ctx *ctx, const double *dJ_dmean_v, double *grad);
+
+/* Number of kernels this context has enqueued since it was created (host output). */
+ABP_API abp_status abp_kernel_launches(const abp_ctx *ctx, int64_t *launches);
+
+/* Wait for the context's stream and report any device-side failure. */
+ABP_API abp_status abp_synchronize(abp_ctx *ctx);
+
+/* Release the context and every buffer it owns.  NULL is allowed. */
+ABP_API void abp_destroy(abp_ctx *ctx);
+
+/* Message of the last failed call on ctx ("" if none; static text if ctx is NULL). */
+ABP_API const char *abp_last_error(const abp_ctx *ctx);
+
+/* --- building blocks exposed for verification ---------------------------- */
+
+/* Philox4x32-10 blocks on the device: out[i][0..3] = Philox(key = seed,
+ * ctr = (m[i]_lo, m[i]_hi, traj[i]_lo, traj[i]_hi)).  traj, m: device arrays of
+ * n uint64; out: device array of 4n uint32.  Runs on cuda_stream. */
+ABP_API abp_status abp_philox(uint64_t seed, const uint64_t *traj, const uint64_t *m, int64_t n, uint32_t *out,
+                      void *cuda_stream);
+
+/* The FP32 standard normals z_k, k = n0 .. n0 + count - 1, that drive the steps
+ * of trajectory traj (device output of count floats). */
+ABP_API abp_status abp_normals(uint64_t seed, uint64_t traj, uint64_t n0, int64_t count, float *out,
+                       void *cuda_stream);
+
+/* Library version string. */
+ABP_API const char *abp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ABP_H */

@@ -1,0 +1,381 @@
+"""Thin Python binding of the C ABI in ``include/abp.h`` (argument marshalling only).
+
+Every computation runs in ``libabp.so`` (sm_103a CUDA).  PyTorch is used for device
+memory and streams only.  There is no fallback: if the library is missing or cannot be
+loaded, every entry point raises.
+
+The functions keep the ABI's names (``abp_create``, ``abp_set_params``, ``abp_integrate``,
+``abp_reduce``, ``abp_backward`` ...); :class:`Ensemble` wraps them for the common
+"set parameters, integrate, reduce" flow and :class:`MeanVelocity` exposes the adjoint
+as a ``torch.autograd.Function``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import workloads as W
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libabp.so")
+
+ABP_OK, ABP_EINVAL, ABP_ENOMEM, ABP_ECUDA, ABP_ETIMEOUT, ABP_ESTATE = range(6)
+_STATUS = {0: "ABP_OK", 1: "ABP_EINVAL", 2: "ABP_ENOMEM", 3: "ABP_ECUDA", 4: "ABP_ETIMEOUT", 5: "ABP_ESTATE"}
+GRAD_PARAMS = ("D", "q", "c", "d", "gamma0", "asym")
+MOMENT_NAMES = ("mean_v", "se_v", "msd", "d_eff", "sum_vbar", "sum_vbar2", "sum_dx", "sum_dx2")
+
+
+class AbpError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (_STATUS.get(status, str(status)), msg))
+        self.status = status
+
+
+class abp_params(C.Structure):
+    _fields_ = [(n, C.c_double) for n in W.PARAM_NAMES]
+
+
+class abp_config(C.Structure):
+    _fields_ = [
+        ("seed", C.c_uint64),
+        ("dt", C.c_double),
+        ("v0_mode", C.c_int32),
+        ("state_fp64", C.c_int32),
+        ("hist_x_bins", C.c_int32),
+        ("hist_v_bins", C.c_int32),
+        ("v_lo", C.c_double),
+        ("v_hi", C.c_double),
+        ("snapshot_every", C.c_int64),
+        ("checkpoint_every", C.c_int64),
+        ("particles_per_thread", C.c_int32),
+        ("reserved", C.c_int32),
+        ("steps_per_launch", C.c_int64),
+        ("traj_base", C.c_uint64),
+    ]
+
+
+_lock = threading.Lock()
+_lib = None
+_VP = C.c_void_p
+
+
+def lib():
+    """Load libabp.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libabp.so not found at %s: build it with "
+                               "`python -m paper_1104_2499_gb300.build` (needs nvcc)" % LIB_PATH)
+        L = C.CDLL(LIB_PATH)
+        st = C.c_int
+        L.abp_create.argtypes = [C.POINTER(_VP), C.POINTER(abp_config), _VP]
+        L.abp_create.restype = st
+        L.abp_set_params.argtypes = [_VP, C.c_int32, C.POINTER(abp_params), C.POINTER(C.c_int64),
+                                     C.POINTER(C.c_int64)]
+        L.abp_set_params.restype = st
+        L.abp_reset.argtypes = [_VP, C.c_uint64]
+        L.abp_reset.restype = st
+        L.abp_kernel_launches.argtypes = [_VP, C.POINTER(C.c_int64)]
+        L.abp_kernel_launches.restype = st
+        L.abp_integrate.argtypes = [_VP, C.c_int64]
+        L.abp_integrate.restype = st
+        L.abp_progress.argtypes = [_VP, C.POINTER(C.c_int64)]
+        L.abp_progress.restype = st
+        L.abp_num_snapshots.argtypes = [_VP, C.POINTER(C.c_int64)]
+        L.abp_num_snapshots.restype = st
+        L.abp_reduce.argtypes = [_VP, _VP, _VP, _VP]
+        L.abp_reduce.restype = st
+        L.abp_get_state.argtypes = [_VP, _VP, _VP, _VP, _VP, _VP]
+        L.abp_get_state.restype = st
+        L.abp_backward.argtypes = [_VP, _VP, _VP]
+        L.abp_backward.restype = st
+        L.abp_synchronize.argtypes = [_VP]
+        L.abp_synchronize.restype = st
+        L.abp_destroy.argtypes = [_VP]
+        L.abp_destroy.restype = None
+        L.abp_last_error.argtypes = [_VP]
+        L.abp_last_error.restype = C.c_char_p
+        L.abp_philox.argtypes = [C.c_uint64, _VP, _VP, C.c_int64, _VP, _VP]
+        L.abp_philox.restype = st
+        L.abp_normals.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64, C.c_int64, _VP, _VP]
+        L.abp_normals.restype = st
+        L.abp_version.argtypes = []
+        L.abp_version.restype = C.c_char_p
+        _lib = L
+        return L
+
+
+def _check(status: int, ctx=None, what: str = ""):
+    if status != ABP_OK:
+        msg = lib().abp_last_error(ctx).decode() if ctx else what
+        raise AbpError(status, msg or what)
+
+
+def _ptr(x):
+    """Raw address of a torch tensor / numpy array (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    if not x.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return x.data_ptr()
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+# ----------------------------------------------------------------------- ABI names
+
+def abp_create(cfg: abp_config, stream=None):
+    h = _VP()
+    _check(lib().abp_create(C.byref(h), C.byref(cfg), _stream_ptr(stream)), what="abp_create rejected the configuration")
+    return h
+
+
+def abp_set_params(ctx, sets, n_traj, n_steps):
+    n = len(sets)
+    arr = (abp_params * max(n, 1))()
+    for i, s in enumerate(sets):
+        for k in W.PARAM_NAMES:
+            setattr(arr[i], k, float(s[k]))
+    M = (C.c_int64 * max(n, 1))(*[int(m) for m in n_traj])
+    N = (C.c_int64 * max(n, 1))(*[int(v) for v in n_steps])
+    _check(lib().abp_set_params(ctx, n, arr, M, N), ctx)
+
+
+def abp_reset(ctx, seed: int):
+    _check(lib().abp_reset(ctx, int(seed)), ctx)
+
+
+def abp_kernel_launches(ctx) -> int:
+    out = C.c_int64()
+    _check(lib().abp_kernel_launches(ctx, C.byref(out)), ctx)
+    return int(out.value)
+
+
+def abp_integrate(ctx, max_steps: int = -1):
+    _check(lib().abp_integrate(ctx, int(max_steps)), ctx)
+
+
+def abp_progress(ctx, n_sets: int):
+    out = (C.c_int64 * max(n_sets, 1))()
+    _check(lib().abp_progress(ctx, out), ctx)
+    return [int(out[i]) for i in range(n_sets)]
+
+
+def abp_num_snapshots(ctx) -> int:
+    out = C.c_int64()
+    _check(lib().abp_num_snapshots(ctx, C.byref(out)), ctx)
+    return int(out.value)
+
+
+def abp_reduce(ctx, moments=None, hist_x=None, hist_v=None):
+    _check(lib().abp_reduce(ctx, _ptr(moments), _ptr(hist_x), _ptr(hist_v)), ctx)
+
+
+def abp_get_state(ctx, x=None, x0=None, v=None, e=None, vbar=None):
+    _check(lib().abp_get_state(ctx, _ptr(x), _ptr(x0), _ptr(v), _ptr(e), _ptr(vbar)), ctx)
+
+
+def abp_backward(ctx, dJ_dmean_v=None, grad=None):
+    _check(lib().abp_backward(ctx, _ptr(dJ_dmean_v), _ptr(grad)), ctx)
+
+
+def abp_synchronize(ctx):
+    _check(lib().abp_synchronize(ctx), ctx)
+
+
+def abp_destroy(ctx):
+    if ctx:
+        lib().abp_destroy(ctx)
+
+
+def abp_philox(seed: int, traj, m, out, stream=None):
+    """traj, m: uint64 device tensors (int64 dtype reinterpreted); out: int32 device tensor [n, 4]."""
+    n = traj.numel()
+    _check(lib().abp_philox(seed, _ptr(traj), _ptr(m), n, _ptr(out), _stream_ptr(stream)),
+           what="abp_philox rejected its arguments")
+
+
+def abp_normals(seed: int, traj: int, n0: int, out, stream=None):
+    _check(lib().abp_normals(seed, traj, n0, out.numel(), _ptr(out), _stream_ptr(stream)),
+           what="abp_normals rejected its arguments")
+
+
+def abp_version() -> str:
+    return lib().abp_version().decode()
+
+
+# ----------------------------------------------------------------------- convenience
+
+def make_config(w: "W.Workload", *, state_fp64: bool = False, particles_per_thread: int = 0,
+                steps_per_launch: int = 0, traj_base: int = 0) -> abp_config:
+    c = abp_config()
+    c.seed = int(w.seed)
+    c.dt = float(w.dt)
+    c.v0_mode = int(w.v0_mode)
+    c.state_fp64 = 1 if state_fp64 else 0
+    c.hist_x_bins = int(w.hist_x_bins)
+    c.hist_v_bins = int(w.hist_v_bins)
+    c.v_lo = float(w.v_lo)
+    c.v_hi = float(w.v_hi)
+    c.snapshot_every = int(w.snapshot_every)
+    c.checkpoint_every = int(w.checkpoint_every)
+    c.particles_per_thread = int(particles_per_thread)
+    c.reserved = 0
+    c.steps_per_launch = int(steps_per_launch)
+    c.traj_base = int(traj_base)
+    return c
+
+
+class Ensemble:
+    """One context bound to a workload: ``run()`` integrates it and ``results()`` reduces it.
+
+    Outputs are torch tensors on the context's device unless ``host=True``.
+    """
+
+    def __init__(self, w: "W.Workload", *, stream=None, state_fp64=False, particles_per_thread=0,
+                 steps_per_launch=0, traj_base=0, device=None):
+        import torch
+
+        self.torch = torch
+        self.w = w
+        self.device = torch.device(device or "cuda")
+        self.stream = stream
+        with torch.cuda.device(self.device):
+            self.ctx = abp_create(make_config(w, state_fp64=state_fp64, particles_per_thread=particles_per_thread,
+                                              steps_per_launch=steps_per_launch, traj_base=traj_base), stream)
+        self._params_set = False
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            abp_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_params(self):
+        abp_set_params(self.ctx, self.w.sets, self.w.n_traj, self.w.n_steps)
+        self._params_set = True
+
+    def reset(self, seed: int | None = None):
+        abp_reset(self.ctx, self.w.seed if seed is None else seed)
+
+    def launches(self) -> int:
+        return abp_kernel_launches(self.ctx)
+
+    def integrate(self, max_steps: int = -1):
+        abp_integrate(self.ctx, max_steps)
+
+    def run(self):
+        self.set_params()
+        self.integrate(-1)
+
+    def n_snapshots(self) -> int:
+        return abp_num_snapshots(self.ctx)
+
+    def results(self, host: bool = False) -> dict:
+        torch = self.torch
+        dev = "cpu" if host else self.device
+        kw = dict(device=dev)
+        if host:
+            kw["pin_memory"] = True
+        S = self.w.n_sets
+        mom = torch.empty((S, 8), dtype=torch.float64, **kw)
+        ns = self.n_snapshots()
+        hx = torch.empty((ns, S, self.w.hist_x_bins), dtype=torch.int32, **kw) if self.w.hist_x_bins and ns else None
+        hv = (torch.empty((ns, S, self.w.hist_v_bins + 2), dtype=torch.int32, **kw)
+              if self.w.hist_v_bins and ns else None)
+        abp_reduce(self.ctx, mom, hx, hv)
+        out = {"moments": mom}
+        if hx is not None:
+            out["hist_x"] = hx
+        if hv is not None:
+            out["hist_v"] = hv
+        return out
+
+    def state(self, host: bool = False) -> dict:
+        torch = self.torch
+        T = self.w.total_traj
+        dev = "cpu" if host else self.device
+        out = {k: torch.empty(T, dtype=torch.float64, device=dev) for k in ("x", "x0", "v", "e", "vbar")}
+        abp_get_state(self.ctx, out["x"], out["x0"], out["v"], out["e"], out["vbar"])
+        return out
+
+    def backward(self, dJ=None, host: bool = False):
+        torch = self.torch
+        dev = "cpu" if host else self.device
+        g = torch.empty((self.w.n_sets, 6), dtype=torch.float64, device=dev)
+        abp_backward(self.ctx, dJ, g)
+        return g
+
+    def synchronize(self):
+        abp_synchronize(self.ctx)
+
+
+class MeanVelocity:
+    """``torch.autograd.Function`` over the ensemble: ``theta`` [n_sets, 6] holds
+    (D, q, c, d, gamma0, asym) of every set (the other parameters come from the workload);
+    the forward integrates the batch and returns the mean velocity of every set, the
+    backward is the pathwise adjoint (noise held fixed) of ``abp_backward``.
+
+    Usage: ``mean_v = MeanVelocity.apply(theta, workload)``.
+    """
+
+    _fn = None
+
+    @classmethod
+    def apply(cls, theta, w, **kw):
+        if cls._fn is None:
+            import torch
+
+            class _F(torch.autograd.Function):
+                @staticmethod
+                def forward(ctx, th, wl, opts):
+                    sets = []
+                    th_h = th.detach().double().cpu().numpy()
+                    for i, base in enumerate(wl.sets):
+                        s = dict(base)
+                        for j, name in enumerate(GRAD_PARAMS):
+                            s[name] = float(th_h[i, j])
+                        sets.append(s)
+                    import dataclasses
+
+                    w2 = dataclasses.replace(wl, sets=sets, checkpoint_every=wl.checkpoint_every or 1000)
+                    ens = Ensemble(w2, **opts)
+                    ens.run()
+                    mom = ens.results()["moments"]
+                    ctx.ens = ens
+                    return mom[:, 0].to(th.device, dtype=th.dtype)
+
+                @staticmethod
+                def backward(ctx, g):
+                    ens = ctx.ens
+                    w = g.detach().double().contiguous().to(ens.device)
+                    grad = ens.backward(w)
+                    ens.close()
+                    return grad.to(g.device, dtype=g.dtype), None, None
+
+            cls._fn = _F
+        return cls._fn.apply(theta, w, kw)

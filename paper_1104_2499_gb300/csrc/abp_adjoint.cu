@@ -1,0 +1,329 @@
+// abp_adjoint.cu -- pathwise adjoint of the ensemble mean velocity (abp_backward).
+//
+// With the noise held fixed, the Euler-Maruyama map s_{n+1} = Phi(s_n, theta, z_n)
+// of Eqs. (ereservoir), (velocity), (pot) (Sec. 2) is differentiated in reverse:
+//   lambda_n = (dPhi/ds_n)^T lambda_{n+1} + dJ/ds_n,     g += (dPhi/dtheta)^T lambda_{n+1}
+// for J_i = sum_{n<N} v_n of each trajectory (the time-averaged velocity times N),
+// theta = (D, q, c, d, gamma0, a).  The states are recomputed, not stored:
+//   level 0  checkpoints in HBM every K steps, written by the forward integrator;
+//   level 1  the K-step segment is re-run from its checkpoint, leaving a
+//            sub-checkpoint every kSub steps in context-owned scratch memory;
+//   level 2  each kSub-step sub-chunk is re-run from its sub-checkpoint into
+//            registers and swept in reverse.
+// Every re-run repeats the forward arithmetic bit for bit (same Philox words,
+// same Box-Muller, same FMA sequence, same position folds), so the adjoint sees
+// exactly the trajectory the forward produced.  Gradient terms are summed in
+// FP32 within a segment and in FP64 across segments and trajectories.
+#include <algorithm>
+#include <cmath>
+
+#include "abp.h"
+#include "abp_ctx.cuh"
+#include "abp_device.cuh"
+#include "abp_internal.cuh"
+
+namespace abp {
+namespace {
+
+constexpr int kSub = 8;  // steps per register-resident sub-chunk
+
+struct AdjArgs {
+    Batch b;
+    Ckpt ck;
+    Noise nz;
+    float4 *sub;        // [n_sub][total_traj] sub-checkpoints (scratch)
+    int64_t n_sub;      // sub-checkpoint slots per segment
+    const double *w;    // [n_sets] dJ/dmean_v, NULL = 1
+    double *partials;   // [n_tiles][6]
+};
+
+// Noise of consecutive steps: one Philox block serves steps 4m .. 4m+3.  The
+// pair (nrs, trig) is exactly what the forward integrator feeds its fused
+// multiply-add, so re-runs reproduce the forward states bit for bit.
+struct NoiseCursor {
+    uint32_t m;
+    bool valid;
+    float nrs01, nrs23, c01, s01, c23, s23;
+
+    __device__ void at(const Coef<float> &k, const Noise &nz, uint32_t tlo, uint32_t thi, int64_t n, float &nrs,
+                       float &trig) {
+        const uint32_t mm = (uint32_t)(n >> 2);
+        if (!valid || mm != m) {
+            const uint4 w = philox4x32_10(mm, 0u, tlo, thi, nz.k0, nz.k1);
+            float nr;
+            box_muller_f32(w.x, w.y, nr, c01, s01);
+            nrs01 = k.sigma * nr;
+            box_muller_f32(w.z, w.w, nr, c23, s23);
+            nrs23 = k.sigma * nr;
+            m = mm;
+            valid = true;
+        }
+        const uint32_t j = (uint32_t)(n & 3);
+        nrs = j < 2 ? nrs01 : nrs23;
+        trig = (j & 1) ? (j < 2 ? s01 : s23) : (j < 2 ? c01 : c23);
+    }
+};
+
+// One forward step at absolute index n, including the position fold the
+// integrator applies after every kBlockSteps-th step (y depends on y and
+// yacc only; the fold's error term and the cell index are not needed here).
+__device__ __forceinline__ void fwd(const Coef<float> &k, float nrs, float trig, int64_t n, float &y, float &yacc,
+                                   float &v, float &e) {
+    em_step_f32(k, nrs, trig, y, yacc, v, e);
+    if (((n + 1) & (kBlockSteps - 1)) == 0) {
+        float lo = 0.0f;
+        int32_t cell = 0;
+        fold_position<float>(y, yacc, lo, cell);
+    }
+}
+
+__device__ __forceinline__ void block_sum6(double (&a)[6], double (*red)[6]) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int j = 0; j < 6; ++j) a[j] += __shfl_down_sync(0xffffffffu, a[j], o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0)
+#pragma unroll
+        for (int j = 0; j < 6; ++j) red[warp][j] = a[j];
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) a[j] = lane < nw ? red[lane][j] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int j = 0; j < 6; ++j) a[j] += __shfl_down_sync(0xffffffffu, a[j], o);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) adjoint_kernel(AdjArgs a) {
+    __shared__ double red[kThreads / 32][6];
+    const Batch &b = a.b;
+    const int tile = blockIdx.x;
+    const int set = b.tile_set[tile];
+    const int64_t N = b.set_steps[set];
+    const int64_t K = a.ck.every;
+    const int64_t T = b.total_traj;
+    const abp_params p = b.params[set];
+    const double dt = a.nz.dt;
+    const Coef<float> k = make_coef<float>(p.q, p.c, p.d, p.gamma0, p.F0, p.D, p.h, p.L, p.asym, dt);
+    const float dtf = (float)dt;
+    const float kx = (float)(-2.0 * kPi / p.L);  // d phi / dx with the sign of d cos / d phi
+    const int64_t first = b.tile_first[tile];
+    const int count = b.tile_count[tile];
+    int64_t M = 0;
+    for (int t = b.set_tile_begin[set]; t < b.set_tile_begin[set + 1]; ++t) M += b.tile_count[t];
+
+    double gsum[6] = {0, 0, 0, 0, 0, 0};
+    for (int li0 = 0; li0 < count; li0 += kThreads) {  // uniform loop over the tile's slots
+        const int li = li0 + threadIdx.x;
+        const bool act = li < count && N > 0;
+        const int64_t idx = first + (li < count ? li : count - 1);
+        const uint64_t gid = (uint64_t)idx + a.nz.traj_base;
+        const uint32_t tlo = (uint32_t)gid, thi = (uint32_t)(gid >> 32);
+        float lx = 0.0f, lv = 0.0f, le = 0.0f;
+        double G[6] = {0, 0, 0, 0, 0, 0};
+        if (act) {
+            const int64_t n_seg = (N + K - 1) / K;
+            for (int64_t seg = n_seg - 1; seg >= 0; --seg) {
+                const int64_t s0 = seg * K, s1 = min(s0 + K, N);
+                // level 1: re-run the segment from its checkpoint, leaving sub-checkpoints
+                const float4 c0 = a.ck.ck[(size_t)seg * T + idx];
+                float y = c0.x, yacc = c0.y, v = c0.z, e = c0.w;
+                NoiseCursor nc;
+                nc.valid = false;
+                nc.m = 0;
+                int64_t slot = 0;
+                for (int64_t n = s0; n < s1; ++n) {
+                    if (((n - s0) % kSub) == 0) a.sub[(size_t)(slot++) * T + idx] = make_float4(y, yacc, v, e);
+                    float nrs, trig;
+                    nc.at(k, a.nz, tlo, thi, n, nrs, trig);
+                    fwd(k, nrs, trig, n, y, yacc, v, e);
+                }
+                // level 2: sub-chunks in reverse
+                float acc[6] = {0, 0, 0, 0, 0, 0};
+                for (int64_t j = slot - 1; j >= 0; --j) {
+                    const int64_t n0 = s0 + j * kSub;
+                    const int len = (int)(s1 - n0 < kSub ? s1 - n0 : kSub);
+                    const float4 cj = a.sub[(size_t)j * T + idx];
+                    float ys[kSub], vs[kSub], es[kSub], szs[kSub];
+                    y = cj.x;
+                    yacc = cj.y;
+                    v = cj.z;
+                    e = cj.w;
+                    nc.valid = false;
+#pragma unroll
+                    for (int i = 0; i < kSub; ++i) {
+                        if (i < len) {
+                            float nrs, trig;
+                            nc.at(k, a.nz, tlo, thi, n0 + i, nrs, trig);
+                            ys[i] = y + yacc;  // the position the force sees
+                            vs[i] = v;
+                            es[i] = e;
+                            szs[i] = nrs * trig;
+                            fwd(k, nrs, trig, n0 + i, y, yacc, v, e);
+                        }
+                    }
+#pragma unroll
+                    for (int i = kSub - 1; i >= 0; --i) {
+                        if (i < len) {
+                            const float yy = ys[i], vv = vs[i], ee = es[i];
+                            float sphi, cphi;
+                            __sincosf(fmaf(yy, kTwoPiF, (float)(2.0 * kPi * kPhaseShifted)), &sphi, &cphi);
+                            // parameter terms use lambda_{n+1}
+                            acc[0] = fmaf(lv, szs[i], acc[0]);                  // D
+                            acc[1] += le;                                       // q
+                            acc[2] = fmaf(le, ee, acc[2]);                      // c
+                            acc[3] = fmaf(ee * vv, fmaf(-le, vv, lv), acc[3]);  // d
+                            acc[4] = fmaf(lv, vv, acc[4]);                      // gamma0
+                            acc[5] = fmaf(lv, fmaf(2.0f * cphi, cphi, -1.0f), acc[5]);  // a
+                            // transposed Jacobian of the step, plus dJ/dv_n = 1
+                            const float dvdx = kx * sphi * fmaf(2.0f * k.A4, cphi, k.K);
+                            const float dvdv = fmaf(k.Bd, ee, k.G);
+                            const float dedv = -2.0f * k.Bd * ee * vv;
+                            const float dvde = k.Bd * vv;
+                            const float dede = fmaf(-k.Bd, vv * vv, k.A);
+                            const float nlx = fmaf(dvdx, lv, lx);
+                            const float nlv = fmaf(dtf, lx, fmaf(dvdv, lv, fmaf(dedv, le, 1.0f)));
+                            const float nle = fmaf(dvde, lv, dede * le);
+                            lx = nlx;
+                            lv = nlv;
+                            le = nle;
+                        }
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 6; ++q) G[q] += (double)acc[q];
+            }
+            // initial condition: v0 = sqrt(D) z depends on D
+            if (a.nz.v0_mode == 1) G[0] += (double)lv * (double)a.ck.ck[idx].z;
+        }
+        if (act) {
+            // dmean_v/dtheta = (1 / (M N)) dJ_i/dtheta, scaled by the caller's weight
+            const double wgt = (a.w ? a.w[set] : 1.0) / ((double)M * (double)N);
+            const double Kd = dt * p.h * 0.453 * (2.0 * kPi / p.L);
+            gsum[0] += wgt * (p.D > 0.0 ? G[0] / (2.0 * p.D) : NAN);
+            gsum[1] += wgt * dt * G[1];
+            gsum[2] += wgt * (-dt) * G[2];
+            gsum[3] += wgt * dt * G[3];
+            gsum[4] += wgt * (-dt) * G[4];
+            gsum[5] += wgt * 2.0 * Kd * G[5];
+        }
+    }
+    block_sum6(gsum, red);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int j = 0; j < 6; ++j) a.partials[(size_t)tile * 6 + j] = gsum[j];
+}
+
+__global__ void __launch_bounds__(kThreads) adjoint_set_kernel(Batch b, const double *partials, double *grad) {
+    __shared__ double red[kThreads / 32][6];
+    const int set = blockIdx.x;
+    const int t0 = b.set_tile_begin[set], t1 = b.set_tile_begin[set + 1];
+    double a[6] = {0, 0, 0, 0, 0, 0};
+    for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x)
+#pragma unroll
+        for (int j = 0; j < 6; ++j) a[j] += partials[(size_t)t * 6 + j];
+    block_sum6(a, red);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int j = 0; j < 6; ++j) grad[(size_t)set * 6 + j] = a[j];
+}
+
+bool device_ptr(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+abp_status set_err(abp_ctx *ctx, abp_status st, const char *msg, cudaError_t e = cudaSuccess) {
+    ctx->err = msg;
+    if (e != cudaSuccess) {
+        ctx->err += ": ";
+        ctx->err += cudaGetErrorString(e);
+    }
+    return st;
+}
+
+}  // namespace
+}  // namespace abp
+
+using namespace abp;
+
+extern "C" abp_status abp_backward(abp_ctx *ctx, const double *dJ_dmean_v, double *grad) {
+    if (!ctx) return ABP_EINVAL;
+    if (!grad) return set_err(ctx, ABP_EINVAL, "abp_backward: grad is NULL");
+    if (!ctx->have_batch) return set_err(ctx, ABP_ESTATE, "abp_backward before abp_set_params");
+    if (ctx->cfg.checkpoint_every <= 0)
+        return set_err(ctx, ABP_ESTATE, "abp_backward needs checkpoint_every > 0 during abp_integrate");
+    if (ctx->g < ctx->max_steps) return set_err(ctx, ABP_ESTATE, "abp_backward before the integration completed");
+    const int64_t T = ctx->total_traj;
+    const int64_t n_sub = (ctx->cfg.checkpoint_every + kSub - 1) / kSub;
+    const size_t sub_bytes = sizeof(float4) * (size_t)n_sub * (size_t)T;
+    const size_t part_bytes = sizeof(double) * 6 * (size_t)std::max(ctx->n_tiles, 1);
+    const size_t grad_bytes = sizeof(double) * 6 * (size_t)std::max(ctx->n_sets, 1);
+    const size_t w_bytes = sizeof(double) * (size_t)std::max(ctx->n_sets, 1);
+    const size_t need = sub_bytes + part_bytes + grad_bytes + w_bytes + 4 * 256;
+    DevBuf &sc = ctx->d_adj;
+    if (!sc.p || sc.cap < need) {
+        sc.release();
+        cudaError_t e = cudaMalloc(&sc.p, need);
+        if (e != cudaSuccess) {
+            sc.p = nullptr;
+            cudaGetLastError();
+            return set_err(ctx, ABP_ENOMEM, "abp_backward: scratch allocation failed", e);
+        }
+        sc.cap = need;
+    }
+    sc.bytes = need;
+    auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    char *base = (char *)sc.p;
+    float4 *sub = (float4 *)base;
+    double *partials = (double *)(base + align(sub_bytes));
+    double *gdev = (double *)(base + align(sub_bytes) + align(part_bytes));
+    double *wdev = (double *)(base + align(sub_bytes) + align(part_bytes) + align(grad_bytes));
+    cudaStream_t s = ctx->stream;
+    cudaError_t e = cudaSuccess;
+    const double *w = nullptr;
+    if (dJ_dmean_v) {
+        if (device_ptr(dJ_dmean_v)) {
+            w = dJ_dmean_v;
+        } else {
+            e = cudaMemcpyAsync(wdev, dJ_dmean_v, sizeof(double) * ctx->n_sets, cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return set_err(ctx, ABP_ECUDA, "abp_backward: weight upload", e);
+            w = wdev;
+        }
+    }
+    if (ctx->n_sets == 0) return ABP_OK;
+    if (ctx->n_tiles > 0) {
+        AdjArgs a;
+        a.b = ctx->batch();
+        a.ck = ctx->ckpt();
+        a.nz = ctx->noise();
+        a.sub = sub;
+        a.n_sub = n_sub;
+        a.w = w;
+        a.partials = partials;
+        adjoint_kernel<<<ctx->n_tiles, kThreads, 0, s>>>(a);
+        ctx->launches += 1;
+    }
+    adjoint_set_kernel<<<ctx->n_sets, kThreads, 0, s>>>(ctx->batch(), partials, gdev);
+    ctx->launches += 1;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return set_err(ctx, ABP_ECUDA, "abp_backward: launch", e);
+    const size_t out_bytes = sizeof(double) * 6 * (size_t)ctx->n_sets;
+    if (device_ptr(grad)) {
+        e = cudaMemcpyAsync(grad, gdev, out_bytes, cudaMemcpyDeviceToDevice, s);
+    } else {
+        e = cudaMemcpyAsync(grad, gdev, out_bytes, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    if (e != cudaSuccess) return set_err(ctx, ABP_ECUDA, "abp_backward: gradient copy", e);
+    return ABP_OK;
+}

@@ -1,0 +1,133 @@
+// abp_ctx.cuh -- definition of the opaque abp_ctx of the C ABI, shared by the
+// runtime translation units (abp_api.cu, abp_adjoint.cu).  Not public.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "abp.h"
+#include "abp_internal.cuh"
+
+namespace abp {
+
+constexpr int64_t kMaxSteps = (int64_t)1 << 34;  // counter blocks n >> 2 stay below 2^32
+
+// A device allocation with a capacity (cap) and the size in use (bytes).
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    size_t bytes = 0;
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        bytes = 0;
+    }
+};
+
+}  // namespace abp
+
+struct abp_ctx {
+    using DevBuf = abp::DevBuf;
+    using Batch = abp::Batch;
+    using State = abp::State;
+    using Hist = abp::Hist;
+    using Ckpt = abp::Ckpt;
+    using Noise = abp::Noise;
+
+    abp_config cfg{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int sm_count = 0;
+    std::string err;
+
+    // batch (host mirror)
+    bool have_batch = false;
+    int32_t n_sets = 0;
+    int32_t n_tiles = 0;
+    int64_t total_traj = 0;
+    int64_t max_steps = 0;
+    int64_t g = 0;  // global steps issued: set s has done min(g, n_steps[s])
+    int ppt = 1;
+    int64_t steps_per_launch = 0;
+    int64_t n_snap = 0;
+    int64_t n_ckpt = 0;
+    int64_t launches = 0;  // kernels enqueued by this context
+    std::vector<abp_params> params;
+    std::vector<int64_t> n_traj, n_steps;
+    std::vector<int32_t> set_tile_begin, tile_count, tile_set;
+    std::vector<int64_t> tile_first;
+
+    // device
+    DevBuf d_params, d_steps, d_set_tile_begin, d_tile_first, d_tile_count, d_tile_set;
+    DevBuf d_y, d_yacc, d_ylo, d_v, d_e, d_y0, d_cell;
+    DevBuf d_hx, d_hv, d_ckpt, d_partials, d_moments, d_status;
+    DevBuf d_adj;  // adjoint scratch
+
+    Batch batch() const {
+        Batch b;
+        b.n_sets = n_sets;
+        b.n_tiles = n_tiles;
+        b.total_traj = total_traj;
+        b.params = (const abp_params *)d_params.p;
+        b.set_steps = (const int64_t *)d_steps.p;
+        b.set_tile_begin = (const int32_t *)d_set_tile_begin.p;
+        b.tile_first = (const int64_t *)d_tile_first.p;
+        b.tile_count = (const int32_t *)d_tile_count.p;
+        b.tile_set = (const int32_t *)d_tile_set.p;
+        return b;
+    }
+    State state() const {
+        State s;
+        s.fp64 = cfg.state_fp64 != 0;
+        s.y = d_y.p;
+        s.yacc = d_yacc.p;
+        s.ylo = d_ylo.p;
+        s.v = d_v.p;
+        s.e = d_e.p;
+        s.y0 = d_y0.p;
+        s.cell = (int32_t *)d_cell.p;
+        return s;
+    }
+    Hist hist() const {
+        Hist h;
+        h.x = (uint32_t *)d_hx.p;
+        h.v = (uint32_t *)d_hv.p;
+        h.bx = cfg.hist_x_bins;
+        h.bv = cfg.hist_v_bins;
+        h.v_lo = cfg.v_lo;
+        h.v_hi = cfg.v_hi;
+        h.snap_every = cfg.snapshot_every;
+        h.n_snap = n_snap;
+        return h;
+    }
+    Ckpt ckpt() const {
+        Ckpt c;
+        c.ck = (float4 *)d_ckpt.p;
+        c.every = cfg.checkpoint_every;
+        c.n_slots = n_ckpt;
+        return c;
+    }
+    Noise noise() const {
+        Noise n;
+        n.k0 = (uint32_t)cfg.seed;
+        n.k1 = (uint32_t)(cfg.seed >> 32);
+        n.dt = cfg.dt;
+        n.v0_mode = cfg.v0_mode;
+        n.traj_base = cfg.traj_base;
+        return n;
+    }
+    void release_batch() {
+        // Buffers are kept (and reused by the next batch when large enough);
+        // see release_all() for freeing them.
+        have_batch = false;
+    }
+    void release_all() {
+        for (DevBuf *b : {&d_params, &d_steps, &d_set_tile_begin, &d_tile_first, &d_tile_count, &d_tile_set, &d_y,
+                          &d_yacc, &d_ylo, &d_v, &d_e, &d_y0, &d_cell, &d_hx, &d_hv, &d_ckpt, &d_partials,
+                          &d_moments, &d_adj})
+            b->release();
+        have_batch = false;
+    }
+};
+

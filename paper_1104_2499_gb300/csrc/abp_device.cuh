@@ -1,0 +1,263 @@
+// abp_device.cuh -- device building blocks of the ABP ensemble integrator
+// (arXiv 1104.2499, Sec. 2 and Fig. 1): counter-based noise, Box-Muller, and one
+// explicit Euler-Maruyama step of Eqs. (ereservoir), (velocity), (pot).
+//
+// State per trajectory: position x = L (cell + y + yacc + ylo) (see Coef
+// below), velocity v, depot energy e.  The arithmetic type R is float
+// (production) or double (precision-reference variant).
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace abp {
+
+// --------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  Key (k0, k1), counter
+// (c0..c3); 10 rounds, key bumped by the Weyl constants between rounds.
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
+constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
+
+__device__ __forceinline__ void philox_round(uint32_t &c0, uint32_t &c1, uint32_t &c2, uint32_t &c3, uint32_t k0,
+                                             uint32_t k1) {
+    const uint32_t lo0 = kPhiloxM0 * c0;
+    const uint32_t hi0 = __umulhi(kPhiloxM0, c0);
+    const uint32_t lo1 = kPhiloxM1 * c2;
+    const uint32_t hi1 = __umulhi(kPhiloxM1, c2);
+    c0 = hi1 ^ c1 ^ k0;
+    c1 = lo1;
+    c2 = hi0 ^ c3 ^ k1;
+    c3 = lo0;
+}
+
+__device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                               uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        philox_round(c0, c1, c2, c3, k0, k1);
+        k0 += kPhiloxW0;
+        k1 += kPhiloxW1;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
+// Counter block m of trajectory t under seed (k0, k1).
+__device__ __forceinline__ uint4 noise_block(uint64_t m, uint64_t t, uint32_t k0, uint32_t k1) {
+    return philox4x32_10((uint32_t)m, (uint32_t)(m >> 32), (uint32_t)t, (uint32_t)(t >> 32), k0, k1);
+}
+
+// Round keys of a seed: rk[2r], rk[2r+1] = key of round r.  Passed to the
+// integrator as a kernel parameter, so each key is an operand of the XOR.
+struct RoundKeys {
+    uint32_t rk[20];
+};
+
+// The step noise of one trajectory: counter (m, 0, t_lo, t_hi) for m < 2^32.
+// The first round's products with the trajectory words do not depend on m
+// and are formed once per trajectory (pre0 = hi(M1 t_lo) ^ k0, pre1 = lo(M1 t_lo)).
+struct StepStream {
+    uint32_t pre0, pre1, c3x;  // c3x = t_hi ^ k1 of round 0
+};
+
+__device__ __forceinline__ StepStream step_stream(uint64_t t, const RoundKeys &K) {
+    StepStream s;
+    const uint32_t tlo = (uint32_t)t, thi = (uint32_t)(t >> 32);
+    s.pre0 = __umulhi(kPhiloxM1, tlo) ^ K.rk[0];  // c1 = m_hi = 0
+    s.pre1 = kPhiloxM1 * tlo;
+    s.c3x = thi ^ K.rk[1];
+    return s;
+}
+
+__device__ __forceinline__ uint4 step_block(uint32_t m, const StepStream &s, const RoundKeys &K) {
+    // round 0 with the trajectory half precomputed
+    uint32_t c0 = s.pre0, c1 = s.pre1;
+    uint32_t c2 = __umulhi(kPhiloxM0, m) ^ s.c3x;
+    uint32_t c3 = kPhiloxM0 * m;
+#pragma unroll
+    for (int r = 1; r < 10; ++r) philox_round(c0, c1, c2, c3, K.rk[2 * r], K.rk[2 * r + 1]);
+    return make_uint4(c0, c1, c2, c3);
+}
+
+// Counter of the initial-condition draw (m = 2^63; step counters stay below 2^32).
+constexpr uint64_t kInitCounter = 0x8000000000000000ull;
+
+// --------------------------------------------------------------------------
+// Hardware approximations used by the FP32 path.  The approximate square
+// root is the PTX instruction itself; log2 and sin/cos are CUDA's intrinsics.
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr float kTwoPiF = 6.28318530717958647692f;
+constexpr float kLn2F = 0.69314718055994530942f;
+
+// Box-Muller of one word pair, FP32.  u1 = (wa + 1/2) 2^-32 (I2F rounds to
+// nearest, the fused multiply-add adds the half exactly), u2 = floor(wb/2^9)
+// 2^-23 built from the top 23 bits.  The angle is taken as 2 pi (u2 - 1/2) in
+// [-pi, pi) so that the hardware sin/cos see a small argument; that flips both
+// signs, which is folded into the returned radius:
+//   z_even = nr * cs,  z_odd = nr * sn,  nr = -sqrt(-2 ln u1).
+__device__ __forceinline__ void box_muller_f32(uint32_t wa, uint32_t wb, float &nr, float &cs, float &sn) {
+    const float u1 = fmaf(__uint2float_rn(wa), 0x1p-32f, 0x1p-33f);
+    const float l2 = __log2f(u1);                       // <= 0
+    nr = -sqrt_approx(fabsf(l2 * (-2.0f * kLn2F)));
+    const float u2h = __uint_as_float(0x3f800000u | (wb >> 9)) - 1.5f;  // u2 - 1/2, exact
+    __sincosf(u2h * kTwoPiF, &sn, &cs);
+}
+
+// Same mapping in FP64 (precision-reference variant).
+__device__ __forceinline__ void box_muller_f64(uint32_t wa, uint32_t wb, double &z_even, double &z_odd) {
+    const double u1 = ((double)wa + 0.5) * 0x1p-32;
+    const double u2 = (double)(wb >> 9) * 0x1p-23;
+    const double r = sqrt(-2.0 * log(u1));
+    double s, c;
+    sincospi(2.0 * u2, &s, &c);
+    z_even = r * c;
+    z_odd = r * s;
+}
+
+// --------------------------------------------------------------------------
+// Per-set coefficients of the Euler-Maruyama map, built once per thread from
+// the set's parameters.  With K = dt h 0.453 (2 pi / L) and c = cos phi,
+//   -U'(x) dt = K (c + 2a cos 2phi) = K c + 4 a K c^2 - 2 a K      (Eq. (pot))
+//   e' = e (1 - dt c - dt d v^2) + dt q                            (Eq. (ereservoir))
+//   v' = v (1 - dt gamma0 + dt d e) + dt F0 - 2aK + c (K + 4aK c) + sqrt(2 D dt) z
+//                                                                  (Eq. (velocity))
+//   x' = x + v dt                                                  (dx/dt = v)
+// Position.  x = L (cell + y + yacc + ylo): y is the fraction of the period,
+// yacc collects the increments v dt / L of the current block of kBlockSteps
+// steps (a small number, so each increment keeps almost all its bits), and
+// at the block end yacc is added to y, whole periods move into cell and the
+// rounding errors of both operations go to ylo, which only the displacement
+// (never the force) reads.  This is the remedy for the precision issue the
+// paper points out for single precision: never add very small numbers to
+// very big ones.
+template <typename R>
+struct Coef {
+    R A;     // 1 - dt c
+    R Bd;    // dt d
+    R Cq;    // dt q
+    R G;     // 1 - dt gamma0
+    R sigma; // sqrt(2 D dt)
+    R F;     // dt F0 - 2 a K
+    R K;     // dt h 0.453 2 pi / L
+    R A4;    // 4 a K
+    R dtL;   // dt / L
+};
+
+// Phase of the potential: phi = 2 pi (y + 0.1903) = 2 pi (y - 0.8097) + 2 pi.
+// The second form keeps |phi| < 2 pi for the y + yacc values that occur.
+constexpr double kPhase = 0.1903;
+constexpr double kPhaseShifted = 0.1903 - 1.0;
+
+template <typename R>
+__device__ __forceinline__ Coef<R> make_coef(double q, double c, double d, double gamma0, double F0, double D,
+                                             double h, double L, double a, double dt) {
+    Coef<R> k;
+    const double K = dt * h * 0.453 * (2.0 * kPi / L);
+    k.A = (R)(1.0 - dt * c);
+    k.Bd = (R)(dt * d);
+    k.Cq = (R)(dt * q);
+    k.G = (R)(1.0 - dt * gamma0);
+    k.sigma = (R)sqrt(2.0 * D * dt);
+    k.F = (R)(dt * F0 - 2.0 * a * K);
+    k.K = (R)K;
+    k.A4 = (R)(4.0 * a * K);
+    k.dtL = (R)(dt / L);
+    return k;
+}
+
+__device__ __forceinline__ float cos_phase(float y) {
+    return __cosf(fmaf(y, kTwoPiF, (float)(2.0 * kPi * kPhaseShifted)));
+}
+__device__ __forceinline__ double cos_phase(double y) { return cospi(2.0 * (y + kPhase)); }
+
+// One Euler-Maruyama step; every right-hand side uses the step-n values.
+// `sz` is sigma * z_n.
+template <typename R>
+__device__ __forceinline__ void em_step(const Coef<R> &k, R sz, R y, R &yacc, R &v, R &e) {
+    const R cphi = cos_phase(y + yacc);
+    const R t1 = fma(-k.Bd, v * v, k.A);
+    const R g = fma(k.Bd, e, k.G);
+    const R a1 = sz + k.F;
+    const R a2 = fma(g, v, a1);
+    const R P = fma(k.A4, cphi, k.K);
+    const R vn = fma(P, cphi, a2);
+    yacc = fma(v, k.dtL, yacc);
+    e = fma(e, t1, k.Cq);
+    v = vn;
+}
+
+// FP32 form with sigma folded into the Box-Muller radius: a1 = (-sigma r) *
+// trig + F is one FMA.
+__device__ __forceinline__ void em_step_f32(const Coef<float> &k, float nrs, float trig, float y, float &yacc,
+                                            float &v, float &e) {
+    const float cphi = cos_phase(y + yacc);
+    const float t1 = fmaf(-k.Bd, v * v, k.A);
+    const float g = fmaf(k.Bd, e, k.G);
+    const float a1 = fmaf(nrs, trig, k.F);
+    const float a2 = fmaf(g, v, a1);
+    const float P = fmaf(k.A4, cphi, k.K);
+    const float vn = fmaf(P, cphi, a2);
+    yacc = fmaf(v, k.dtL, yacc);
+    e = fmaf(e, t1, k.Cq);
+    v = vn;
+}
+
+template <typename R>
+__device__ __forceinline__ R floor_r(R x);
+template <>
+__device__ __forceinline__ float floor_r<float>(float x) { return floorf(x); }
+template <>
+__device__ __forceinline__ double floor_r<double>(double x) { return floor(x); }
+
+// Error-free sum (Knuth's TwoSum): s + err == a + b exactly.
+template <typename R>
+__device__ __forceinline__ R two_sum(R a, R b, R &err) {
+    const R s = a + b;
+    const R bb = s - a;
+    err = (a - (s - bb)) + (b - bb);
+    return s;
+}
+
+// End of a block of kBlockSteps steps: fold yacc into y and move whole
+// periods into cell.  y's new value depends on (y, yacc) only; the rounding
+// errors are added to ylo.
+template <typename R>
+__device__ __forceinline__ void fold_position(R &y, R &yacc, R &ylo, int32_t &cell) {
+    R e1, e2;
+    const R s = two_sum(y, yacc, e1);
+    const R fl = floor_r<R>(s);
+    const R w = two_sum(s, -fl, e2);
+    y = w;
+    yacc = 0;
+    ylo += e1 + e2;
+    cell += (int32_t)fl;
+}
+
+// The standard normal for step n from its counter block (generic, one step).
+__device__ __forceinline__ float normal_from_block_f32(uint4 w, uint32_t k) {
+    float nr, cs, sn;
+    if (k < 2)
+        box_muller_f32(w.x, w.y, nr, cs, sn);
+    else
+        box_muller_f32(w.z, w.w, nr, cs, sn);
+    return (k & 1) ? nr * sn : nr * cs;
+}
+
+__device__ __forceinline__ double normal_from_block_f64(uint4 w, uint32_t k) {
+    double ze, zo;
+    if (k < 2)
+        box_muller_f64(w.x, w.y, ze, zo);
+    else
+        box_muller_f64(w.z, w.w, ze, zo);
+    return (k & 1) ? zo : ze;
+}
+
+}  // namespace abp

@@ -1,0 +1,93 @@
+// abp_internal.cuh -- device-side views shared by the C-ABI runtime
+// (abp_api.cu) and the kernels (abp_kernels.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "abp.h"
+
+namespace abp {
+
+// Trajectories per CUDA block of the integrator and the per-tile kernels.
+constexpr int kThreads = 256;
+// Steps between position folds (yacc into y, whole periods into cell).  Folds
+// happen at absolute step multiples, so any split of a run into launches gives
+// bitwise identical arithmetic.
+constexpr int kBlockSteps = 64;
+
+// One batch of parameter sets, tiled for the device.  A tile is a contiguous
+// run of at most kThreads * ppt trajectories of one set; tiles of a set are
+// consecutive.
+struct Batch {
+    int32_t n_sets;
+    int32_t n_tiles;
+    int64_t total_traj;
+    const abp_params *params;      // [n_sets]
+    const int64_t *set_steps;      // [n_sets] steps to run
+    const int32_t *set_tile_begin; // [n_sets + 1]
+    const int64_t *tile_first;     // [n_tiles] first global trajectory id (= state index)
+    const int32_t *tile_count;     // [n_tiles] trajectories in the tile (>= 1)
+    const int32_t *tile_set;       // [n_tiles]
+};
+
+// Structure-of-arrays trajectory state.  Element type is float (fp64 = false)
+// or double (fp64 = true) for y, yacc, ylo, v, e, y0.
+// x = L (cell + y + yacc + ylo); the time-averaged velocity of n steps is
+// (x_n - x_0) / (n dt), since the scheme advances x by v_k dt at every step.
+struct State {
+    bool fp64;
+    void *y;       // fraction of the period
+    void *yacc;    // increments v dt / L of the open block of kBlockSteps steps
+    void *ylo;     // rounding errors of the folds (displacement only)
+    void *v;       // velocity
+    void *e;       // depot energy
+    void *y0;      // initial fraction (x0 = L y0)
+    int32_t *cell; // period index
+};
+
+struct Hist {
+    uint32_t *x;         // [n_snap][n_sets][bx]
+    uint32_t *v;         // [n_snap][n_sets][bv + 2]
+    int32_t bx, bv;
+    double v_lo, v_hi;
+    int64_t snap_every;  // 0: after the last step of each set
+    int64_t n_snap;
+};
+
+// Checkpoints for the adjoint: state after steps 0, K, 2K, ... as
+// (y, yacc, v, e) -- everything the dynamics read -- slot-major:
+// ck[slot * total_traj + traj].
+struct Ckpt {
+    float4 *ck;
+    int64_t every;  // 0: none
+    int64_t n_slots;
+};
+
+struct Noise {
+    uint32_t k0, k1;     // Philox key = seed
+    double dt;
+    int32_t v0_mode;
+    uint64_t traj_base;  // added to every state index to give the global trajectory id
+    uint32_t rk[20];     // round keys: rk[2r], rk[2r+1] = (k0 + r W0, k1 + r W1)
+};
+
+cudaError_t launch_init(const Batch &b, const State &s, const Hist &h, const Ckpt &c, const Noise &nz,
+                        cudaStream_t st);
+cudaError_t launch_integrate(const Batch &b, const State &s, const Hist &h, const Ckpt &c, const Noise &nz,
+                             int ppt, int64_t g0, int64_t g1, cudaStream_t st);
+// partials: [n_tiles][4] scratch; sums: [n_sets][4]; moments: [n_sets][8] (may alias nothing).
+cudaError_t launch_reduce(const Batch &b, const State &s, const Noise &nz, int64_t g, double *partials,
+                          double *moments, cudaStream_t st);
+cudaError_t launch_get_state(const Batch &b, const State &s, double dt, int64_t g, double *x, double *x0, double *v,
+                             double *e, double *vbar, cudaStream_t st);
+cudaError_t launch_philox(uint32_t k0, uint32_t k1, const uint64_t *traj, const uint64_t *m, int64_t n,
+                          uint32_t *out, cudaStream_t st);
+cudaError_t launch_normals(uint32_t k0, uint32_t k1, uint64_t traj, uint64_t n0, int64_t count, float *out,
+                           cudaStream_t st);
+
+// Integrator kernel attributes for the launch-shape choice.
+cudaError_t integrate_occupancy(bool fp64, int ppt, size_t smem, int *blocks_per_sm);
+
+}  // namespace abp

@@ -1,0 +1,579 @@
+// abp_kernels.cu -- sm_103a kernels of the ABP ensemble integrator
+// (arXiv 1104.2499, Sec. 2, Fig. 1).
+//
+//   init_kernel       initial condition of every trajectory (Philox counter 2^63)
+//   integrate_kernel  the hot loop: Philox4x32-10 -> Box-Muller -> Euler-Maruyama
+//                     with the state in registers for thousands of steps,
+//                     block-compensated position, shared-memory snapshot
+//                     histograms and adjoint checkpoints
+//   tile_reduce_kernel / set_reduce_kernel
+//                     fixed-order FP64 ensemble reduction (mean velocity,
+//                     standard error, MSD, D_eff)
+//   get_state_kernel  per-trajectory readback in FP64
+//   philox_kernel / normals_kernel  raw noise for verification
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+
+#include "abp_device.cuh"
+#include "abp_internal.cuh"
+
+// Minimum resident blocks per SM requested from the compiler for the
+// integrator (bounds its register use); 0 leaves the choice to the compiler.
+#ifndef ABP_MIN_BLOCKS
+#define ABP_MIN_BLOCKS 0
+#endif
+#if ABP_MIN_BLOCKS > 0
+#define ABP_INTEGRATE_BOUNDS __launch_bounds__(abp::kThreads, ABP_MIN_BLOCKS)
+#else
+#define ABP_INTEGRATE_BOUNDS __launch_bounds__(abp::kThreads)
+#endif
+
+namespace abp {
+
+namespace {
+
+template <typename R>
+struct SV {
+    R *y, *yacc, *ylo, *v, *e, *y0;
+    int32_t *cell;
+};
+
+template <typename R>
+__host__ __device__ SV<R> view(const State &s) {
+    return SV<R>{(R *)s.y, (R *)s.yacc, (R *)s.ylo, (R *)s.v, (R *)s.e, (R *)s.y0, s.cell};
+}
+
+// Displacement in periods, x_n - x_0 = L * disp, accumulated in FP64.
+template <typename R>
+__device__ __forceinline__ double disp_periods(const SV<R> &s, int64_t t) {
+    return (((double)s.cell[t] + (double)s.y[t]) + ((double)s.yacc[t] + (double)s.ylo[t])) - (double)s.y0[t];
+}
+
+// ---------------------------------------------------------------- snapshots
+
+// Bin of the position fraction y (any real; wrapped here) into [0, bx).
+template <typename R>
+__device__ __forceinline__ int bin_x(R y, int bx) {
+    const R yb = y - floor_r<R>(y);
+    int b = (int)(yb * (R)bx);
+    return b < bx ? (b < 0 ? 0 : b) : bx - 1;
+}
+
+// Bin of v: [0, bv) inside [v_lo, v_hi), bv for v < v_lo, bv + 1 for v >= v_hi.
+template <typename R>
+__device__ __forceinline__ int bin_v(R v, R v_lo, R v_hi, R scale, int bv) {
+    if (!(v >= v_lo)) return bv;  // also catches NaN as underflow
+    if (v >= v_hi) return bv + 1;
+    int b = (int)((v - v_lo) * scale);
+    return b < bv ? b : bv - 1;
+}
+
+// Add the block's counts to the global histogram of (snap, set) and clear
+// the shared copy.  Must be reached by every thread of the block.
+__device__ __forceinline__ void flush_hist(uint32_t *sh, const Hist &h, int64_t snap, int32_t set, int32_t n_sets) {
+    __syncthreads();
+    const int nb = h.bx + (h.bv > 0 ? h.bv + 2 : 0);
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        const uint32_t c = sh[i];
+        if (c) {
+            if (i < h.bx)
+                atomicAdd(&h.x[((size_t)snap * n_sets + set) * h.bx + i], c);
+            else
+                atomicAdd(&h.v[((size_t)snap * n_sets + set) * (h.bv + 2) + (i - h.bx)], c);
+        }
+        sh[i] = 0;
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------- init
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads) init_kernel(Batch b, State st, Hist h, Ckpt ck, Noise nz) {
+    extern __shared__ uint32_t sh[];
+    const SV<R> s = view<R>(st);
+    const int tile = blockIdx.x;
+    const int set = b.tile_set[tile];
+    const int64_t first = b.tile_first[tile];
+    const int count = b.tile_count[tile];
+    const abp_params p = b.params[set];
+    const bool snap0 = h.snap_every <= 0 && b.set_steps[set] == 0 && (h.bx > 0 || h.bv > 0);
+    const int nb = h.bx + (h.bv > 0 ? h.bv + 2 : 0);
+    if (snap0) {
+        for (int i = threadIdx.x; i < nb; i += blockDim.x) sh[i] = 0;
+        __syncthreads();
+    }
+    for (int li = threadIdx.x; li < count; li += blockDim.x) {
+        const int64_t t = first + li;
+        const uint4 w = noise_block(kInitCounter, (uint64_t)t + nz.traj_base, nz.k0, nz.k1);
+        const R y0 = (R)(w.x >> 8) * (R)0x1p-24;
+        R v0 = 0;
+        if (nz.v0_mode == 1) {
+            if constexpr (sizeof(R) == 4) {
+                float nr, cs, sn;
+                box_muller_f32(w.y, w.z, nr, cs, sn);
+                v0 = (float)sqrt(p.D) * (nr * cs);
+            } else {
+                double ze, zo;
+                box_muller_f64(w.y, w.z, ze, zo);
+                v0 = sqrt(p.D) * ze;
+            }
+        }
+        s.y[t] = y0;
+        s.y0[t] = y0;
+        s.yacc[t] = 0;
+        s.ylo[t] = 0;
+        s.v[t] = v0;
+        s.e[t] = 0;
+        s.cell[t] = 0;
+        if (ck.every > 0 && sizeof(R) == 4) ck.ck[t] = make_float4((float)y0, 0.0f, (float)v0, 0.0f);
+        if (snap0) {
+            if (h.bx > 0) atomicAdd(&sh[bin_x<R>(y0, h.bx)], 1u);
+            if (h.bv > 0) {
+                const R lo = (R)h.v_lo, hi = (R)h.v_hi;
+                atomicAdd(&sh[h.bx + bin_v<R>(v0, lo, hi, (R)(h.bv / (h.v_hi - h.v_lo)), h.bv)], 1u);
+            }
+        }
+    }
+    if (snap0) flush_hist(sh, h, 0, set, b.n_sets);
+}
+
+// ---------------------------------------------------------------- integrator
+
+template <typename R, int PPT>
+struct Slots {
+    R y[PPT], yacc[PPT], ylo[PPT], v[PPT], e[PPT];
+    int32_t cell[PPT];
+    StepStream ss[PPT];
+};
+
+// Round keys of the launch's seed as a kernel parameter (constant bank).
+struct KeyParam {
+    RoundKeys K;
+};
+
+// One Euler-Maruyama step of every slot at an arbitrary step index n (the
+// unaligned head / tail of a range): the counter block of n is generated for
+// this step alone.
+template <typename R, int PPT>
+__device__ __forceinline__ void single_step(const Coef<R> &k, const RoundKeys &K, Slots<R, PPT> &S, int64_t n) {
+    const uint32_t j = (uint32_t)(n & 3);
+    const uint32_t m = (uint32_t)(n >> 2);
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+        const uint4 w = step_block(m, S.ss[q], K);
+        if constexpr (sizeof(R) == 4) {
+            float nr, cs, sn;
+            if (j < 2)
+                box_muller_f32(w.x, w.y, nr, cs, sn);
+            else
+                box_muller_f32(w.z, w.w, nr, cs, sn);
+            em_step_f32(k, k.sigma * nr, (j & 1) ? sn : cs, S.y[q], S.yacc[q], S.v[q], S.e[q]);
+        } else {
+            const double z = normal_from_block_f64(w, j);
+            em_step<double>(k, k.sigma * z, S.y[q], S.yacc[q], S.v[q], S.e[q]);
+        }
+    }
+}
+
+// Four steps 4m .. 4m+3 of every slot from one counter block each.
+template <typename R, int PPT>
+__device__ __forceinline__ void group_step(const Coef<R> &k, const RoundKeys &K, Slots<R, PPT> &S, uint32_t m) {
+    uint4 w[PPT];
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) w[q] = step_block(m, S.ss[q], K);
+    if constexpr (sizeof(R) == 4) {
+        float nr[PPT], cs[PPT], sn[PPT];
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) {
+            box_muller_f32(w[q].x, w[q].y, nr[q], cs[q], sn[q]);
+            nr[q] *= k.sigma;
+        }
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) em_step_f32(k, nr[q], cs[q], S.y[q], S.yacc[q], S.v[q], S.e[q]);
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) em_step_f32(k, nr[q], sn[q], S.y[q], S.yacc[q], S.v[q], S.e[q]);
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) {
+            box_muller_f32(w[q].z, w[q].w, nr[q], cs[q], sn[q]);
+            nr[q] *= k.sigma;
+        }
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) em_step_f32(k, nr[q], cs[q], S.y[q], S.yacc[q], S.v[q], S.e[q]);
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) em_step_f32(k, nr[q], sn[q], S.y[q], S.yacc[q], S.v[q], S.e[q]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) {
+            double z0, z1, z2, z3;
+            box_muller_f64(w[q].x, w[q].y, z0, z1);
+            box_muller_f64(w[q].z, w[q].w, z2, z3);
+            em_step<double>(k, k.sigma * z0, S.y[q], S.yacc[q], S.v[q], S.e[q]);
+            em_step<double>(k, k.sigma * z1, S.y[q], S.yacc[q], S.v[q], S.e[q]);
+            em_step<double>(k, k.sigma * z2, S.y[q], S.yacc[q], S.v[q], S.e[q]);
+            em_step<double>(k, k.sigma * z3, S.y[q], S.yacc[q], S.v[q], S.e[q]);
+        }
+    }
+}
+
+// Steps [n, n_end) of every slot.  Folds happen after absolute multiples of
+// kBlockSteps steps; counter blocks are absolute multiples of 4.
+template <typename R, int PPT>
+__device__ __forceinline__ void advance(const Coef<R> &k, const RoundKeys &K, Slots<R, PPT> &S, int64_t n,
+                                        int64_t n_end) {
+    while (n < n_end) {
+        const int64_t blk_end = min(n_end, (n | (int64_t)(kBlockSteps - 1)) + 1);
+        while (n < blk_end && (n & 3)) {
+            single_step<R, PPT>(k, K, S, n);
+            ++n;
+        }
+        if (n < blk_end) {
+            const uint32_t m_end = (uint32_t)(blk_end >> 2);
+            uint32_t m = (uint32_t)(n >> 2);
+#pragma unroll 1
+            for (; m < m_end; ++m) group_step<R, PPT>(k, K, S, m);
+            n = (int64_t)m << 2;
+        }
+        while (n < blk_end) {
+            single_step<R, PPT>(k, K, S, n);
+            ++n;
+        }
+        if ((blk_end & (kBlockSteps - 1)) == 0) {
+#pragma unroll
+            for (int q = 0; q < PPT; ++q) fold_position<R>(S.y[q], S.yacc[q], S.ylo[q], S.cell[q]);
+        }
+    }
+}
+
+template <typename R, int PPT>
+__global__ void ABP_INTEGRATE_BOUNDS integrate_kernel(Batch b, State st, Hist h, Ckpt ck, Noise nz,
+                                                             KeyParam kp, int64_t g0, int64_t g1) {
+    extern __shared__ uint32_t sh[];
+    const int tile = blockIdx.x;
+    const int set = b.tile_set[tile];
+    const int64_t N = b.set_steps[set];
+    const int64_t n_begin = min(g0, N);
+    const int64_t n_end = min(g1, N);
+    if (n_begin >= n_end) return;  // uniform over the block
+
+    const SV<R> s = view<R>(st);
+    const abp_params p = b.params[set];
+    const Coef<R> k = make_coef<R>(p.q, p.c, p.d, p.gamma0, p.F0, p.D, p.h, p.L, p.asym, nz.dt);
+    const int64_t first = b.tile_first[tile];
+    const int count = b.tile_count[tile];
+
+    Slots<R, PPT> S;
+    int64_t idx[PPT];
+    bool act[PPT];
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+        const int li = threadIdx.x + q * kThreads;
+        act[q] = li < count;
+        idx[q] = first + (act[q] ? li : count - 1);
+        S.y[q] = s.y[idx[q]];
+        S.yacc[q] = s.yacc[idx[q]];
+        S.ylo[q] = s.ylo[idx[q]];
+        S.v[q] = s.v[idx[q]];
+        S.e[q] = s.e[idx[q]];
+        S.cell[q] = s.cell[idx[q]];
+        S.ss[q] = step_stream((uint64_t)idx[q] + nz.traj_base, kp.K);
+    }
+
+    const bool hist = h.bx > 0 || h.bv > 0;
+    const int nb = h.bx + (h.bv > 0 ? h.bv + 2 : 0);
+    if (hist) {
+        for (int i = threadIdx.x; i < nb; i += blockDim.x) sh[i] = 0;
+        __syncthreads();
+    }
+    const R v_lo = (R)h.v_lo, v_hi = (R)h.v_hi;
+    const R v_scale = h.bv > 0 ? (R)(h.bv / (h.v_hi - h.v_lo)) : (R)0;
+
+    int64_t n = n_begin;
+    while (n < n_end) {
+        int64_t seg_end = n_end;
+        if (hist && h.snap_every > 0) seg_end = min(seg_end, (n / h.snap_every + 1) * h.snap_every);
+        if (ck.every > 0) seg_end = min(seg_end, (n / ck.every + 1) * ck.every);
+        advance<R, PPT>(k, kp.K, S, n, seg_end);
+        n = seg_end;
+        if (hist && (h.snap_every > 0 ? (n % h.snap_every == 0) : (n == N))) {
+            const int64_t snap = h.snap_every > 0 ? n / h.snap_every - 1 : 0;
+#pragma unroll
+            for (int q = 0; q < PPT; ++q) {
+                if (!act[q]) continue;
+                if (h.bx > 0) atomicAdd(&sh[bin_x<R>(S.y[q] + S.yacc[q], h.bx)], 1u);
+                if (h.bv > 0) atomicAdd(&sh[h.bx + bin_v<R>(S.v[q], v_lo, v_hi, v_scale, h.bv)], 1u);
+            }
+            flush_hist(sh, h, snap, set, b.n_sets);
+        }
+        if (ck.every > 0 && n % ck.every == 0 && sizeof(R) == 4) {
+            const int64_t slot = n / ck.every;
+#pragma unroll
+            for (int q = 0; q < PPT; ++q)
+                if (act[q])
+                    ck.ck[(size_t)slot * b.total_traj + idx[q]] =
+                        make_float4((float)S.y[q], (float)S.yacc[q], (float)S.v[q], (float)S.e[q]);
+        }
+    }
+
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+        if (!act[q]) continue;
+        s.y[idx[q]] = S.y[q];
+        s.yacc[idx[q]] = S.yacc[q];
+        s.ylo[idx[q]] = S.ylo[q];
+        s.v[idx[q]] = S.v[q];
+        s.e[idx[q]] = S.e[q];
+        s.cell[idx[q]] = S.cell[q];
+    }
+}
+
+// ---------------------------------------------------------------- reduction
+
+// Fixed-order sum over the block of four doubles per thread; result valid in
+// thread 0.
+__device__ __forceinline__ void block_sum4(double (&a)[4], double (*red)[4]) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) a[j] += __shfl_down_sync(0xffffffffu, a[j], o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) red[warp][j] = a[j];
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) a[j] = lane < nw ? red[lane][j] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) a[j] += __shfl_down_sync(0xffffffffu, a[j], o);
+    }
+}
+
+// Per tile: sum vbar, sum vbar^2, sum dx, sum dx^2 with dx = x_n - x_0 and
+// vbar = dx / (n dt), n = min(g, N) steps done (the scheme advances x by
+// v_k dt at every step, so dx / (n dt) is the time average of v_0 .. v_{n-1}).
+template <typename R>
+__global__ void __launch_bounds__(kThreads) tile_reduce_kernel(Batch b, State st, double dt, int64_t g,
+                                                               double *partials) {
+    __shared__ double red[kThreads / 32][4];
+    const SV<R> s = view<R>(st);
+    const int tile = blockIdx.x;
+    const int set = b.tile_set[tile];
+    const int64_t n = min(g, b.set_steps[set]);
+    const double L = b.params[set].L;
+    const double inv_T = n > 0 ? 1.0 / ((double)n * dt) : 0.0;
+    const int64_t first = b.tile_first[tile];
+    const int count = b.tile_count[tile];
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int li = threadIdx.x; li < count; li += blockDim.x) {
+        const int64_t t = first + li;
+        const double dx = L * disp_periods<R>(s, t);
+        const double vbar = dx * inv_T;
+        a[0] += vbar;
+        a[1] += vbar * vbar;
+        a[2] += dx;
+        a[3] += dx * dx;
+    }
+    block_sum4(a, red);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) partials[(size_t)tile * 4 + j] = a[j];
+}
+
+// Per set: fixed-order sum of its tiles' partials and the derived moments.
+__global__ void __launch_bounds__(kThreads) set_reduce_kernel(Batch b, double dt, int64_t g, const double *partials,
+                                                              double *moments) {
+    __shared__ double red[kThreads / 32][4];
+    const int set = blockIdx.x;
+    const int t0 = b.set_tile_begin[set], t1 = b.set_tile_begin[set + 1];
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) a[j] += partials[(size_t)t * 4 + j];
+    block_sum4(a, red);
+    if (threadIdx.x == 0) {
+        int64_t M = 0;
+        for (int t = t0; t < t1; ++t) M += b.tile_count[t];
+        const int64_t n = min(g, b.set_steps[set]);
+        double *o = moments + (size_t)set * 8;
+        const double Md = (double)M;
+        const double mean_v = M > 0 ? a[0] / Md : 0.0;
+        const double var_v = M > 1 ? (a[1] - Md * mean_v * mean_v) / (Md - 1.0) : 0.0;
+        const double msd = M > 0 ? a[3] / Md : 0.0;
+        const double mdx = M > 0 ? a[2] / Md : 0.0;
+        const double T = (double)n * dt;
+        o[0] = mean_v;
+        o[1] = M > 0 ? sqrt(fmax(var_v, 0.0) / Md) : 0.0;
+        o[2] = msd;
+        o[3] = T > 0.0 ? (msd - mdx * mdx) / (2.0 * T) : 0.0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) o[4 + j] = a[j];
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads) get_state_kernel(Batch b, State st, double dt, int64_t g, double *x,
+                                                             double *x0, double *v, double *e, double *vbar) {
+    const SV<R> s = view<R>(st);
+    const int tile = blockIdx.x;
+    const int set = b.tile_set[tile];
+    const int64_t n = min(g, b.set_steps[set]);
+    const double L = b.params[set].L;
+    const int64_t first = b.tile_first[tile];
+    const int count = b.tile_count[tile];
+    for (int li = threadIdx.x; li < count; li += blockDim.x) {
+        const int64_t t = first + li;
+        const double x0t = L * (double)s.y0[t];
+        const double dx = L * disp_periods<R>(s, t);
+        if (x) x[t] = x0t + dx;
+        if (x0) x0[t] = x0t;
+        if (v) v[t] = (double)s.v[t];
+        if (e) e[t] = (double)s.e[t];
+        if (vbar) vbar[t] = n > 0 ? dx / ((double)n * dt) : 0.0;
+    }
+}
+
+// ---------------------------------------------------------------- verification
+
+__global__ void philox_kernel(uint32_t k0, uint32_t k1, const uint64_t *traj, const uint64_t *m, int64_t n,
+                              uint32_t *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint4 w = noise_block(m[i], traj[i], k0, k1);
+        out[4 * i + 0] = w.x;
+        out[4 * i + 1] = w.y;
+        out[4 * i + 2] = w.z;
+        out[4 * i + 3] = w.w;
+    }
+}
+
+// The normals of the integrator's own noise path (step_block + box_muller_f32).
+__global__ void normals_kernel(KeyParam kp, uint64_t traj, uint64_t n0, int64_t count, float *out) {
+    const StepStream ss = step_stream(traj, kp.K);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t n = n0 + (uint64_t)i;
+        const uint4 w = step_block((uint32_t)(n >> 2), ss, kp.K);
+        out[i] = normal_from_block_f32(w, (uint32_t)(n & 3));
+    }
+}
+
+size_t hist_smem(const Hist &h) { return sizeof(uint32_t) * (size_t)(h.bx + (h.bv > 0 ? h.bv + 2 : 0)); }
+
+KeyParam key_param(uint32_t k0, uint32_t k1) {
+    KeyParam kp;
+    for (int r = 0; r < 10; ++r) {
+        kp.K.rk[2 * r] = k0 + (uint32_t)r * kPhiloxW0;
+        kp.K.rk[2 * r + 1] = k1 + (uint32_t)r * kPhiloxW1;
+    }
+    return kp;
+}
+
+template <typename R, int PPT>
+cudaError_t launch_integrate_t(const Batch &b, const State &s, const Hist &h, const Ckpt &c, const Noise &nz,
+                               int64_t g0, int64_t g1, cudaStream_t st) {
+    const size_t smem = hist_smem(h);
+    auto kern = integrate_kernel<R, PPT>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    kern<<<b.n_tiles, kThreads, smem, st>>>(b, s, h, c, nz, key_param(nz.k0, nz.k1), g0, g1);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- launchers
+
+cudaError_t launch_init(const Batch &b, const State &s, const Hist &h, const Ckpt &c, const Noise &nz,
+                        cudaStream_t st) {
+    if (b.n_tiles == 0) return cudaSuccess;
+    const size_t smem = hist_smem(h);
+    if (s.fp64) {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(init_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        init_kernel<double><<<b.n_tiles, kThreads, smem, st>>>(b, s, h, c, nz);
+    } else {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(init_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        init_kernel<float><<<b.n_tiles, kThreads, smem, st>>>(b, s, h, c, nz);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_integrate(const Batch &b, const State &s, const Hist &h, const Ckpt &c, const Noise &nz, int ppt,
+                             int64_t g0, int64_t g1, cudaStream_t st) {
+    if (b.n_tiles == 0 || g1 <= g0) return cudaSuccess;
+    if (s.fp64) {
+        switch (ppt) {
+            case 1: return launch_integrate_t<double, 1>(b, s, h, c, nz, g0, g1, st);
+            case 2: return launch_integrate_t<double, 2>(b, s, h, c, nz, g0, g1, st);
+            case 4: return launch_integrate_t<double, 4>(b, s, h, c, nz, g0, g1, st);
+        }
+    } else {
+        switch (ppt) {
+            case 1: return launch_integrate_t<float, 1>(b, s, h, c, nz, g0, g1, st);
+            case 2: return launch_integrate_t<float, 2>(b, s, h, c, nz, g0, g1, st);
+            case 4: return launch_integrate_t<float, 4>(b, s, h, c, nz, g0, g1, st);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t integrate_occupancy(bool fp64, int ppt, size_t smem, int *blocks_per_sm) {
+    const void *f = nullptr;
+    if (fp64) {
+        f = ppt == 1 ? (const void *)integrate_kernel<double, 1>
+                     : ppt == 2 ? (const void *)integrate_kernel<double, 2> : (const void *)integrate_kernel<double, 4>;
+    } else {
+        f = ppt == 1 ? (const void *)integrate_kernel<float, 1>
+                     : ppt == 2 ? (const void *)integrate_kernel<float, 2> : (const void *)integrate_kernel<float, 4>;
+    }
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, kThreads, smem);
+}
+
+cudaError_t launch_reduce(const Batch &b, const State &s, const Noise &nz, int64_t g, double *partials,
+                          double *moments, cudaStream_t st) {
+    if (b.n_sets == 0) return cudaSuccess;
+    if (b.n_tiles > 0) {
+        if (s.fp64)
+            tile_reduce_kernel<double><<<b.n_tiles, kThreads, 0, st>>>(b, s, nz.dt, g, partials);
+        else
+            tile_reduce_kernel<float><<<b.n_tiles, kThreads, 0, st>>>(b, s, nz.dt, g, partials);
+    }
+    set_reduce_kernel<<<b.n_sets, kThreads, 0, st>>>(b, nz.dt, g, partials, moments);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_get_state(const Batch &b, const State &s, double dt, int64_t g, double *x, double *x0, double *v,
+                             double *e, double *vbar, cudaStream_t st) {
+    if (b.n_tiles == 0) return cudaSuccess;
+    if (s.fp64)
+        get_state_kernel<double><<<b.n_tiles, kThreads, 0, st>>>(b, s, dt, g, x, x0, v, e, vbar);
+    else
+        get_state_kernel<float><<<b.n_tiles, kThreads, 0, st>>>(b, s, dt, g, x, x0, v, e, vbar);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_philox(uint32_t k0, uint32_t k1, const uint64_t *traj, const uint64_t *m, int64_t n, uint32_t *out,
+                          cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    philox_kernel<<<blocks, 256, 0, st>>>(k0, k1, traj, m, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_normals(uint32_t k0, uint32_t k1, uint64_t traj, uint64_t n0, int64_t count, float *out,
+                           cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    if (n0 + (uint64_t)count > ((uint64_t)1 << 34)) return cudaErrorInvalidValue;  // step counters below 2^34
+    const int blocks = (int)std::min<int64_t>((count + 255) / 256, 4096);
+    normals_kernel<<<blocks, 256, 0, st>>>(key_param(k0, k1), traj, n0, count, out);
+    return cudaGetLastError();
+}
+
+}  // namespace abp

@@ -1,0 +1,89 @@
+"""Pathwise adjoint (abp_backward) against the oracle's FP64 tangent-linear gradient.
+
+The oracle's tangent-linear is itself pinned to FP64 central differences with common
+random numbers (tests/test_oracle_pins.py).  Bar: the GPU adjoint of the mean velocity
+agrees with it within 1e-3 relative (of the largest gradient component of the set),
+on runs short enough that the FP32 and FP64 trajectories stay together.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1104_2499_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def abp():
+    from paper_1104_2499_gb300 import abp as A
+    from paper_1104_2499_gb300 import build as B
+
+    B.build()
+    A.lib()
+    return A
+
+
+def batch(K=500, v0_mode=1):
+    sets = [W._with(D=0.05), W._with(D=0.2, q=2.0, asym=0.1, gamma0=1.5), W._with(D=0.1, F0=0.3, c=0.3, d=0.7)]
+    return W.Workload(name="adj", sets=sets, n_traj=[256, 100, 300], n_steps=[2000, 1900, 777], dt=1e-3, seed=31,
+                      v0_mode=v0_mode, checkpoint_every=K)
+
+
+def oracle_grads(w):
+    base = w.traj_base()
+    out = []
+    for i, p in enumerate(w.sets):
+        r = O.run_set(p, seed=w.seed, dt=w.dt, n_traj=w.n_traj[i], n_steps=w.n_steps[i], traj_base=base[i],
+                      v0_mode=w.v0_mode, want_grad=True)
+        out.append(r["grad"])
+    return np.array(out)
+
+
+@pytest.mark.parametrize("K,v0_mode", [(500, 1), (64, 0), (333, 1)])
+def test_adjoint_matches_oracle_tangent_linear(abp, K, v0_mode):
+    w = batch(K, v0_mode)
+    with abp.Ensemble(w) as ens:
+        ens.run()
+        g = ens.backward(host=True).numpy()
+    ref = oracle_grads(w)
+    for i in range(w.n_sets):
+        scale = np.max(np.abs(ref[i]))
+        np.testing.assert_allclose(g[i], ref[i], rtol=1e-3, atol=1e-3 * scale, err_msg="set %d" % i)
+
+
+def test_adjoint_weights_and_device_outputs(abp):
+    w = batch()
+    with abp.Ensemble(w) as ens:
+        ens.run()
+        g1 = ens.backward()
+        wt = torch.tensor([2.0, -1.0, 0.5], dtype=torch.float64, device="cuda")
+        g2 = ens.backward(wt)
+        torch.cuda.synchronize()
+    np.testing.assert_allclose(g2.cpu().numpy(), g1.cpu().numpy() * np.array([[2.0], [-1.0], [0.5]]), rtol=1e-12)
+
+
+def test_adjoint_requires_checkpoints_and_completion(abp):
+    w = batch(K=0)
+    with abp.Ensemble(w) as ens:
+        ens.run()
+        with pytest.raises(abp.AbpError) as ei:
+            ens.backward()
+        assert ei.value.status == abp.ABP_ESTATE
+    w = batch(K=100)
+    with abp.Ensemble(w) as ens:
+        ens.set_params()
+        ens.integrate(50)
+        with pytest.raises(abp.AbpError) as ei:
+            ens.backward()
+        assert ei.value.status == abp.ABP_ESTATE
+
+
+def test_autograd_function(abp):
+    w = batch()
+    theta = torch.tensor([[s[k] for k in abp.GRAD_PARAMS] for s in w.sets], dtype=torch.float64, requires_grad=True)
+    mv = abp.MeanVelocity.apply(theta, w)
+    mv.sum().backward()
+    ref = oracle_grads(w)
+    np.testing.assert_allclose(theta.grad.numpy(), ref, rtol=1e-3, atol=1e-3 * np.abs(ref).max())
