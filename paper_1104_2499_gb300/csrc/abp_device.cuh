@@ -135,9 +135,8 @@ __device__ __forceinline__ void box_muller_f64(uint32_t wa, uint32_t wb, double 
 // steps (a small number, so each increment keeps almost all its bits), and
 // at the block end yacc is added to y, whole periods move into cell and the
 // rounding errors of both operations go to ylo, which only the displacement
-// (never the force) reads.  This is the remedy for the precision issue the
-// paper points out for single precision: never add very small numbers to
-// very big ones.
+// (never the force) reads.  This answers the single-precision caveat of the
+// paper's Sec. 2: tiny increments are not added straight onto large values.
 template <typename R>
 struct Coef {
     R A;     // 1 - dt c
