@@ -197,6 +197,37 @@ ABP_API abp_status abp_philox(uint64_t seed, const uint64_t *traj, const uint64_
 ABP_API abp_status abp_normals(uint64_t seed, uint64_t traj, uint64_t n0, int64_t count, float *out,
                        void *cuda_stream);
 
+/* --- allocation-free entry point ------------------------------------------ */
+
+/* The paper has no counterpart to this call; it serves callers that cannot
+ * allocate device memory: code embedded in a host framework that owns all
+ * device memory through its own pool and forbids cudaMalloc / cudaFree (both
+ * also synchronise the device), or a latency-critical loop that must never
+ * stall on an allocation.
+ *
+ * abp_run_set_noalloc integrates ONE parameter set (n_traj trajectories of
+ * n_steps steps, configuration cfg; cfg->traj_base offsets the trajectory ids)
+ * to completion and reduces it, exactly like abp_set_params + abp_integrate +
+ * abp_reduce on a context, but allocates nothing: the trajectory state, tile
+ * table and reduction partials live in one static device array of
+ * ABP_NOALLOC_SCRATCH_BYTES bytes that every GPU which loads the library holds
+ * until the process exits.  Limits: 0 <= n_traj <= ABP_NOALLOC_MAX_TRAJ, FP32
+ * state only (state_fp64 = 0), no checkpoints (checkpoint_every = 0); anything
+ * else returns ABP_EINVAL with a message in err (err_len bytes, may be NULL).
+ * Outputs, all DEVICE memory owned by the caller: moments [8] doubles as in
+ * abp_reduce; hist_x [n_snap][hist_x_bins] and hist_v [n_snap][hist_v_bins + 2]
+ * uint32 (required when their bins are > 0, zeroed by the call).
+ * The call only enqueues work on cuda_stream; results are ready when the stream
+ * is.  The first call on a device looks up the array's device address (with
+ * that device current); make that first call before any stream capture.  All
+ * calls share the one array, so calls whose work overlaps on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller. */
+#define ABP_NOALLOC_MAX_TRAJ 65536
+#define ABP_NOALLOC_SCRATCH_BYTES 1848064
+ABP_API abp_status abp_run_set_noalloc(const abp_params *params, const abp_config *cfg, int64_t n_traj,
+                                       int64_t n_steps, double *moments, uint32_t *hist_x, uint32_t *hist_v,
+                                       void *cuda_stream, char *err, size_t err_len);
+
 /* Library version string. */
 ABP_API const char *abp_version(void);
 

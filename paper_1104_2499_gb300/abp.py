@@ -379,3 +379,22 @@ class MeanVelocity:
 
             cls._fn = _F
         return cls._fn.apply(theta, w, kw)
+
+
+def abp_run_set_noalloc(params: dict, cfg: abp_config, n_traj: int, n_steps: int, moments, hist_x=None, hist_v=None,
+                        stream=None):
+    """One parameter set integrated and reduced by the allocation-free entry point; the
+    outputs are caller-owned device tensors (moments [8] float64, histograms int32)."""
+    L = lib()
+    f = L.abp_run_set_noalloc
+    f.argtypes = [C.POINTER(abp_params), C.POINTER(abp_config), C.c_int64, C.c_int64, _VP, _VP, _VP, _VP,
+                  C.c_char_p, C.c_size_t]
+    f.restype = C.c_int
+    p = abp_params()
+    for k in W.PARAM_NAMES:
+        setattr(p, k, float(params[k]))
+    err = C.create_string_buffer(512)
+    st = f(C.byref(p), C.byref(cfg), int(n_traj), int(n_steps), _ptr(moments), _ptr(hist_x), _ptr(hist_v),
+           _stream_ptr(stream), err, 512)
+    if st != ABP_OK:
+        raise AbpError(st, err.value.decode())

@@ -19,7 +19,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libabp.so")
-SOURCES = ["abp_api.cu", "abp_kernels.cu", "abp_adjoint.cu"]
+SOURCES = ["abp_api.cu", "abp_kernels.cu", "abp_adjoint.cu", "abp_noalloc.cu"]
 HEADERS = ["abp_device.cuh", "abp_internal.cuh", "abp_ctx.cuh"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
