@@ -41,7 +41,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--ppt", type=int, default=0, help="particles per thread (0 = library default)")
-    ap.add_argument("--steps-per-launch", type=int, default=10_000)
+    ap.add_argument("--steps-per-launch", type=int, default=0,
+                    help="steps per work item (0 = autotuned)")
+    ap.add_argument("--schedule", type=int, default=0,
+                    help="0 autotuned, 1 lockstep launches, 2 work queue (persistent launch)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -255,10 +258,8 @@ def main():
     n_sm = props.multi_processor_count
     # weak scaling: every rank integrates its own copy of the sweep with distinct trajectory ids
     ens = A.Ensemble(w, stream=stream, particles_per_thread=args.ppt, steps_per_launch=args.steps_per_launch,
-                     traj_base=rank * w.total_traj)
+                     traj_base=rank * w.total_traj, schedule=args.schedule)
     S = w.n_sets
-    spl = args.steps_per_launch
-    n_launch = math.ceil(w.n_steps[0] / spl)
     mom = torch.empty((S, 8), dtype=torch.float64, device="cuda")
     ns = 1
     hx = torch.empty((ns, S, w.hist_x_bins), dtype=torch.int32, device="cuda")
@@ -266,13 +267,19 @@ def main():
 
     with torch.cuda.stream(stream):
         ens.set_params()
+    tuning = ens.tuning()
+    spl = tuning["steps_per_item"]
+    queue = tuning["schedule"] == 2
+    # work queue: one persistent launch per step; lockstep: one launch per steps_per_launch
+    n_launch = 1 if queue else math.ceil(w.n_steps[0] / spl)
+    chunk = -1 if queue else spl
 
     def gpu_step(ev_k=None):
         ens.reset(w.seed)
         for j in range(n_launch):
             if ev_k is not None:
                 ev_k[j][0].record(stream)
-            ens.integrate(spl)
+            ens.integrate(chunk)
             if ev_k is not None:
                 ev_k[j][1].record(stream)
         A.abp_reduce(ens.ctx, mom, hx, None)
@@ -328,8 +335,10 @@ def main():
     if not args.no_e2e:
         mom_h = torch.empty((S, 8), dtype=torch.float64, pin_memory=True)
         hx_h = torch.empty((ns, S, w.hist_x_bins), dtype=torch.int32, pin_memory=True)
-        n_tiles = sum(math.ceil(m / (256 * max(args.ppt, 1))) for m in w.n_traj)
-        h2d = S * (72 + 8) + 4 * (S + 1) + 16 * n_tiles
+        n_tiles = sum(math.ceil(m / (256 * tuning["particles_per_thread"])) for m in w.n_traj)
+        n_rounds = math.ceil(w.n_steps[0] / spl) if queue else 0
+        # parameters, step counts, tile table and work-queue order, round starts
+        h2d = S * (72 + 8) + 4 * (S + 1) + (16 + 4) * n_tiles + 4 * (n_rounds + 1)
         d2h = mom_h.numel() * 8 + hx_h.numel() * 4
         times = []
         with torch.cuda.stream(stream):
@@ -347,11 +356,12 @@ def main():
     pk, pk_kind = peaks()
     f_max = float(pk.get("sm_max_mhz", 2070.0)) * 1e6
     peak = n_sm * LANES_PER_SM * f_max / 1e12  # T lane-ops/s
-    ps_launch = w.total_traj * spl
+    ps_launch = ps_step // n_launch
     kern_avg = statistics.mean(kern_ms) * 1e-3
     achieved = N_ALG * ps_launch / kern_avg / 1e12
+    kname = ("persistent_kernel<float,%d>" if queue else "integrate_kernel<float,%d>") % tuning["particles_per_thread"]
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T lane-op/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "integrate_kernel<float,PPT>", "n_alg_per_particle_step": N_ALG,
+            "traffic": None, "kernel": kname, "n_alg_per_particle_step": N_ALG,
             "peak_basis": "%d SMs x %d FP32 lanes x %.0f MHz (%s sm_max_mhz)" % (n_sm, LANES_PER_SM, f_max / 1e6,
                                                                                 pk_kind),
             "launch_ms_avg": kern_avg * 1e3, "particle_steps_per_launch": ps_launch,
@@ -370,8 +380,11 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": config_dict(w, args, {"steps_per_launch": spl, "particles_per_thread": args.ppt or 1,
-                                                "launches_per_step": n_launch,
+                "config": config_dict(w, args, {"schedule": "work queue" if queue else "lockstep",
+                                                "steps_per_item": spl,
+                                                "particles_per_thread": tuning["particles_per_thread"],
+                                                "resident_blocks": tuning["blocks"],
+                                                "integrator_launches_per_step": n_launch,
                                                 "parallelism": "dp%d (independent replicas)" % world}),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
                 "wall_s_timed": wall, "sm_count": n_sm, "device": props.name}

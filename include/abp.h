@@ -99,9 +99,15 @@ typedef struct {
                                     0: one snapshot after each set's last step */
     int64_t checkpoint_every;    /* K > 0: keep the state every K steps for abp_backward;
                                     0: no checkpoints (abp_backward returns ABP_ESTATE) */
-    int32_t particles_per_thread;/* 1, 2 or 4 trajectories per CUDA thread; 0 = choose automatically */
-    int32_t reserved;            /* must be 0 */
-    int64_t steps_per_launch;    /* steps per integrator launch; 0 = choose automatically */
+    int32_t particles_per_thread;/* 1, 2 or 4 trajectories per CUDA thread; 0 = autotuned (timed on
+                                    this device once per process) */
+    int32_t schedule;            /* 0: chosen by the autotuner (timed on this device once per
+                                    process); 1: lockstep -- one launch per window of
+                                    steps_per_launch steps over all tiles; 2: work queue -- one
+                                    persistent launch whose blocks pop (tile, round) items, so
+                                    uneven sets balance across SMs */
+    int64_t steps_per_launch;    /* lockstep: steps per launch; work queue: steps per work item
+                                    (round); 0 = chosen automatically */
     uint64_t traj_base;          /* added to every global trajectory id: a process that runs
                                     one shard of a larger ensemble passes the id of its first
                                     trajectory, so every trajectory keeps its own noise */
@@ -171,6 +177,24 @@ ABP_API abp_status abp_get_state(abp_ctx *ctx, double *x, double *x0, double *v,
  * ABP_ESTATE); recomputes each checkpoint interval forward and sweeps it in
  * reverse, accumulating in FP64. */
 ABP_API abp_status abp_backward(abp_ctx *ctx, const double *dJ_dmean_v, double *grad);
+
+/* Upper bound, in nanoseconds, of every device-side wait of the work-queue
+ * schedule (schedule 2) (a work item waiting for the previous round of its tile); 0 restores
+ * the default of 60 s.  An expired wait ends the launch with ABP_ETIMEOUT
+ * (reported by abp_synchronize); the context stays usable after abp_reset. */
+ABP_API abp_status abp_set_wait_limit(abp_ctx *ctx, int64_t wait_limit_ns);
+
+/* Test hook for failure detection: tile `tile` (index in the tile table, -1 to
+ * clear) never publishes the completion of its rounds in later work-queue
+ * launches, so the items that depend on it wait until the wait limit expires.
+ * Nothing faults or hangs: the launch ends and reports ABP_ETIMEOUT. */
+ABP_API abp_status abp_test_hold_tile(abp_ctx *ctx, int32_t tile);
+
+/* The autotuner's choices for the current batch (host outputs, any may be NULL):
+ * schedule (1 lockstep, 2 work queue), particles per thread, steps per launch
+ * (lockstep) or per work item (work queue), resident blocks of the work queue. */
+ABP_API abp_status abp_tuning(const abp_ctx *ctx, int32_t *schedule, int32_t *particles_per_thread,
+                              int64_t *steps_per_item, int32_t *blocks);
 
 /* Number of kernels this context has enqueued since it was created (host output). */
 ABP_API abp_status abp_kernel_launches(const abp_ctx *ctx, int64_t *launches);

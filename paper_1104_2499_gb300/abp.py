@@ -51,7 +51,7 @@ class abp_config(C.Structure):
         ("snapshot_every", C.c_int64),
         ("checkpoint_every", C.c_int64),
         ("particles_per_thread", C.c_int32),
-        ("reserved", C.c_int32),
+        ("schedule", C.c_int32),
         ("steps_per_launch", C.c_int64),
         ("traj_base", C.c_uint64),
     ]
@@ -82,6 +82,13 @@ def lib():
         L.abp_reset.restype = st
         L.abp_kernel_launches.argtypes = [_VP, C.POINTER(C.c_int64)]
         L.abp_kernel_launches.restype = st
+        L.abp_set_wait_limit.argtypes = [_VP, C.c_int64]
+        L.abp_set_wait_limit.restype = st
+        L.abp_test_hold_tile.argtypes = [_VP, C.c_int32]
+        L.abp_test_hold_tile.restype = st
+        L.abp_tuning.argtypes = [_VP, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int64),
+                                 C.POINTER(C.c_int32)]
+        L.abp_tuning.restype = st
         L.abp_integrate.argtypes = [_VP, C.c_int64]
         L.abp_integrate.restype = st
         L.abp_progress.argtypes = [_VP, C.POINTER(C.c_int64)]
@@ -164,6 +171,20 @@ def abp_kernel_launches(ctx) -> int:
     return int(out.value)
 
 
+def abp_set_wait_limit(ctx, wait_limit_ns: int):
+    _check(lib().abp_set_wait_limit(ctx, int(wait_limit_ns)), ctx)
+
+
+def abp_test_hold_tile(ctx, tile: int):
+    _check(lib().abp_test_hold_tile(ctx, int(tile)), ctx)
+
+
+def abp_tuning(ctx):
+    sc, p, s, b = C.c_int32(), C.c_int32(), C.c_int64(), C.c_int32()
+    _check(lib().abp_tuning(ctx, C.byref(sc), C.byref(p), C.byref(s), C.byref(b)), ctx)
+    return {"schedule": sc.value, "particles_per_thread": p.value, "steps_per_item": s.value, "blocks": b.value}
+
+
 def abp_integrate(ctx, max_steps: int = -1):
     _check(lib().abp_integrate(ctx, int(max_steps)), ctx)
 
@@ -220,7 +241,7 @@ def abp_version() -> str:
 # ----------------------------------------------------------------------- convenience
 
 def make_config(w: "W.Workload", *, state_fp64: bool = False, particles_per_thread: int = 0,
-                steps_per_launch: int = 0, traj_base: int = 0) -> abp_config:
+                steps_per_launch: int = 0, traj_base: int = 0, schedule: int = 0) -> abp_config:
     c = abp_config()
     c.seed = int(w.seed)
     c.dt = float(w.dt)
@@ -233,7 +254,7 @@ def make_config(w: "W.Workload", *, state_fp64: bool = False, particles_per_thre
     c.snapshot_every = int(w.snapshot_every)
     c.checkpoint_every = int(w.checkpoint_every)
     c.particles_per_thread = int(particles_per_thread)
-    c.reserved = 0
+    c.schedule = int(schedule)
     c.steps_per_launch = int(steps_per_launch)
     c.traj_base = int(traj_base)
     return c
@@ -246,7 +267,7 @@ class Ensemble:
     """
 
     def __init__(self, w: "W.Workload", *, stream=None, state_fp64=False, particles_per_thread=0,
-                 steps_per_launch=0, traj_base=0, device=None):
+                 steps_per_launch=0, traj_base=0, schedule=0, device=None):
         import torch
 
         self.torch = torch
@@ -255,7 +276,8 @@ class Ensemble:
         self.stream = stream
         with torch.cuda.device(self.device):
             self.ctx = abp_create(make_config(w, state_fp64=state_fp64, particles_per_thread=particles_per_thread,
-                                              steps_per_launch=steps_per_launch, traj_base=traj_base), stream)
+                                              steps_per_launch=steps_per_launch, traj_base=traj_base,
+                                              schedule=schedule), stream)
         self._params_set = False
 
     def close(self):
@@ -284,6 +306,9 @@ class Ensemble:
 
     def launches(self) -> int:
         return abp_kernel_launches(self.ctx)
+
+    def tuning(self) -> dict:
+        return abp_tuning(self.ctx)
 
     def integrate(self, max_steps: int = -1):
         abp_integrate(self.ctx, max_steps)

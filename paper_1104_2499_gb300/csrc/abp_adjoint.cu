@@ -50,11 +50,8 @@ struct NoiseCursor {
         const uint32_t mm = (uint32_t)(n >> 2);
         if (!valid || mm != m) {
             const uint4 w = philox4x32_10(mm, 0u, tlo, thi, nz.k0, nz.k1);
-            float nr;
-            box_muller_f32(w.x, w.y, nr, c01, s01);
-            nrs01 = k.sigma * nr;
-            box_muller_f32(w.z, w.w, nr, c23, s23);
-            nrs23 = k.sigma * nr;
+            box_muller_f32(w.x, w.y, k.bm, nrs01, c01, s01);
+            box_muller_f32(w.z, w.w, k.bm, nrs23, c23, s23);
             m = mm;
             valid = true;
         }

@@ -79,11 +79,14 @@ bool finite_params(const abp_params &p) {
 }
 
 int64_t default_steps_per_launch(const abp_ctx *ctx) {
-    // About 2e10 particle-steps per launch (tens of ms on a GB300), a multiple of 64.
-    if (ctx->total_traj == 0) return std::max<int64_t>(ctx->max_steps, 1);
-    int64_t s = (int64_t)(2.0e10 / (double)ctx->total_traj);
-    s = std::max<int64_t>(64, (s / 64) * 64);
-    return std::max<int64_t>(1, std::min<int64_t>(s, std::max<int64_t>(ctx->max_steps, 1)));
+    // Equal windows of about 2e10 particle-steps each (tens of ms on a GB300),
+    // a multiple of 64 steps.
+    if (ctx->total_traj == 0 || ctx->max_steps == 0) return std::max<int64_t>(ctx->max_steps, 1);
+    const double work = (double)ctx->total_traj * (double)ctx->max_steps;
+    const int64_t n_launch = std::max<int64_t>(1, (int64_t)std::ceil(work / 2.0e10));
+    int64_t s = (ctx->max_steps + n_launch - 1) / n_launch;
+    s = ((s + 63) / 64) * 64;
+    return std::max<int64_t>(1, std::min<int64_t>(s, ctx->max_steps));
 }
 
 // Copy n bytes of a device buffer to a caller pointer that may be host or device.
@@ -96,6 +99,205 @@ abp_status deliver(abp_ctx *ctx, void *dst, const void *src, size_t n, bool *syn
         *synced = true;
     }
     return ABP_OK;
+}
+
+// ---------------------------------------------------------------- autotuner
+
+// Schedule and particles per thread.  Every (schedule, PPT) candidate is timed
+// once per process, device and state type on a synthetic single-set batch that
+// fills the GPU (1,024 trajectories per SM, 2,048 steps after a 256-step
+// warm-up, CUDA events on the context's stream); the fastest candidate allowed
+// by the configuration wins.
+struct TuneTable {
+    bool done = false;
+    float ms[3][3] = {};  // [schedule 1 = lockstep, 2 = work queue][ppt 1, 2, 4]
+};
+TuneTable g_tune[64][2];
+
+void measure_candidates(abp_ctx *ctx, TuneTable &tt) {
+    const int fp = ctx->cfg.state_fp64 ? 1 : 0;
+    const int64_t T = (int64_t)std::max(ctx->sm_count, 1) * 1024;
+    const int64_t warm = 256, steps = 2048;
+    const size_t rsz = fp ? sizeof(double) : sizeof(float);
+    const int cands[3] = {1, 2, 4};
+    const int max_tiles = (int)((T + kThreads - 1) / kThreads);
+    const size_t bytes = 256 * 16 + (sizeof(int64_t) + 5 * sizeof(int32_t)) * max_tiles + (6 * rsz + 4) * T + 8192;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) tt.ms[i][j] = 1e30f;
+    void *mem = nullptr;
+    if (cudaMalloc(&mem, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    char *p = (char *)mem;
+    auto take = [&](size_t n) {
+        char *r = p;
+        p += (n + 255) & ~(size_t)255;
+        return r;
+    };
+    abp_params prm{1.0, 0.1, 1.0, 1.0, 0.0, 0.1, 1.0, 1.0, 0.25};
+    const int64_t nsteps = warm + steps;
+    abp_params *d_prm = (abp_params *)take(sizeof(abp_params));
+    int64_t *d_steps = (int64_t *)take(sizeof(int64_t));
+    int32_t *d_stb = (int32_t *)take(2 * sizeof(int32_t));
+    int64_t *d_first = (int64_t *)take(sizeof(int64_t) * max_tiles);
+    int32_t *d_count = (int32_t *)take(sizeof(int32_t) * max_tiles);
+    int32_t *d_tset = (int32_t *)take(sizeof(int32_t) * max_tiles);
+    State st;
+    st.fp64 = fp != 0;
+    st.y = take(rsz * T);
+    st.yacc = take(rsz * T);
+    st.ylo = take(rsz * T);
+    st.v = take(rsz * T);
+    st.e = take(rsz * T);
+    st.y0 = take(rsz * T);
+    st.cell = (int32_t *)take(sizeof(int32_t) * T);
+    int32_t *d_queue = (int32_t *)take(sizeof(int32_t) * ((size_t)max_tiles + 1));
+    int32_t *d_perm = (int32_t *)take(sizeof(int32_t) * max_tiles);
+    int32_t *d_rs = (int32_t *)take(sizeof(int32_t) * 2);
+    int32_t *d_status = (int32_t *)take(sizeof(int32_t));
+    Hist h{};
+    Ckpt ck{};
+    Noise nz{};
+    nz.dt = 1e-3;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaStream_t s = ctx->stream;
+    for (int ci = 0; ci < 3; ++ci) {
+        const int c = cands[ci];
+        const int64_t tile = (int64_t)kThreads * c;
+        const int nt = (int)((T + tile - 1) / tile);
+        std::vector<int64_t> first(nt);
+        std::vector<int32_t> count(nt), tset(nt, 0), perm(nt);
+        for (int t = 0; t < nt; ++t) {
+            first[t] = t * tile;
+            count[t] = (int32_t)std::min<int64_t>(tile, T - t * tile);
+            perm[t] = t;
+        }
+        const int32_t stb[2] = {0, nt};
+        const int32_t rs[2] = {0, nt};
+        cudaMemcpyAsync(d_prm, &prm, sizeof(prm), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(d_steps, &nsteps, sizeof(nsteps), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(d_stb, stb, sizeof(stb), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(d_first, first.data(), sizeof(int64_t) * nt, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(d_count, count.data(), sizeof(int32_t) * nt, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(d_tset, tset.data(), sizeof(int32_t) * nt, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(d_perm, perm.data(), sizeof(int32_t) * nt, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(d_rs, rs, sizeof(rs), cudaMemcpyHostToDevice, s);
+        cudaMemsetAsync(d_status, 0, sizeof(int32_t), s);
+        Batch b;
+        b.n_sets = 1;
+        b.n_tiles = nt;
+        b.total_traj = T;
+        b.params = d_prm;
+        b.set_steps = d_steps;
+        b.set_tile_begin = d_stb;
+        b.tile_first = d_first;
+        b.tile_count = d_count;
+        b.tile_set = d_tset;
+        int bps = 0;
+        persistent_occupancy(fp != 0, c, 0, &bps);
+        Queue q;
+        q.head = d_queue;
+        q.done = d_queue + 1;
+        q.status = d_status;
+        q.round_start = d_rs;
+        q.perm = d_perm;
+        q.n_rounds = 1;
+        q.n_items = nt;
+        q.hold_tile = -1;
+        q.wait_limit_ns = 10000000000LL;
+        const int grid = std::min(std::max(bps, 1) * std::max(ctx->sm_count, 1), nt);
+        for (int sch = 1; sch <= 2; ++sch) {
+            auto window = [&](int64_t g0, int64_t g1) {
+                if (sch == 1) {
+                    launch_integrate(b, st, h, ck, nz, c, g0, g1, s);
+                } else {
+                    cudaMemsetAsync(d_queue, 0, sizeof(int32_t) * ((size_t)nt + 1), s);
+                    launch_persistent(b, st, h, ck, nz, q, c, grid, g0, g1, g1 - g0, s);
+                }
+            };
+            launch_init(b, st, h, ck, nz, s);
+            window(0, warm);
+            cudaEventRecord(e0, s);
+            window(warm, warm + steps);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            if (cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms > 0.0f) tt.ms[sch][ci] = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamSynchronize(s);
+    cudaFree(mem);
+    cudaGetLastError();
+    tt.done = true;
+}
+
+// Sets ctx->sched and ctx->ppt from the configuration and the timing table.
+void autotune(abp_ctx *ctx) {
+    const int want_sched = ctx->cfg.schedule;          // 0 auto, 1 lockstep, 2 work queue
+    const int want_ppt = ctx->cfg.particles_per_thread;  // 0 auto
+    if (want_sched != 0 && want_ppt != 0) {
+        ctx->sched = want_sched;
+        ctx->ppt = want_ppt;
+        return;
+    }
+    const int dev = ctx->device, fp = ctx->cfg.state_fp64 ? 1 : 0;
+    TuneTable local;
+    TuneTable &tt = (dev >= 0 && dev < 64) ? g_tune[dev][fp] : local;
+    if (!tt.done) measure_candidates(ctx, tt);
+    const int cands[3] = {1, 2, 4};
+    float best = 1e30f;
+    int bs = want_sched ? want_sched : 1, bp = want_ppt ? want_ppt : 1;
+    for (int sch = 1; sch <= 2; ++sch) {
+        if (want_sched && sch != want_sched) continue;
+        for (int ci = 0; ci < 3; ++ci) {
+            if (want_ppt && cands[ci] != want_ppt) continue;
+            if (tt.ms[sch][ci] < best) {
+                best = tt.ms[sch][ci];
+                bs = sch;
+                bp = cands[ci];
+            }
+        }
+    }
+    ctx->sched = bs;
+    ctx->ppt = bp;
+}
+
+// Steps per work item of the work-queue schedule: the largest of 10^5, 10^4,
+// 10^3 that still gives at least 32 items per resident block (so the last
+// items leave under ~2% of the launch idle), else 10^3.
+int64_t choose_round_steps(const abp_ctx *ctx) {
+    const int64_t cands[3] = {100000, 10000, 1000};
+    const int64_t cap = std::max(ctx->grid, 1);
+    for (int64_t S : cands) {
+        int64_t items = 0;
+        for (int32_t t = 0; t < ctx->n_tiles; ++t)
+            items += (ctx->n_steps[ctx->tile_set[t]] + S - 1) / S;
+        if (items >= 32 * cap) return S;
+    }
+    return 1000;
+}
+
+// Round starts of the window [g0, g1): round j holds the tiles whose sets still
+// have steps past g0 + j seg; since perm orders tiles by decreasing step count,
+// those tiles are a prefix of perm.
+std::vector<int32_t> round_starts(const abp_ctx *ctx, int64_t g0, int64_t g1, int64_t seg) {
+    const int64_t n_rounds = (g1 - g0 + seg - 1) / seg;
+    std::vector<int32_t> rs((size_t)n_rounds + 1, 0);
+    int64_t cnt = ctx->n_tiles;  // tiles with n_steps > g0 + j seg
+    int64_t acc = 0;
+    for (int64_t j = 0; j < n_rounds; ++j) {
+        const int64_t thr = g0 + j * seg;
+        while (cnt > 0 && ctx->perm_steps[cnt - 1] <= thr) --cnt;
+        rs[j] = (int32_t)acc;
+        acc += cnt;
+    }
+    rs[n_rounds] = (int32_t)acc;
+    return rs;
 }
 
 }  // namespace
@@ -125,7 +327,7 @@ abp_status abp_create(abp_ctx **out, const abp_config *cfg, void *cuda_stream) {
     if (cfg->particles_per_thread != 0 && cfg->particles_per_thread != 1 && cfg->particles_per_thread != 2 &&
         cfg->particles_per_thread != 4)
         return ABP_EINVAL;
-    if (cfg->reserved != 0) return ABP_EINVAL;
+    if (cfg->schedule < 0 || cfg->schedule > 2) return ABP_EINVAL;
     if (cfg->checkpoint_every > 0 && cfg->state_fp64) return ABP_EINVAL;  // adjoint runs on the FP32 path
     abp_ctx *ctx = new (std::nothrow) abp_ctx();
     if (!ctx) return ABP_ENOMEM;
@@ -146,7 +348,7 @@ abp_status abp_create(abp_ctx **out, const abp_config *cfg, void *cuda_stream) {
         delete ctx;
         return e == cudaErrorMemoryAllocation ? ABP_ENOMEM : ABP_ECUDA;
     }
-    ctx->ppt = cfg->particles_per_thread ? cfg->particles_per_thread : 1;
+    ctx->ppt = cfg->particles_per_thread;  // 0: autotuned by abp_set_params
     *out = ctx;
     return ABP_OK;
 }
@@ -190,6 +392,7 @@ abp_status abp_set_params(abp_ctx *ctx, int32_t n_sets, const abp_params *sets, 
     ctx->g = 0;
 
     // Tiles: contiguous runs of at most kThreads * ppt trajectories of one set.
+    autotune(ctx);
     const int64_t tile = (int64_t)kThreads * ctx->ppt;
     ctx->set_tile_begin.assign(1, 0);
     ctx->tile_first.clear();
@@ -211,7 +414,26 @@ abp_status abp_set_params(abp_ctx *ctx, int32_t n_sets, const abp_params *sets, 
     const bool any_hist = c.hist_x_bins > 0 || c.hist_v_bins > 0;
     ctx->n_snap = any_hist ? (c.snapshot_every > 0 ? max_n / c.snapshot_every : 1) : 0;
     ctx->n_ckpt = c.checkpoint_every > 0 ? max_n / c.checkpoint_every + 1 : 0;
-    ctx->steps_per_launch = c.steps_per_launch > 0 ? c.steps_per_launch : default_steps_per_launch(ctx);
+    // Work-queue order: tiles by decreasing step count of their set (stable).
+    ctx->perm.resize(ctx->n_tiles);
+    for (int32_t t = 0; t < ctx->n_tiles; ++t) ctx->perm[t] = t;
+    std::stable_sort(ctx->perm.begin(), ctx->perm.end(), [&](int32_t a, int32_t b) {
+        return ctx->n_steps[ctx->tile_set[a]] > ctx->n_steps[ctx->tile_set[b]];
+    });
+    ctx->perm_steps.resize(ctx->n_tiles);
+    for (int32_t k = 0; k < ctx->n_tiles; ++k) ctx->perm_steps[k] = ctx->n_steps[ctx->tile_set[ctx->perm[k]]];
+    {
+        int bps = 0;
+        const size_t smem = sizeof(uint32_t) * (size_t)(std::max(c.hist_x_bins, 0) +
+                                                        (c.hist_v_bins > 0 ? c.hist_v_bins + 2 : 0));
+        cudaError_t oe = persistent_occupancy(c.state_fp64 != 0, ctx->ppt, smem, &bps);
+        if (oe != cudaSuccess) return cuda_fail(ctx, oe, "occupancy query");
+        ctx->grid = std::max(bps, 1) * std::max(ctx->sm_count, 1);
+    }
+    if (c.steps_per_launch > 0)
+        ctx->steps_per_launch = c.steps_per_launch;
+    else
+        ctx->steps_per_launch = ctx->sched == 1 ? default_steps_per_launch(ctx) : choose_round_steps(ctx);
 
     const size_t T = (size_t)total;
     const size_t rsz = c.state_fp64 ? sizeof(double) : sizeof(float);
@@ -237,6 +459,8 @@ abp_status abp_set_params(abp_ctx *ctx, int32_t n_sets, const abp_params *sets, 
     ALLOC(d_ckpt, sizeof(float4) * (size_t)ctx->n_ckpt * T, "checkpoints");
     ALLOC(d_partials, sizeof(double) * 4 * (size_t)std::max(ctx->n_tiles, 1), "reduction scratch");
     ALLOC(d_moments, sizeof(double) * 8 * (size_t)std::max(n_sets, 1), "moments");
+    ALLOC(d_queue, sizeof(int32_t) * ((size_t)ctx->n_tiles + 1), "work queue");
+    ALLOC(d_perm, sizeof(int32_t) * (size_t)std::max(ctx->n_tiles, 1), "work queue order");
 #undef ALLOC
 
     cudaStream_t s = ctx->stream;
@@ -249,6 +473,8 @@ abp_status abp_set_params(abp_ctx *ctx, int32_t n_sets, const abp_params *sets, 
     if (e == cudaSuccess) e = up(ctx->d_tile_first, ctx->tile_first.data(), sizeof(int64_t) * ctx->n_tiles);
     if (e == cudaSuccess) e = up(ctx->d_tile_count, ctx->tile_count.data(), sizeof(int32_t) * ctx->n_tiles);
     if (e == cudaSuccess) e = up(ctx->d_tile_set, ctx->tile_set.data(), sizeof(int32_t) * ctx->n_tiles);
+    if (e == cudaSuccess) e = up(ctx->d_perm, ctx->perm.data(), sizeof(int32_t) * ctx->n_tiles);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_status.p, 0, sizeof(int32_t), s);
     if (e == cudaSuccess && ctx->d_hx.bytes) e = cudaMemsetAsync(ctx->d_hx.p, 0, ctx->d_hx.bytes, s);
     if (e == cudaSuccess && ctx->d_hv.bytes) e = cudaMemsetAsync(ctx->d_hv.p, 0, ctx->d_hv.bytes, s);
     if (e == cudaSuccess) {
@@ -272,8 +498,8 @@ abp_status abp_reset(abp_ctx *ctx, uint64_t seed) {
     ctx->cfg.seed = seed;
     ctx->g = 0;
     cudaStream_t s = ctx->stream;
-    cudaError_t e = cudaSuccess;
-    if (ctx->d_hx.bytes) e = cudaMemsetAsync(ctx->d_hx.p, 0, ctx->d_hx.bytes, s);
+    cudaError_t e = cudaMemsetAsync(ctx->d_status.p, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess && ctx->d_hx.bytes) e = cudaMemsetAsync(ctx->d_hx.p, 0, ctx->d_hx.bytes, s);
     if (e == cudaSuccess && ctx->d_hv.bytes) e = cudaMemsetAsync(ctx->d_hv.p, 0, ctx->d_hv.bytes, s);
     if (e == cudaSuccess) {
         e = launch_init(ctx->batch(), ctx->state(), ctx->hist(), ctx->ckpt(), ctx->noise(), s);
@@ -288,22 +514,163 @@ abp_status abp_kernel_launches(const abp_ctx *ctx, int64_t *launches) {
     return ABP_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+Queue make_queue(abp_ctx *ctx, const int32_t *round_start, int32_t n_rounds, int32_t n_items) {
+    Queue q;
+    q.head = (int32_t *)ctx->d_queue.p;
+    q.done = (int32_t *)ctx->d_queue.p + 1;
+    q.status = (int32_t *)ctx->d_status.p;
+    q.round_start = round_start;
+    q.perm = (const int32_t *)ctx->d_perm.p;
+    q.n_rounds = n_rounds;
+    q.n_items = n_items;
+    q.hold_tile = ctx->hold_tile;
+    q.wait_limit_ns = ctx->wait_limit_ns;
+    return q;
+}
+
+// Enqueue the window [g0, g1) on the context's stream: lockstep launches of at
+// most steps_per_launch steps each, or one work-queue launch whose round starts
+// are read from `round_start`.  Returns the number of kernels enqueued.
+cudaError_t enqueue_window(abp_ctx *ctx, int64_t g0, int64_t g1, const int32_t *round_start, int32_t n_rounds,
+                           int32_t n_items, int64_t *kernels) {
+    cudaStream_t s = ctx->stream;
+    const Batch b = ctx->batch();
+    const State st = ctx->state();
+    const Hist h = ctx->hist();
+    const Ckpt c = ctx->ckpt();
+    const Noise nz = ctx->noise();
+    *kernels = 0;
+    if (ctx->sched == 1) {
+        for (int64_t g = g0; g < g1; g += ctx->steps_per_launch) {
+            cudaError_t e = launch_integrate(b, st, h, c, nz, ctx->ppt, g, std::min(g1, g + ctx->steps_per_launch), s);
+            if (e != cudaSuccess) return e;
+            *kernels += b.n_tiles > 0 ? 1 : 0;
+        }
+        return cudaSuccess;
+    }
+    if (n_items == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(ctx->d_queue.p, 0, sizeof(int32_t) * ((size_t)ctx->n_tiles + 1), s);
+    if (e != cudaSuccess) return e;
+    const Queue q = make_queue(ctx, round_start, n_rounds, n_items);
+    const int grid = (int)std::min<int64_t>(ctx->grid, n_items);
+    e = launch_persistent(b, st, h, c, nz, q, ctx->ppt, grid, g0, g1, ctx->steps_per_launch, s);
+    *kernels = 1;
+    return e;
+}
+
+// Run the window [g0, g1).  A window met for the second time (same schedule,
+// step range, seed and test settings) is captured into a CUDA graph, which is
+// replayed from then on; work-queue graphs keep their round starts in a buffer
+// of their own.
+abp_status run_window(abp_ctx *ctx, int64_t g0, int64_t g1) {
+    cudaStream_t s = ctx->stream;
+    const int64_t seg = ctx->steps_per_launch;
+    const uint64_t traj_base = ctx->cfg.traj_base, seed = ctx->cfg.seed;
+    for (abp_ctx::GraphEntry &ge : ctx->graphs)
+        if (ge.sched == ctx->sched && ge.g0 == g0 && ge.g1 == g1 && ge.seg == seg && ge.seed == seed &&
+            ge.traj_base == traj_base && ge.hold == ctx->hold_tile && ge.wait_limit_ns == ctx->wait_limit_ns) {
+            cudaError_t e = cudaGraphLaunch(ge.exec, s);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "graph replay");
+            ctx->launches += ge.kernels;
+            return ABP_OK;
+        }
+    std::vector<int32_t> rs;
+    int32_t n_rounds = 0;
+    int64_t n_items = 0;
+    if (ctx->sched == 2) {
+        rs = round_starts(ctx, g0, g1, seg);
+        n_rounds = (int32_t)rs.size() - 1;
+        n_items = rs.back();
+        if (n_items == 0) return ABP_OK;
+        if (n_items > INT32_MAX / 2) return fail(ctx, ABP_EINVAL, "too many work items; raise steps_per_launch");
+    }
+    const bool seen = std::find(ctx->windows_seen.begin(), ctx->windows_seen.end(), std::make_pair(g0, g1)) !=
+                      ctx->windows_seen.end();
+    if (!seen) ctx->windows_seen.emplace_back(g0, g1);
+    if (s != nullptr && seen && ctx->graphs.size() < 8) {
+        abp_ctx::GraphEntry ge{ctx->sched, 0, g0, g1, seg, seed, traj_base, ctx->hold_tile, ctx->wait_limit_ns,
+                               (int32_t)n_items, nullptr, nullptr};
+        cudaError_t e = cudaSuccess;
+        if (ctx->sched == 2) {
+            e = cudaMalloc(&ge.round_start, sizeof(int32_t) * rs.size());
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(ge.round_start, rs.data(), sizeof(int32_t) * rs.size(), cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        }
+        cudaGraph_t graph = nullptr;
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            const cudaError_t le = enqueue_window(ctx, g0, g1, (const int32_t *)ge.round_start, n_rounds,
+                                                  (int32_t)n_items, &ge.kernels);
+            e = cudaStreamEndCapture(s, &graph);
+            if (le != cudaSuccess) e = le;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&ge.exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e == cudaSuccess) {
+            ctx->graphs.push_back(ge);
+            e = cudaGraphLaunch(ge.exec, s);
+            ctx->launches += ge.kernels;
+            return e == cudaSuccess ? ABP_OK : cuda_fail(ctx, e, "graph launch");
+        }
+        // capture failed: fall back to direct launches
+        cudaGetLastError();
+        if (ge.round_start) cudaFree(ge.round_start);
+    }
+    const int32_t *d_rs = nullptr;
+    if (ctx->sched == 2) {
+        abp_status stt = alloc(ctx, ctx->d_round, sizeof(int32_t) * rs.size(), "work-queue rounds");
+        if (stt != ABP_OK) return stt;
+        cudaError_t e =
+            cudaMemcpyAsync(ctx->d_round.p, rs.data(), sizeof(int32_t) * rs.size(), cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "work-queue rounds upload");
+        d_rs = (const int32_t *)ctx->d_round.p;
+    }
+    int64_t k = 0;
+    const cudaError_t e = enqueue_window(ctx, g0, g1, d_rs, n_rounds, (int32_t)n_items, &k);
+    ctx->launches += k;
+    return e == cudaSuccess ? ABP_OK : cuda_fail(ctx, e, "integrator launch");
+}
+
+}  // namespace
+
+extern "C" {
+
 abp_status abp_integrate(abp_ctx *ctx, int64_t max_steps) {
     if (!ctx) return ABP_EINVAL;
     if (!ctx->have_batch) return fail(ctx, ABP_ESTATE, "abp_integrate before abp_set_params");
     const int64_t target = max_steps < 0 ? ctx->max_steps : std::min(ctx->max_steps, ctx->g + max_steps);
-    const Batch b = ctx->batch();
-    const State s = ctx->state();
-    const Hist h = ctx->hist();
-    const Ckpt c = ctx->ckpt();
-    const Noise nz = ctx->noise();
-    while (ctx->g < target) {
-        const int64_t g1 = std::min(target, ctx->g + ctx->steps_per_launch);
-        cudaError_t e = launch_integrate(b, s, h, c, nz, ctx->ppt, ctx->g, g1, ctx->stream);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "integrator launch");
-        ctx->launches += b.n_tiles > 0 ? 1 : 0;
-        ctx->g = g1;
-    }
+    if (target <= ctx->g) return ABP_OK;
+    const abp_status st = run_window(ctx, ctx->g, target);
+    if (st != ABP_OK) return st;
+    ctx->g = target;
+    return ABP_OK;
+}
+
+abp_status abp_set_wait_limit(abp_ctx *ctx, int64_t wait_limit_ns) {
+    if (!ctx || wait_limit_ns < 0) return ABP_EINVAL;
+    ctx->wait_limit_ns = wait_limit_ns > 0 ? wait_limit_ns : 60000000000LL;
+    return ABP_OK;
+}
+
+abp_status abp_test_hold_tile(abp_ctx *ctx, int32_t tile) {
+    if (!ctx) return ABP_EINVAL;
+    if (tile < -1 || (ctx->have_batch && tile >= ctx->n_tiles)) return fail(ctx, ABP_EINVAL, "tile out of range");
+    ctx->hold_tile = tile;
+    return ABP_OK;
+}
+
+abp_status abp_tuning(const abp_ctx *ctx, int32_t *schedule, int32_t *particles_per_thread, int64_t *steps_per_item,
+                      int32_t *blocks) {
+    if (!ctx) return ABP_EINVAL;
+    if (schedule) *schedule = ctx->sched;
+    if (particles_per_thread) *particles_per_thread = ctx->ppt;
+    if (steps_per_item) *steps_per_item = ctx->steps_per_launch;
+    if (blocks) *blocks = ctx->grid;
     return ABP_OK;
 }
 

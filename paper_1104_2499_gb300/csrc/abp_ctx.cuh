@@ -5,6 +5,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_runtime.h>
+
 #include "abp.h"
 #include "abp_internal.cuh"
 
@@ -49,7 +51,27 @@ struct abp_ctx {
     int64_t max_steps = 0;
     int64_t g = 0;  // global steps issued: set s has done min(g, n_steps[s])
     int ppt = 1;
-    int64_t steps_per_launch = 0;
+    int sched = 1;                 // 1: lockstep launches, 2: work queue (autotuned when cfg.schedule = 0)
+    int64_t steps_per_launch = 0;  // lockstep: steps per launch; work queue: steps per round
+    int grid = 0;                  // work queue: resident blocks of the persistent launch
+    int32_t hold_tile = -1;        // test hook (abp_test_hold_tile)
+    int64_t wait_limit_ns = 60000000000LL;
+    std::vector<int32_t> perm;     // tiles by decreasing step count
+    std::vector<int64_t> perm_steps;
+    // CUDA graphs of repeated work-queue windows
+    struct GraphEntry {
+        int sched;
+        int64_t kernels;  // kernels per replay
+        int64_t g0, g1, seg;
+        uint64_t seed, traj_base;
+        int32_t hold;
+        int64_t wait_limit_ns;
+        int32_t n_items;
+        void *round_start;  // device copy owned by the entry
+        cudaGraphExec_t exec;
+    };
+    std::vector<GraphEntry> graphs;
+    std::vector<std::pair<int64_t, int64_t>> windows_seen;
     int64_t n_snap = 0;
     int64_t n_ckpt = 0;
     int64_t launches = 0;  // kernels enqueued by this context
@@ -62,6 +84,7 @@ struct abp_ctx {
     DevBuf d_params, d_steps, d_set_tile_begin, d_tile_first, d_tile_count, d_tile_set;
     DevBuf d_y, d_yacc, d_ylo, d_v, d_e, d_y0, d_cell;
     DevBuf d_hx, d_hv, d_ckpt, d_partials, d_moments, d_status;
+    DevBuf d_queue, d_round, d_perm;  // work queue: head + done[n_tiles]; round starts; tile order
     DevBuf d_adj;  // adjoint scratch
 
     Batch batch() const {
@@ -117,13 +140,23 @@ struct abp_ctx {
         n.traj_base = cfg.traj_base;
         return n;
     }
+    void drop_graphs() {
+        for (GraphEntry &g : graphs) {
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+            if (g.round_start) cudaFree(g.round_start);
+        }
+        graphs.clear();
+        windows_seen.clear();
+    }
     void release_batch() {
         // Buffers are kept (and reused by the next batch when large enough);
         // see release_all() for freeing them.
+        drop_graphs();
         have_batch = false;
     }
     void release_all() {
-        for (DevBuf *b : {&d_params, &d_steps, &d_set_tile_begin, &d_tile_first, &d_tile_count, &d_tile_set, &d_y,
+        drop_graphs();
+        for (DevBuf *b : {&d_queue, &d_round, &d_perm, &d_params, &d_steps, &d_set_tile_begin, &d_tile_first, &d_tile_count, &d_tile_set, &d_y,
                           &d_yacc, &d_ylo, &d_v, &d_e, &d_y0, &d_cell, &d_hx, &d_hv, &d_ckpt, &d_partials,
                           &d_moments, &d_adj})
             b->release();

@@ -71,13 +71,27 @@ __device__ __forceinline__ StepStream step_stream(uint64_t t, const RoundKeys &K
     return s;
 }
 
+#ifndef ABP_KEYS_IN_KERNEL
+#define ABP_KEYS_IN_KERNEL 0
+#endif
+
 __device__ __forceinline__ uint4 step_block(uint32_t m, const StepStream &s, const RoundKeys &K) {
     // round 0 with the trajectory half precomputed
     uint32_t c0 = s.pre0, c1 = s.pre1;
     uint32_t c2 = __umulhi(kPhiloxM0, m) ^ s.c3x;
     uint32_t c3 = kPhiloxM0 * m;
+#if ABP_KEYS_IN_KERNEL
+    uint32_t k0 = K.rk[0], k1 = K.rk[1];
+#pragma unroll
+    for (int r = 1; r < 10; ++r) {
+        k0 += kPhiloxW0;
+        k1 += kPhiloxW1;
+        philox_round(c0, c1, c2, c3, k0, k1);
+    }
+#else
 #pragma unroll
     for (int r = 1; r < 10; ++r) philox_round(c0, c1, c2, c3, K.rk[2 * r], K.rk[2 * r + 1]);
+#endif
     return make_uint4(c0, c1, c2, c3);
 }
 
@@ -93,23 +107,36 @@ __device__ __forceinline__ float sqrt_approx(float x) {
     return r;
 }
 
+#ifndef ABP_ANGLE_FFMA
+#define ABP_ANGLE_FFMA 1
+#endif
+
 constexpr double kPi = 3.14159265358979323846;
 constexpr float kTwoPiF = 6.28318530717958647692f;
 constexpr float kLn2F = 0.69314718055994530942f;
 
 // Box-Muller of one word pair, FP32.  u1 = (wa + 1/2) 2^-32 (I2F rounds to
 // nearest, the fused multiply-add adds the half exactly), u2 = floor(wb/2^9)
-// 2^-23 built from the top 23 bits.  The angle is taken as 2 pi (u2 - 1/2) in
-// [-pi, pi) so that the hardware sin/cos see a small argument; that flips both
-// signs, which is folded into the returned radius:
-//   z_even = nr * cs,  z_odd = nr * sn,  nr = -sqrt(-2 ln u1).
-__device__ __forceinline__ void box_muller_f32(uint32_t wa, uint32_t wb, float &nr, float &cs, float &sn) {
+// 2^-23 built from the top 23 bits as f = 1 + u2 in [1, 2).  The angle is
+// taken as 2 pi (u2 - 1/2) = 2 pi f - 3 pi in [-pi, pi), so the hardware
+// sin/cos see a small argument; that flips both signs, which is folded into
+// the returned (scaled) radius.  With c2 = -2 ln(2) s^2 for a scale s >= 0:
+//   s z_even = nrs * cs,  s z_odd = nrs * sn,  nrs = -s sqrt(-2 ln u1).
+__device__ __forceinline__ void box_muller_f32(uint32_t wa, uint32_t wb, float c2, float &nrs, float &cs,
+                                               float &sn) {
     const float u1 = fmaf(__uint2float_rn(wa), 0x1p-32f, 0x1p-33f);
-    const float l2 = __log2f(u1);                       // <= 0
-    nr = -sqrt_approx(fabsf(l2 * (-2.0f * kLn2F)));
-    const float u2h = __uint_as_float(0x3f800000u | (wb >> 9)) - 1.5f;  // u2 - 1/2, exact
-    __sincosf(u2h * kTwoPiF, &sn, &cs);
+    const float l2 = __log2f(u1);  // <= 0
+    nrs = -sqrt_approx(fabsf(l2 * c2));
+    const float f = __uint_as_float(0x3f800000u | (wb >> 9));
+#if ABP_ANGLE_FFMA
+    __sincosf(fmaf(f, kTwoPiF, -1.5f * kTwoPiF), &sn, &cs);
+#else
+    __sincosf((f - 1.5f) * kTwoPiF, &sn, &cs);
+#endif
 }
+
+// c2 of box_muller_f32 for the unscaled normal (s = 1).
+constexpr float kBoxMullerUnit = -2.0f * kLn2F;
 
 // Same mapping in FP64 (precision-reference variant).
 __device__ __forceinline__ void box_muller_f64(uint32_t wa, uint32_t wb, double &z_even, double &z_odd) {
@@ -144,6 +171,7 @@ struct Coef {
     R Cq;    // dt q
     R G;     // 1 - dt gamma0
     R sigma; // sqrt(2 D dt)
+    R bm;    // -2 ln(2) sigma^2: Box-Muller constant of the scaled radius
     R F;     // dt F0 - 2 a K
     R K;     // dt h 0.453 2 pi / L
     R A4;    // 4 a K
@@ -165,6 +193,7 @@ __device__ __forceinline__ Coef<R> make_coef(double q, double c, double d, doubl
     k.Cq = (R)(dt * q);
     k.G = (R)(1.0 - dt * gamma0);
     k.sigma = (R)sqrt(2.0 * D * dt);
+    k.bm = (R)(-2.0 * 0.69314718055994530942 * 2.0 * D * dt);
     k.F = (R)(dt * F0 - 2.0 * a * K);
     k.K = (R)K;
     k.A4 = (R)(4.0 * a * K);
@@ -244,9 +273,9 @@ __device__ __forceinline__ void fold_position(R &y, R &yacc, R &ylo, int32_t &ce
 __device__ __forceinline__ float normal_from_block_f32(uint4 w, uint32_t k) {
     float nr, cs, sn;
     if (k < 2)
-        box_muller_f32(w.x, w.y, nr, cs, sn);
+        box_muller_f32(w.x, w.y, kBoxMullerUnit, nr, cs, sn);
     else
-        box_muller_f32(w.z, w.w, nr, cs, sn);
+        box_muller_f32(w.z, w.w, kBoxMullerUnit, nr, cs, sn);
     return (k & 1) ? nr * sn : nr * cs;
 }
 

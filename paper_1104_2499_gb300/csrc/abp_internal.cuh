@@ -73,6 +73,19 @@ struct Noise {
     uint32_t rk[20];     // round keys: rk[2r], rk[2r+1] = (k0 + r W0, k1 + r W1)
 };
 
+// Work queue of the persistent integrator (device buffers owned by the context).
+struct Queue {
+    int32_t *head;              // next item to pop
+    int32_t *done;              // [n_tiles] rounds of the window each tile has published
+    int32_t *status;            // 0 ok; 1 a dependency wait exceeded wait_limit_ns
+    const int32_t *round_start; // [n_rounds + 1] first item of each round
+    const int32_t *perm;        // [n_tiles] tiles by decreasing step count (stable)
+    int32_t n_rounds;
+    int32_t n_items;
+    int32_t hold_tile;          // test hook: this tile never publishes its rounds (-1: none)
+    int64_t wait_limit_ns;
+};
+
 cudaError_t launch_init(const Batch &b, const State &s, const Hist &h, const Ckpt &c, const Noise &nz,
                         cudaStream_t st);
 cudaError_t launch_integrate(const Batch &b, const State &s, const Hist &h, const Ckpt &c, const Noise &nz,
@@ -87,7 +100,10 @@ cudaError_t launch_philox(uint32_t k0, uint32_t k1, const uint64_t *traj, const 
 cudaError_t launch_normals(uint32_t k0, uint32_t k1, uint64_t traj, uint64_t n0, int64_t count, float *out,
                            cudaStream_t st);
 
-// Integrator kernel attributes for the launch-shape choice.
-cudaError_t integrate_occupancy(bool fp64, int ppt, size_t smem, int *blocks_per_sm);
+cudaError_t launch_persistent(const Batch &b, const State &s, const Hist &h, const Ckpt &c, const Noise &nz,
+                              const Queue &q, int ppt, int grid, int64_t g0, int64_t g1, int64_t seg,
+                              cudaStream_t st);
+// Resident blocks per SM of the persistent integrator (sets its shared-memory limit too).
+cudaError_t persistent_occupancy(bool fp64, int ppt, size_t smem, int *blocks_per_sm);
 
 }  // namespace abp

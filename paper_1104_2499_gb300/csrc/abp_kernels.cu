@@ -20,6 +20,10 @@
 
 // Minimum resident blocks per SM requested from the compiler for the
 // integrator (bounds its register use); 0 leaves the choice to the compiler.
+// Counter blocks (4 steps each) per iteration of the integrator's inner loop.
+#ifndef ABP_GROUP_UNROLL
+#define ABP_GROUP_UNROLL 2
+#endif
 #ifndef ABP_MIN_BLOCKS
 #define ABP_MIN_BLOCKS 0
 #endif
@@ -32,6 +36,8 @@
 namespace abp {
 
 namespace {
+
+constexpr int kGroupUnroll = ABP_GROUP_UNROLL;
 
 template <typename R>
 struct SV {
@@ -112,7 +118,7 @@ __global__ void __launch_bounds__(kThreads) init_kernel(Batch b, State st, Hist 
         if (nz.v0_mode == 1) {
             if constexpr (sizeof(R) == 4) {
                 float nr, cs, sn;
-                box_muller_f32(w.y, w.z, nr, cs, sn);
+                box_muller_f32(w.y, w.z, kBoxMullerUnit, nr, cs, sn);
                 v0 = (float)sqrt(p.D) * (nr * cs);
             } else {
                 double ze, zo;
@@ -164,12 +170,12 @@ __device__ __forceinline__ void single_step(const Coef<R> &k, const RoundKeys &K
     for (int q = 0; q < PPT; ++q) {
         const uint4 w = step_block(m, S.ss[q], K);
         if constexpr (sizeof(R) == 4) {
-            float nr, cs, sn;
+            float nrs, cs, sn;
             if (j < 2)
-                box_muller_f32(w.x, w.y, nr, cs, sn);
+                box_muller_f32(w.x, w.y, k.bm, nrs, cs, sn);
             else
-                box_muller_f32(w.z, w.w, nr, cs, sn);
-            em_step_f32(k, k.sigma * nr, (j & 1) ? sn : cs, S.y[q], S.yacc[q], S.v[q], S.e[q]);
+                box_muller_f32(w.z, w.w, k.bm, nrs, cs, sn);
+            em_step_f32(k, nrs, (j & 1) ? sn : cs, S.y[q], S.yacc[q], S.v[q], S.e[q]);
         } else {
             const double z = normal_from_block_f64(w, j);
             em_step<double>(k, k.sigma * z, S.y[q], S.yacc[q], S.v[q], S.e[q]);
@@ -186,19 +192,13 @@ __device__ __forceinline__ void group_step(const Coef<R> &k, const RoundKeys &K,
     if constexpr (sizeof(R) == 4) {
         float nr[PPT], cs[PPT], sn[PPT];
 #pragma unroll
-        for (int q = 0; q < PPT; ++q) {
-            box_muller_f32(w[q].x, w[q].y, nr[q], cs[q], sn[q]);
-            nr[q] *= k.sigma;
-        }
+        for (int q = 0; q < PPT; ++q) box_muller_f32(w[q].x, w[q].y, k.bm, nr[q], cs[q], sn[q]);
 #pragma unroll
         for (int q = 0; q < PPT; ++q) em_step_f32(k, nr[q], cs[q], S.y[q], S.yacc[q], S.v[q], S.e[q]);
 #pragma unroll
         for (int q = 0; q < PPT; ++q) em_step_f32(k, nr[q], sn[q], S.y[q], S.yacc[q], S.v[q], S.e[q]);
 #pragma unroll
-        for (int q = 0; q < PPT; ++q) {
-            box_muller_f32(w[q].z, w[q].w, nr[q], cs[q], sn[q]);
-            nr[q] *= k.sigma;
-        }
+        for (int q = 0; q < PPT; ++q) box_muller_f32(w[q].z, w[q].w, k.bm, nr[q], cs[q], sn[q]);
 #pragma unroll
         for (int q = 0; q < PPT; ++q) em_step_f32(k, nr[q], cs[q], S.y[q], S.yacc[q], S.v[q], S.e[q]);
 #pragma unroll
@@ -231,7 +231,7 @@ __device__ __forceinline__ void advance(const Coef<R> &k, const RoundKeys &K, Sl
         if (n < blk_end) {
             const uint32_t m_end = (uint32_t)(blk_end >> 2);
             uint32_t m = (uint32_t)(n >> 2);
-#pragma unroll 1
+#pragma unroll kGroupUnroll
             for (; m < m_end; ++m) group_step<R, PPT>(k, K, S, m);
             n = (int64_t)m << 2;
         }
@@ -246,15 +246,19 @@ __device__ __forceinline__ void advance(const Coef<R> &k, const RoundKeys &K, Sl
     }
 }
 
+// Steps [max(w0, 0), w1) ∩ [0, N) of every trajectory of one tile: load the
+// state (through L2, so a tile continued by another block sees its latest
+// state), step it in registers, fill snapshot histograms and checkpoints, and
+// store it back.  Must be reached by every thread of the block; `sh` holds
+// zeros on entry (when histograms are on) and on exit.
 template <typename R, int PPT>
-__global__ void ABP_INTEGRATE_BOUNDS integrate_kernel(Batch b, State st, Hist h, Ckpt ck, Noise nz,
-                                                             KeyParam kp, int64_t g0, int64_t g1) {
-    extern __shared__ uint32_t sh[];
-    const int tile = blockIdx.x;
+__device__ __forceinline__ void run_tile(const Batch &b, const State &st, const Hist &h, const Ckpt &ck,
+                                         const Noise &nz, const RoundKeys &K, uint32_t *sh, int tile, int64_t w0,
+                                         int64_t w1) {
     const int set = b.tile_set[tile];
     const int64_t N = b.set_steps[set];
-    const int64_t n_begin = min(g0, N);
-    const int64_t n_end = min(g1, N);
+    const int64_t n_begin = min(w0, N);
+    const int64_t n_end = min(w1, N);
     if (n_begin >= n_end) return;  // uniform over the block
 
     const SV<R> s = view<R>(st);
@@ -271,30 +275,31 @@ __global__ void ABP_INTEGRATE_BOUNDS integrate_kernel(Batch b, State st, Hist h,
         const int li = threadIdx.x + q * kThreads;
         act[q] = li < count;
         idx[q] = first + (act[q] ? li : count - 1);
-        S.y[q] = s.y[idx[q]];
-        S.yacc[q] = s.yacc[idx[q]];
-        S.ylo[q] = s.ylo[idx[q]];
-        S.v[q] = s.v[idx[q]];
-        S.e[q] = s.e[idx[q]];
-        S.cell[q] = s.cell[idx[q]];
-        S.ss[q] = step_stream((uint64_t)idx[q] + nz.traj_base, kp.K);
+        S.y[q] = __ldcg(&s.y[idx[q]]);
+        S.yacc[q] = __ldcg(&s.yacc[idx[q]]);
+        S.ylo[q] = __ldcg(&s.ylo[idx[q]]);
+        S.v[q] = __ldcg(&s.v[idx[q]]);
+        S.e[q] = __ldcg(&s.e[idx[q]]);
+        S.cell[q] = __ldcg(&s.cell[idx[q]]);
+        S.ss[q] = step_stream((uint64_t)idx[q] + nz.traj_base, K);
     }
 
     const bool hist = h.bx > 0 || h.bv > 0;
-    const int nb = h.bx + (h.bv > 0 ? h.bv + 2 : 0);
-    if (hist) {
-        for (int i = threadIdx.x; i < nb; i += blockDim.x) sh[i] = 0;
-        __syncthreads();
-    }
     const R v_lo = (R)h.v_lo, v_hi = (R)h.v_hi;
     const R v_scale = h.bv > 0 ? (R)(h.bv / (h.v_hi - h.v_lo)) : (R)0;
+    // Warps with no trajectory of the tile (a short tile) skip the stepping but
+    // still reach the block's barriers.
+    bool any_act = false;
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) any_act |= act[q];
+    const bool warp_live = __any_sync(0xffffffffu, any_act);
 
     int64_t n = n_begin;
     while (n < n_end) {
         int64_t seg_end = n_end;
         if (hist && h.snap_every > 0) seg_end = min(seg_end, (n / h.snap_every + 1) * h.snap_every);
         if (ck.every > 0) seg_end = min(seg_end, (n / ck.every + 1) * ck.every);
-        advance<R, PPT>(k, kp.K, S, n, seg_end);
+        if (warp_live) advance<R, PPT>(k, K, S, n, seg_end);
         n = seg_end;
         if (hist && (h.snap_every > 0 ? (n % h.snap_every == 0) : (n == N))) {
             const int64_t snap = h.snap_every > 0 ? n / h.snap_every - 1 : 0;
@@ -325,6 +330,101 @@ __global__ void ABP_INTEGRATE_BOUNDS integrate_kernel(Batch b, State st, Hist h,
         s.v[idx[q]] = S.v[q];
         s.e[idx[q]] = S.e[q];
         s.cell[idx[q]] = S.cell[q];
+    }
+}
+
+__device__ __forceinline__ void zero_hist(uint32_t *sh, const Hist &h) {
+    if (h.bx > 0 || h.bv > 0) {
+        const int nb = h.bx + (h.bv > 0 ? h.bv + 2 : 0);
+        for (int i = threadIdx.x; i < nb; i += blockDim.x) sh[i] = 0;
+        __syncthreads();
+    }
+}
+
+// Lockstep schedule: one block per tile, every tile over the window [g0, g1).
+template <typename R, int PPT>
+__global__ void ABP_INTEGRATE_BOUNDS integrate_kernel(Batch b, State st, Hist h, Ckpt ck, Noise nz,
+                                                     KeyParam kp, int64_t g0, int64_t g1) {
+    extern __shared__ uint32_t sh[];
+    zero_hist(sh, h);
+    run_tile<R, PPT>(b, st, h, ck, nz, kp.K, sh, blockIdx.x, g0, g1);
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ int load_acquire(const int32_t *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void store_release(int32_t *p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Work-queue schedule: a persistent grid pops work items (tile, round) in a
+// fixed order -- round-major, tiles of longer sets first -- where round j of
+// a tile is its steps [g0 + j seg, g0 + (j+1) seg).  Round j of a tile may
+// start only when round j-1 of that tile has been published; that item was
+// popped earlier by a running block that itself waits only on items popped
+// before it, so the earliest unfinished item is always runnable.  The wait is
+// bounded: past q.wait_limit_ns the block records status 1 and every block
+// leaves at its next check, without touching the item.
+template <typename R, int PPT>
+__global__ void ABP_INTEGRATE_BOUNDS persistent_kernel(Batch b, State st, Hist h, Ckpt ck, Noise nz, KeyParam kp,
+                                                      Queue q, int64_t g0, int64_t g1, int64_t seg) {
+    extern __shared__ uint32_t sh[];
+    __shared__ int s_tile, s_round;
+    zero_hist(sh, h);
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int tile = -1, round = 0;
+            const int item = atomicAdd(q.head, 1);
+            if (item < q.n_items && *(volatile int32_t *)q.status == 0) {
+                int lo = 0, hi = q.n_rounds - 1;  // last round whose start is <= item
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (q.round_start[mid] <= item)
+                        lo = mid;
+                    else
+                        hi = mid - 1;
+                }
+                round = lo;
+                tile = q.perm[item - q.round_start[round]];
+                if (round > 0) {
+                    const uint64_t t0 = global_ns();
+                    while (load_acquire(&q.done[tile]) < round) {
+                        if (*(volatile int32_t *)q.status != 0) {
+                            tile = -1;
+                            break;
+                        }
+                        if (global_ns() - t0 > (uint64_t)q.wait_limit_ns) {
+                            atomicCAS(q.status, 0, 1);
+                            tile = -1;
+                            break;
+                        }
+                        __nanosleep(500);
+                    }
+                }
+            }
+            s_tile = tile;
+            s_round = round;
+        }
+        __syncthreads();
+        if (s_tile < 0) break;
+        {
+            const int64_t w0 = g0 + (int64_t)s_round * seg;
+            run_tile<R, PPT>(b, st, h, ck, nz, kp.K, sh, s_tile, w0, min(w0 + seg, g1));
+        }
+        __syncthreads();  // every thread's state stores precede the publication
+        if (threadIdx.x == 0 && s_tile != q.hold_tile) {
+            __threadfence();
+            store_release(&q.done[s_tile], s_round + 1);
+        }
     }
 }
 
@@ -473,6 +573,19 @@ KeyParam key_param(uint32_t k0, uint32_t k1) {
 }
 
 template <typename R, int PPT>
+cudaError_t launch_persistent_t(const Batch &b, const State &s, const Hist &h, const Ckpt &c, const Noise &nz,
+                                const Queue &q, int grid, int64_t g0, int64_t g1, int64_t seg, cudaStream_t st) {
+    const size_t smem = hist_smem(h);
+    auto kern = persistent_kernel<R, PPT>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    kern<<<grid, kThreads, smem, st>>>(b, s, h, c, nz, key_param(nz.k0, nz.k1), q, g0, g1, seg);
+    return cudaGetLastError();
+}
+
+template <typename R, int PPT>
 cudaError_t launch_integrate_t(const Batch &b, const State &s, const Hist &h, const Ckpt &c, const Noise &nz,
                                int64_t g0, int64_t g1, cudaStream_t st) {
     const size_t smem = hist_smem(h);
@@ -524,14 +637,38 @@ cudaError_t launch_integrate(const Batch &b, const State &s, const Hist &h, cons
     return cudaErrorInvalidValue;
 }
 
-cudaError_t integrate_occupancy(bool fp64, int ppt, size_t smem, int *blocks_per_sm) {
+cudaError_t launch_persistent(const Batch &b, const State &s, const Hist &h, const Ckpt &c, const Noise &nz,
+                              const Queue &q, int ppt, int grid, int64_t g0, int64_t g1, int64_t seg,
+                              cudaStream_t st) {
+    if (q.n_items == 0 || grid <= 0) return cudaSuccess;
+    if (s.fp64) {
+        switch (ppt) {
+            case 1: return launch_persistent_t<double, 1>(b, s, h, c, nz, q, grid, g0, g1, seg, st);
+            case 2: return launch_persistent_t<double, 2>(b, s, h, c, nz, q, grid, g0, g1, seg, st);
+            case 4: return launch_persistent_t<double, 4>(b, s, h, c, nz, q, grid, g0, g1, seg, st);
+        }
+    } else {
+        switch (ppt) {
+            case 1: return launch_persistent_t<float, 1>(b, s, h, c, nz, q, grid, g0, g1, seg, st);
+            case 2: return launch_persistent_t<float, 2>(b, s, h, c, nz, q, grid, g0, g1, seg, st);
+            case 4: return launch_persistent_t<float, 4>(b, s, h, c, nz, q, grid, g0, g1, seg, st);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t persistent_occupancy(bool fp64, int ppt, size_t smem, int *blocks_per_sm) {
     const void *f = nullptr;
     if (fp64) {
-        f = ppt == 1 ? (const void *)integrate_kernel<double, 1>
-                     : ppt == 2 ? (const void *)integrate_kernel<double, 2> : (const void *)integrate_kernel<double, 4>;
+        f = ppt == 1 ? (const void *)persistent_kernel<double, 1>
+                     : ppt == 2 ? (const void *)persistent_kernel<double, 2> : (const void *)persistent_kernel<double, 4>;
     } else {
-        f = ppt == 1 ? (const void *)integrate_kernel<float, 1>
-                     : ppt == 2 ? (const void *)integrate_kernel<float, 2> : (const void *)integrate_kernel<float, 4>;
+        f = ppt == 1 ? (const void *)persistent_kernel<float, 1>
+                     : ppt == 2 ? (const void *)persistent_kernel<float, 2> : (const void *)persistent_kernel<float, 4>;
+    }
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
     }
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, kThreads, smem);
 }

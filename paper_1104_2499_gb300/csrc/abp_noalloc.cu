@@ -136,8 +136,8 @@ extern "C" abp_status abp_run_set_noalloc(const abp_params *params, const abp_co
         return say(err, err_len, ABP_EINVAL, "histogram bins must be in [0, 8192]");
     if (cfg->hist_v_bins > 0 && !(cfg->v_hi > cfg->v_lo))
         return say(err, err_len, ABP_EINVAL, "v_hi must exceed v_lo");
-    if (cfg->snapshot_every < 0 || cfg->steps_per_launch < 0 || cfg->reserved != 0)
-        return say(err, err_len, ABP_EINVAL, "invalid snapshot_every / steps_per_launch / reserved");
+    if (cfg->snapshot_every < 0 || cfg->steps_per_launch < 0 || (cfg->schedule < 0 || cfg->schedule > 2))
+        return say(err, err_len, ABP_EINVAL, "invalid snapshot_every / steps_per_launch / schedule");
     const int ppt = cfg->particles_per_thread ? cfg->particles_per_thread : 1;
     if (ppt != 1 && ppt != 2 && ppt != 4) return say(err, err_len, ABP_EINVAL, "particles_per_thread must be 1, 2 or 4");
     if (n_traj < 0 || n_traj > kNoAllocMaxTraj)
