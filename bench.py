@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--small", action="store_true", help="reduced sweep (for quick checks, not a bench line)")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the pathwise-adjoint leg")
     return ap.parse_args()
 
 
@@ -221,6 +222,70 @@ def config_dict(w, args, extra=None):
     return d
 
 
+# ----------------------------------------------------------------------------- adjoint leg
+
+def adjoint_leg(A, stream, small=False):
+    """Pathwise adjoint of <v> w.r.t. (D, q, c, d, gamma0, a).
+
+    Cost: forward (with checkpoints every 1,000 steps) and backward on the differentiation
+    workload (1,048,576 trajectories x 10^5 steps, D = 0.05), timed with CUDA events.
+    Accuracy: at horizons where the pathwise derivative is well conditioned (the first 4,096
+    trajectories of the same set; 1,000 steps with central differences h = 1e-4 |theta|, and
+    2,000 steps, where h = 1e-4 |theta| is already past the linear range of a few paths, with
+    h = 1e-6 |theta|), the GPU adjoint against FP64 central differences with common random
+    numbers and against the FP64 tangent-linear, both from the oracle on the same trajectories.  (Over 10^5 steps the
+    frozen-noise dynamics is chaotic and the pathwise derivative grows exponentially; its
+    size at the full horizon is reported as found.)"""
+    import numpy as np
+    import torch
+    from oracle import oracle as O
+    from paper_1104_2499_gb300 import workloads as W
+
+    w = W.differentiation(n_traj=1 << 16, n_steps=20_000) if small else W.differentiation()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    with A.Ensemble(w, stream=stream) as ens, torch.cuda.stream(stream):
+        ens.set_params()
+        ens.integrate(-1)
+        ens.backward()  # warm-up (and allocation of the adjoint scratch)
+        ens.reset(w.seed)
+        ev[0].record(stream)
+        ens.integrate(-1)
+        ev[1].record(stream)
+        g = ens.backward()
+        ev[2].record(stream)
+        stream.synchronize()
+        fwd_ms, bwd_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+        g_full = g.cpu().numpy()[0]
+    def check(n_steps, rel_h, K):
+        wa = W.differentiation(n_traj=4096, n_steps=n_steps, checkpoint_every=K)
+        with A.Ensemble(wa, stream=stream) as ens, torch.cuda.stream(stream):
+            ens.run()
+            g_gpu = ens.backward(host=True).numpy()[0]
+        base = wa.sets[0]
+        kw = dict(seed=wa.seed, dt=wa.dt, n_traj=wa.n_traj[0], n_steps=wa.n_steps[0], v0_mode=wa.v0_mode)
+        g_tl = O.run_set(base, want_grad=True, **kw)["grad"]
+        fd = []
+        for name in A.GRAD_PARAMS:
+            h = rel_h * abs(base[name])
+            up = O.run_set(dict(base, **{name: base[name] + h}), **kw)["mean_v"]
+            dn = O.run_set(dict(base, **{name: base[name] - h}), **kw)["mean_v"]
+            fd.append((up - dn) / (2 * h))
+        fd = np.array(fd)
+        scale = float(np.max(np.abs(fd)))
+        return {"workload": wa.name, "checkpoint_every": K, "fd_h": "%g |theta|" % rel_h,
+                "grad_gpu": dict(zip(A.GRAD_PARAMS, map(float, g_gpu))),
+                "central_fd_fp64": dict(zip(A.GRAD_PARAMS, map(float, fd))),
+                "max_err_vs_fd_over_largest": float(np.max(np.abs(g_gpu - fd)) / scale),
+                "max_err_vs_tangent_linear_over_largest": float(np.max(np.abs(g_gpu - g_tl)) / scale),
+                "bar": 1e-3, "fd": "oracle FP64, common random numbers"}
+
+    acc = [check(1000, 1e-4, 200), check(2000, 1e-6, 1000)]
+    return {"workload": w.name, "particle_steps": w.particle_steps, "checkpoint_every": w.checkpoint_every,
+            "forward_ms": fwd_ms, "backward_ms": bwd_ms, "backward_over_forward": bwd_ms / fwd_ms,
+            "max_abs_pathwise_grad_full_horizon": float(np.max(np.abs(g_full))),
+            "accuracy": acc}
+
+
 # ----------------------------------------------------------------------------- GPU arm
 
 def main():
@@ -376,6 +441,10 @@ def main():
         if parity:
             cpu["parity_mean_v"] = parity
 
+    adj = None
+    if rank == 0 and world == 1 and not args.no_adjoint:
+        adj = adjoint_leg(A, stream, small=args.small)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -387,6 +456,7 @@ def main():
                                                 "integrator_launches_per_step": n_launch,
                                                 "parallelism": "dp%d (independent replicas)" % world}),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+                "adjoint": adj,
                 "wall_s_timed": wall, "sm_count": n_sm, "device": props.name}
         print(json.dumps(line), flush=True)
     ens.close()

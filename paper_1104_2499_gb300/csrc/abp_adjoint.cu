@@ -31,33 +31,50 @@ struct AdjArgs {
     Batch b;
     Ckpt ck;
     Noise nz;
+    RoundKeys K;        // Philox round keys of the seed (constant bank)
     float4 *sub;        // [n_sub][total_traj] sub-checkpoints (scratch)
     int64_t n_sub;      // sub-checkpoint slots per segment
     const double *w;    // [n_sets] dJ/dmean_v, NULL = 1
     double *partials;   // [n_tiles][6]
 };
 
-// Noise of consecutive steps: one Philox block serves steps 4m .. 4m+3.  The
-// pair (nrs, trig) is exactly what the forward integrator feeds its fused
+// Noise of the four steps 4m .. 4m+3 as the forward integrator consumes it:
+// the pair (nrs, trig) of each step is exactly what it feeds its fused
 // multiply-add, so re-runs reproduce the forward states bit for bit.
+__device__ __forceinline__ void block_noise(const Coef<float> &k, const StepStream &ss, const RoundKeys &K,
+                                            uint32_t m, float (&nrs)[4], float (&tr)[4]) {
+    const uint4 w = step_block(m, ss, K);
+    float a, c, s;
+    box_muller_f32(w.x, w.y, k.bm, a, c, s);
+    nrs[0] = a;
+    tr[0] = c;
+    nrs[1] = a;
+    tr[1] = s;
+    box_muller_f32(w.z, w.w, k.bm, a, c, s);
+    nrs[2] = a;
+    tr[2] = c;
+    nrs[3] = a;
+    tr[3] = s;
+}
+
+// The same noise one step at a time, for segments that do not start on a
+// multiple of 8 steps (one Philox block kept for its four steps).
 struct NoiseCursor {
     uint32_t m;
     bool valid;
-    float nrs01, nrs23, c01, s01, c23, s23;
+    float nrs[4], tr[4];
 
-    __device__ void at(const Coef<float> &k, const Noise &nz, uint32_t tlo, uint32_t thi, int64_t n, float &nrs,
-                       float &trig) {
+    __device__ void at(const Coef<float> &k, const StepStream &ss, const RoundKeys &K, int64_t n, float &nrs_n,
+                       float &tr_n) {
         const uint32_t mm = (uint32_t)(n >> 2);
         if (!valid || mm != m) {
-            const uint4 w = philox4x32_10(mm, 0u, tlo, thi, nz.k0, nz.k1);
-            box_muller_f32(w.x, w.y, k.bm, nrs01, c01, s01);
-            box_muller_f32(w.z, w.w, k.bm, nrs23, c23, s23);
+            block_noise(k, ss, K, mm, nrs, tr);
             m = mm;
             valid = true;
         }
-        const uint32_t j = (uint32_t)(n & 3);
-        nrs = j < 2 ? nrs01 : nrs23;
-        trig = (j & 1) ? (j < 2 ? s01 : s23) : (j < 2 ? c01 : c23);
+        const int j = (int)(n & 3);
+        nrs_n = j == 0 ? nrs[0] : j == 1 ? nrs[1] : j == 2 ? nrs[2] : nrs[3];
+        tr_n = j == 0 ? tr[0] : j == 1 ? tr[1] : j == 2 ? tr[2] : tr[3];
     }
 };
 
@@ -72,6 +89,32 @@ __device__ __forceinline__ void fwd(const Coef<float> &k, float nrs, float trig,
         int32_t cell = 0;
         fold_position<float>(y, yacc, lo, cell);
     }
+}
+
+// One reverse step at the pre-step state (x/L = yy, v = vv, e = ee, sigma z =
+// sz): parameter terms with lambda_{n+1}, then lambda_n = J^T lambda_{n+1} +
+// dJ/ds_n with dJ/dv_n = 1.
+__device__ __forceinline__ void reverse_step(const Coef<float> &k, float kx, float dtf, float yy, float vv, float ee,
+                                             float sz, float &lx, float &lv, float &le, float (&acc)[6]) {
+    float sphi, cphi;
+    __sincosf(fmaf(yy, kTwoPiF, (float)(2.0 * kPi * kPhaseShifted)), &sphi, &cphi);
+    acc[0] = fmaf(lv, sz, acc[0]);                              // D
+    acc[1] += le;                                               // q
+    acc[2] = fmaf(le, ee, acc[2]);                              // c
+    acc[3] = fmaf(ee * vv, fmaf(-le, vv, lv), acc[3]);          // d
+    acc[4] = fmaf(lv, vv, acc[4]);                              // gamma0
+    acc[5] = fmaf(lv, fmaf(2.0f * cphi, cphi, -1.0f), acc[5]);  // a
+    const float dvdx = kx * sphi * fmaf(2.0f * k.A4, cphi, k.K);
+    const float dvdv = fmaf(k.Bd, ee, k.G);
+    const float dedv = -2.0f * k.Bd * ee * vv;
+    const float dvde = k.Bd * vv;
+    const float dede = fmaf(-k.Bd, vv * vv, k.A);
+    const float nlx = fmaf(dvdx, lv, lx);
+    const float nlv = fmaf(dtf, lx, fmaf(dvdv, lv, fmaf(dedv, le, 1.0f)));
+    const float nle = fmaf(dvde, lv, dede * le);
+    lx = nlx;
+    lv = nlv;
+    le = nle;
 }
 
 __device__ __forceinline__ void block_sum6(double (&a)[6], double (*red)[6]) {
@@ -95,7 +138,96 @@ __device__ __forceinline__ void block_sum6(double (&a)[6], double (*red)[6]) {
     }
 }
 
-__global__ void __launch_bounds__(kThreads) adjoint_kernel(AdjArgs a) {
+// Segment [s0, s1) of one trajectory in reverse, from its checkpoint (y,
+// yacc, v, e) = c0.  Segments that start on a multiple of kSub steps run in
+// whole kSub-step chunks whose noise comes two Philox blocks at a time (the
+// forward's own path); others step one at a time.
+__device__ __forceinline__ void reverse_segment(const AdjArgs &a, const Coef<float> &k, const StepStream &ss,
+                                                float kx, float dtf, int64_t idx, int64_t s0, int64_t s1, float4 c0,
+                                                float &lx, float &lv, float &le, float (&acc)[6]) {
+    const int64_t T = a.b.total_traj;
+    float y = c0.x, yacc = c0.y, v = c0.z, e = c0.w;
+    const int n_chunks = (int)((s1 - s0 + kSub - 1) / kSub);
+    const bool aligned = (s0 & (kSub - 1)) == 0;
+    NoiseCursor nc;
+    nc.valid = false;
+    nc.m = 0;
+    // level 1: sub-checkpoints at s0, s0 + kSub, ...
+    for (int j = 0; j < n_chunks; ++j) {
+        const int64_t n0 = s0 + (int64_t)j * kSub;
+        a.sub[(size_t)j * T + idx] = make_float4(y, yacc, v, e);
+        const int len = (int)(s1 - n0 < kSub ? s1 - n0 : kSub);
+        if (aligned && len == kSub) {
+#pragma unroll
+            for (int b2 = 0; b2 < kSub / 4; ++b2) {
+                float nrs[4], tr[4];
+                block_noise(k, ss, a.K, (uint32_t)(n0 >> 2) + b2, nrs, tr);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) em_step_f32(k, nrs[i], tr[i], y, yacc, v, e);
+            }
+            if (((n0 + kSub) & (kBlockSteps - 1)) == 0) {
+                float lo = 0.0f;
+                int32_t cell = 0;
+                fold_position<float>(y, yacc, lo, cell);
+            }
+        } else {
+            for (int i = 0; i < len; ++i) {
+                float nrs, tr;
+                nc.at(k, ss, a.K, n0 + i, nrs, tr);
+                fwd(k, nrs, tr, n0 + i, y, yacc, v, e);
+            }
+        }
+    }
+    // level 2: chunks in reverse, re-run into registers and swept backwards
+    for (int j = n_chunks - 1; j >= 0; --j) {
+        const int64_t n0 = s0 + (int64_t)j * kSub;
+        const int len = (int)(s1 - n0 < kSub ? s1 - n0 : kSub);
+        const float4 cj = a.sub[(size_t)j * T + idx];
+        y = cj.x;
+        yacc = cj.y;
+        v = cj.z;
+        e = cj.w;
+        float ys[kSub], vs[kSub], es[kSub], szs[kSub];
+        if (aligned && len == kSub) {
+            // no fold falls inside an aligned chunk (folds come after multiples of kBlockSteps)
+#pragma unroll
+            for (int b2 = 0; b2 < kSub / 4; ++b2) {
+                float nrs[4], tr[4];
+                block_noise(k, ss, a.K, (uint32_t)(n0 >> 2) + b2, nrs, tr);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int q = 4 * b2 + i;
+                    ys[q] = y + yacc;  // the position the force sees
+                    vs[q] = v;
+                    es[q] = e;
+                    szs[q] = nrs[i] * tr[i];
+                    em_step_f32(k, nrs[i], tr[i], y, yacc, v, e);
+                }
+            }
+#pragma unroll
+            for (int i = kSub - 1; i >= 0; --i) reverse_step(k, kx, dtf, ys[i], vs[i], es[i], szs[i], lx, lv, le, acc);
+        } else {
+            nc.valid = false;
+#pragma unroll
+            for (int i = 0; i < kSub; ++i) {
+                if (i < len) {
+                    float nrs, tr;
+                    nc.at(k, ss, a.K, n0 + i, nrs, tr);
+                    ys[i] = y + yacc;
+                    vs[i] = v;
+                    es[i] = e;
+                    szs[i] = nrs * tr;
+                    fwd(k, nrs, tr, n0 + i, y, yacc, v, e);
+                }
+            }
+#pragma unroll
+            for (int i = kSub - 1; i >= 0; --i)
+                if (i < len) reverse_step(k, kx, dtf, ys[i], vs[i], es[i], szs[i], lx, lv, le, acc);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 2) adjoint_kernel(AdjArgs a) {
     __shared__ double red[kThreads / 32][6];
     const Batch &b = a.b;
     const int tile = blockIdx.x;
@@ -118,79 +250,15 @@ __global__ void __launch_bounds__(kThreads) adjoint_kernel(AdjArgs a) {
         const int li = li0 + threadIdx.x;
         const bool act = li < count && N > 0;
         const int64_t idx = first + (li < count ? li : count - 1);
-        const uint64_t gid = (uint64_t)idx + a.nz.traj_base;
-        const uint32_t tlo = (uint32_t)gid, thi = (uint32_t)(gid >> 32);
+        const StepStream ss = step_stream((uint64_t)idx + a.nz.traj_base, a.K);
         float lx = 0.0f, lv = 0.0f, le = 0.0f;
         double G[6] = {0, 0, 0, 0, 0, 0};
         if (act) {
             const int64_t n_seg = (N + K - 1) / K;
             for (int64_t seg = n_seg - 1; seg >= 0; --seg) {
                 const int64_t s0 = seg * K, s1 = min(s0 + K, N);
-                // level 1: re-run the segment from its checkpoint, leaving sub-checkpoints
-                const float4 c0 = a.ck.ck[(size_t)seg * T + idx];
-                float y = c0.x, yacc = c0.y, v = c0.z, e = c0.w;
-                NoiseCursor nc;
-                nc.valid = false;
-                nc.m = 0;
-                int64_t slot = 0;
-                for (int64_t n = s0; n < s1; ++n) {
-                    if (((n - s0) % kSub) == 0) a.sub[(size_t)(slot++) * T + idx] = make_float4(y, yacc, v, e);
-                    float nrs, trig;
-                    nc.at(k, a.nz, tlo, thi, n, nrs, trig);
-                    fwd(k, nrs, trig, n, y, yacc, v, e);
-                }
-                // level 2: sub-chunks in reverse
                 float acc[6] = {0, 0, 0, 0, 0, 0};
-                for (int64_t j = slot - 1; j >= 0; --j) {
-                    const int64_t n0 = s0 + j * kSub;
-                    const int len = (int)(s1 - n0 < kSub ? s1 - n0 : kSub);
-                    const float4 cj = a.sub[(size_t)j * T + idx];
-                    float ys[kSub], vs[kSub], es[kSub], szs[kSub];
-                    y = cj.x;
-                    yacc = cj.y;
-                    v = cj.z;
-                    e = cj.w;
-                    nc.valid = false;
-#pragma unroll
-                    for (int i = 0; i < kSub; ++i) {
-                        if (i < len) {
-                            float nrs, trig;
-                            nc.at(k, a.nz, tlo, thi, n0 + i, nrs, trig);
-                            ys[i] = y + yacc;  // the position the force sees
-                            vs[i] = v;
-                            es[i] = e;
-                            szs[i] = nrs * trig;
-                            fwd(k, nrs, trig, n0 + i, y, yacc, v, e);
-                        }
-                    }
-#pragma unroll
-                    for (int i = kSub - 1; i >= 0; --i) {
-                        if (i < len) {
-                            const float yy = ys[i], vv = vs[i], ee = es[i];
-                            float sphi, cphi;
-                            __sincosf(fmaf(yy, kTwoPiF, (float)(2.0 * kPi * kPhaseShifted)), &sphi, &cphi);
-                            // parameter terms use lambda_{n+1}
-                            acc[0] = fmaf(lv, szs[i], acc[0]);                  // D
-                            acc[1] += le;                                       // q
-                            acc[2] = fmaf(le, ee, acc[2]);                      // c
-                            acc[3] = fmaf(ee * vv, fmaf(-le, vv, lv), acc[3]);  // d
-                            acc[4] = fmaf(lv, vv, acc[4]);                      // gamma0
-                            acc[5] = fmaf(lv, fmaf(2.0f * cphi, cphi, -1.0f), acc[5]);  // a
-                            // transposed Jacobian of the step, plus dJ/dv_n = 1
-                            const float dvdx = kx * sphi * fmaf(2.0f * k.A4, cphi, k.K);
-                            const float dvdv = fmaf(k.Bd, ee, k.G);
-                            const float dedv = -2.0f * k.Bd * ee * vv;
-                            const float dvde = k.Bd * vv;
-                            const float dede = fmaf(-k.Bd, vv * vv, k.A);
-                            const float nlx = fmaf(dvdx, lv, lx);
-                            const float nlv = fmaf(dtf, lx, fmaf(dvdv, lv, fmaf(dedv, le, 1.0f)));
-                            const float nle = fmaf(dvde, lv, dede * le);
-                            lx = nlx;
-                            lv = nlv;
-                            le = nle;
-                        }
-                    }
-                }
+                reverse_segment(a, k, ss, kx, dtf, idx, s0, s1, a.ck.ck[(size_t)seg * T + idx], lx, lv, le, acc);
 #pragma unroll
                 for (int q = 0; q < 6; ++q) G[q] += (double)acc[q];
             }
@@ -307,6 +375,10 @@ extern "C" abp_status abp_backward(abp_ctx *ctx, const double *dJ_dmean_v, doubl
         a.n_sub = n_sub;
         a.w = w;
         a.partials = partials;
+        for (int r = 0; r < 10; ++r) {
+            a.K.rk[2 * r] = a.nz.k0 + (uint32_t)r * kPhiloxW0;
+            a.K.rk[2 * r + 1] = a.nz.k1 + (uint32_t)r * kPhiloxW1;
+        }
         adjoint_kernel<<<ctx->n_tiles, kThreads, 0, s>>>(a);
         ctx->launches += 1;
     }
