@@ -32,6 +32,10 @@ UNIT = "particle-steps/s"
 # wrap ~16, Philox4x32-10 amortised over its four steps 15, Box-Muller ~4.
 N_ALG = 35
 LANES_PER_SM = 128
+# DRAM bytes (read + write) per launch of the integrator on the 2,097,152-trajectory sweep grid,
+# from one ncu capture of that kernel (dram__bytes_read.sum + dram__bytes_write.sum); the traffic
+# is the state load/store, independent of the steps per launch.
+TRAFFIC_PER_LAUNCH = {"integrate_kernel<float,2>": (52505600 + 1640192, 2097152)}
 
 
 def parse():
@@ -48,7 +52,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--small", action="store_true", help="reduced sweep (for quick checks, not a bench line)")
+    ap.add_argument("--small", action="store_true",
+                    help="the sweep grid at 2,000 steps (profiling and quick checks; not a bench line)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the pathwise-adjoint leg")
     return ap.parse_args()
 
@@ -56,8 +61,8 @@ def parse():
 def workload(args):
     from paper_1104_2499_gb300 import workloads as W
 
-    if args.small:
-        return W.sweep_grid(n_D=16, n_q=8, traj_per_set=1024, n_steps=10_000)
+    if args.small:  # the same grid, 2,000 steps: several waves of the integrator, a few ms per launch
+        return W.sweep_grid(n_steps=2000)
     return W.sweep_grid()
 
 
@@ -425,8 +430,12 @@ def main():
     kern_avg = statistics.mean(kern_ms) * 1e-3
     achieved = N_ALG * ps_launch / kern_avg / 1e12
     kname = ("persistent_kernel<float,%d>" if queue else "integrate_kernel<float,%d>") % tuning["particles_per_thread"]
+    traffic = None
+    if kname in TRAFFIC_PER_LAUNCH and not args.small:
+        b_cap, t_cap = TRAFFIC_PER_LAUNCH[kname]
+        traffic = b_cap * w.total_traj / t_cap
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T lane-op/s", "frac": achieved / peak,
-            "traffic": None, "kernel": kname, "n_alg_per_particle_step": N_ALG,
+            "traffic": traffic, "traffic_unit": "bytes per launch", "kernel": kname, "n_alg_per_particle_step": N_ALG,
             "peak_basis": "%d SMs x %d FP32 lanes x %.0f MHz (%s sm_max_mhz)" % (n_sm, LANES_PER_SM, f_max / 1e6,
                                                                                 pk_kind),
             "launch_ms_avg": kern_avg * 1e3, "particle_steps_per_launch": ps_launch,

@@ -4,6 +4,9 @@
 // tile table, histograms, adjoint checkpoints, reduction scratch), validates
 // every argument, tiles the parameter sets for the device and enqueues the
 // kernels of abp_kernels.cu / abp_adjoint.cu on the context's stream.
+#include <dlfcn.h>
+#include <unistd.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -104,10 +107,10 @@ abp_status deliver(abp_ctx *ctx, void *dst, const void *src, size_t n, bool *syn
 // ---------------------------------------------------------------- autotuner
 
 // Schedule and particles per thread.  Every (schedule, PPT) candidate is timed
-// once per process, device and state type on a synthetic single-set batch that
-// fills the GPU (1,024 trajectories per SM, 2,048 steps after a 256-step
-// warm-up, CUDA events on the context's stream); the fastest candidate allowed
-// by the configuration wins.
+// once per device and state type on a synthetic single-set batch several
+// waves deep (4,096 trajectories per SM, 2,048 steps after a 256-step warm-up,
+// CUDA events on the context's stream); the fastest candidate allowed by the
+// configuration wins.
 struct TuneTable {
     bool done = false;
     float ms[3][3] = {};  // [schedule 1 = lockstep, 2 = work queue][ppt 1, 2, 4]
@@ -116,7 +119,7 @@ TuneTable g_tune[64][2];
 
 void measure_candidates(abp_ctx *ctx, TuneTable &tt) {
     const int fp = ctx->cfg.state_fp64 ? 1 : 0;
-    const int64_t T = (int64_t)std::max(ctx->sm_count, 1) * 1024;
+    const int64_t T = (int64_t)std::max(ctx->sm_count, 1) * 4096;
     const int64_t warm = 256, steps = 2048;
     const size_t rsz = fp ? sizeof(double) : sizeof(float);
     const int cands[3] = {1, 2, 4};
@@ -236,6 +239,76 @@ void measure_candidates(abp_ctx *ctx, TuneTable &tt) {
     tt.done = true;
 }
 
+// The timing table is also kept on disk beside the library (one line per
+// device model, SM count, state type and library version), so that every
+// process on the machine -- including a profiled rerun, whose own timings
+// would be distorted by the profiler -- makes the same choice.
+std::string tune_cache_path() {
+    Dl_info info;
+    if (!dladdr((const void *)&abp_version, &info) || !info.dli_fname) return std::string();
+    std::string p(info.dli_fname);
+    const size_t slash = p.rfind('/');
+    return (slash == std::string::npos ? std::string(".") : p.substr(0, slash)) + "/abp_tune_cache.txt";
+}
+
+std::string tune_key(const abp_ctx *ctx) {
+    cudaDeviceProp prop;
+    char name[256] = "unknown";
+    if (cudaGetDeviceProperties(&prop, ctx->device) == cudaSuccess) snprintf(name, sizeof(name), "%s", prop.name);
+    cudaGetLastError();
+    for (char *c = name; *c; ++c)
+        if (*c == ' ' || *c == '|') *c = '_';
+    char key[512];
+    snprintf(key, sizeof(key), "%s|%d|%d|%s", name, ctx->sm_count, ctx->cfg.state_fp64 ? 1 : 0, abp_version());
+    for (char *c = key; *c; ++c)
+        if (*c == ' ') *c = '_';
+    return key;
+}
+
+bool load_tune(const abp_ctx *ctx, TuneTable &tt) {
+    const std::string path = tune_cache_path(), key = tune_key(ctx);
+    if (path.empty()) return false;
+    FILE *f = fopen(path.c_str(), "r");
+    if (!f) return false;
+    char line[1024];
+    bool ok = false;
+    while (fgets(line, sizeof(line), f)) {
+        char k[512];
+        float m[6];
+        if (sscanf(line, "%511s %f %f %f %f %f %f", k, &m[0], &m[1], &m[2], &m[3], &m[4], &m[5]) == 7 && key == k) {
+            for (int i = 0; i < 3; ++i) {
+                tt.ms[1][i] = m[i];
+                tt.ms[2][i] = m[3 + i];
+            }
+            tt.done = ok = true;
+        }
+    }
+    fclose(f);
+    return ok;
+}
+
+void save_tune(const abp_ctx *ctx, const TuneTable &tt) {
+    const std::string path = tune_cache_path(), key = tune_key(ctx);
+    if (path.empty()) return;
+    std::vector<std::string> keep;
+    if (FILE *f = fopen(path.c_str(), "r")) {
+        char line[1024];
+        while (fgets(line, sizeof(line), f)) {
+            char k[512];
+            if (sscanf(line, "%511s", k) == 1 && key != k) keep.emplace_back(line);
+        }
+        fclose(f);
+    }
+    const std::string tmp = path + ".tmp." + std::to_string((long)getpid());
+    FILE *f = fopen(tmp.c_str(), "w");
+    if (!f) return;
+    for (const std::string &l : keep) fputs(l.c_str(), f);
+    fprintf(f, "%s %.6g %.6g %.6g %.6g %.6g %.6g\n", key.c_str(), tt.ms[1][0], tt.ms[1][1], tt.ms[1][2], tt.ms[2][0],
+            tt.ms[2][1], tt.ms[2][2]);
+    fclose(f);
+    if (rename(tmp.c_str(), path.c_str()) != 0) remove(tmp.c_str());
+}
+
 // Sets ctx->sched and ctx->ppt from the configuration and the timing table.
 void autotune(abp_ctx *ctx) {
     const int want_sched = ctx->cfg.schedule;          // 0 auto, 1 lockstep, 2 work queue
@@ -248,7 +321,10 @@ void autotune(abp_ctx *ctx) {
     const int dev = ctx->device, fp = ctx->cfg.state_fp64 ? 1 : 0;
     TuneTable local;
     TuneTable &tt = (dev >= 0 && dev < 64) ? g_tune[dev][fp] : local;
-    if (!tt.done) measure_candidates(ctx, tt);
+    if (!tt.done && !load_tune(ctx, tt)) {
+        measure_candidates(ctx, tt);
+        if (tt.done) save_tune(ctx, tt);
+    }
     const int cands[3] = {1, 2, 4};
     float best = 1e30f;
     int bs = want_sched ? want_sched : 1, bp = want_ppt ? want_ppt : 1;
