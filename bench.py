@@ -314,6 +314,7 @@ def main():
 
     from paper_1104_2499_gb300 import abp as A
     from paper_1104_2499_gb300 import build as B
+    from paper_1104_2499_gb300 import shard
 
     if rank == 0 or world == 1:
         B.build()
@@ -328,7 +329,7 @@ def main():
     n_sm = props.multi_processor_count
     # weak scaling: every rank integrates its own copy of the sweep with distinct trajectory ids
     ens = A.Ensemble(w, stream=stream, particles_per_thread=args.ppt, steps_per_launch=args.steps_per_launch,
-                     traj_base=rank * w.total_traj, schedule=args.schedule)
+                     traj_base=shard.replica_traj_base(rank, w.total_traj), schedule=args.schedule)
     S = w.n_sets
     mom = torch.empty((S, 8), dtype=torch.float64, device="cuda")
     ns = 1

@@ -169,6 +169,19 @@ ABP_API abp_status abp_num_snapshots(const abp_ctx *ctx, int64_t *n_snap);
  * velocity so far. */
 ABP_API abp_status abp_get_state(abp_ctx *ctx, double *x, double *x0, double *v, double *e, double *vbar);
 
+/* Checkpoint / resume of a batch on the host side.  abp_save writes the
+ * context's current batch -- step counter, seed, the per-trajectory state
+ * (28 bytes per FP32 trajectory) and the histograms -- into buf (host or device
+ * memory, caller-owned); with buf == NULL it only stores the size needed in
+ * *bytes.  abp_load restores such an image into a context whose batch was set
+ * with the same sets, sizes and state type (checked; ABP_EINVAL otherwise);
+ * integrating on then gives bitwise the same results as an uninterrupted run.
+ * The adjoint checkpoints are not part of the image: abp_backward after
+ * abp_load returns ABP_ESTATE until the batch is integrated again from step 0.
+ * Both calls return after their copies have completed. */
+ABP_API abp_status abp_save(abp_ctx *ctx, void *buf, size_t *bytes);
+ABP_API abp_status abp_load(abp_ctx *ctx, const void *buf, size_t bytes);
+
 /* Pathwise adjoint.  With the noise held fixed, returns for every set
  * grad[s][j] = dJ/dtheta_j, J = sum_s dJ_dmean_v[s] * mean_v[s], theta =
  * (D, q, c, d, gamma0, asym) of that set.  dJ_dmean_v: host or device, n_sets

@@ -99,6 +99,10 @@ def lib():
         L.abp_reduce.restype = st
         L.abp_get_state.argtypes = [_VP, _VP, _VP, _VP, _VP, _VP]
         L.abp_get_state.restype = st
+        L.abp_save.argtypes = [_VP, _VP, C.POINTER(C.c_size_t)]
+        L.abp_save.restype = st
+        L.abp_load.argtypes = [_VP, _VP, C.c_size_t]
+        L.abp_load.restype = st
         L.abp_backward.argtypes = [_VP, _VP, _VP]
         L.abp_backward.restype = st
         L.abp_synchronize.argtypes = [_VP]
@@ -207,6 +211,23 @@ def abp_reduce(ctx, moments=None, hist_x=None, hist_v=None):
 
 def abp_get_state(ctx, x=None, x0=None, v=None, e=None, vbar=None):
     _check(lib().abp_get_state(ctx, _ptr(x), _ptr(x0), _ptr(v), _ptr(e), _ptr(vbar)), ctx)
+
+
+def abp_save(ctx, buf=None):
+    """Image of the context's batch.  buf: None (a new numpy uint8 host array is returned)
+    or a contiguous host/device tensor or array large enough."""
+    n = C.c_size_t(0)
+    _check(lib().abp_save(ctx, None, C.byref(n)), ctx)
+    if buf is None:
+        buf = np.empty(n.value, dtype=np.uint8)
+    have = C.c_size_t(buf.nbytes if isinstance(buf, np.ndarray) else buf.numel() * buf.element_size())
+    _check(lib().abp_save(ctx, _ptr(buf), C.byref(have)), ctx)
+    return buf
+
+
+def abp_load(ctx, buf):
+    nbytes = buf.nbytes if isinstance(buf, np.ndarray) else buf.numel() * buf.element_size()
+    _check(lib().abp_load(ctx, _ptr(buf), nbytes), ctx)
 
 
 def abp_backward(ctx, dJ_dmean_v=None, grad=None):

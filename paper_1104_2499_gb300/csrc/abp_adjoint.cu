@@ -327,6 +327,8 @@ extern "C" abp_status abp_backward(abp_ctx *ctx, const double *dJ_dmean_v, doubl
     if (ctx->cfg.checkpoint_every <= 0)
         return set_err(ctx, ABP_ESTATE, "abp_backward needs checkpoint_every > 0 during abp_integrate");
     if (ctx->g < ctx->max_steps) return set_err(ctx, ABP_ESTATE, "abp_backward before the integration completed");
+    if (!ctx->ckpt_complete)
+        return set_err(ctx, ABP_ESTATE, "abp_backward after abp_load: the checkpoints do not cover the run from step 0");
     const int64_t T = ctx->total_traj;
     const int64_t n_sub = (ctx->cfg.checkpoint_every + kSub - 1) / kSub;
     const size_t sub_bytes = sizeof(float4) * (size_t)n_sub * (size_t)T;

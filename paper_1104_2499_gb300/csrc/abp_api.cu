@@ -466,6 +466,7 @@ abp_status abp_set_params(abp_ctx *ctx, int32_t n_sets, const abp_params *sets, 
     ctx->total_traj = total;
     ctx->max_steps = max_n;
     ctx->g = 0;
+    ctx->ckpt_complete = true;
 
     // Tiles: contiguous runs of at most kThreads * ppt trajectories of one set.
     autotune(ctx);
@@ -573,6 +574,7 @@ abp_status abp_reset(abp_ctx *ctx, uint64_t seed) {
     if (!ctx->have_batch) return fail(ctx, ABP_ESTATE, "abp_reset before abp_set_params");
     ctx->cfg.seed = seed;
     ctx->g = 0;
+    ctx->ckpt_complete = true;
     cudaStream_t s = ctx->stream;
     cudaError_t e = cudaMemsetAsync(ctx->d_status.p, 0, sizeof(int32_t), s);
     if (e == cudaSuccess && ctx->d_hx.bytes) e = cudaMemsetAsync(ctx->d_hx.p, 0, ctx->d_hx.bytes, s);
@@ -780,6 +782,121 @@ abp_status abp_reduce(abp_ctx *ctx, double *moments, uint32_t *hist_x, uint32_t 
     if (hist_v && ctx->d_hv.bytes)
         if ((st = deliver(ctx, hist_v, ctx->d_hv.p, ctx->d_hv.bytes, &synced)) != ABP_OK) return st;
     if (synced) return abp_synchronize(ctx);
+    return ABP_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+struct SaveHeader {
+    char magic[8];  // "ABPSAVE1"
+    uint32_t version, fp64;
+    int64_t g, total_traj;
+    int32_t n_sets, reserved;
+    uint64_t seed, traj_base;
+    uint64_t hx_bytes, hv_bytes;
+    uint64_t signature;  // FNV-1a of the sets' parameters, sizes and step counts
+};
+
+uint64_t batch_signature(const abp_ctx *ctx) {
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](const void *p, size_t n) {
+        const unsigned char *c = (const unsigned char *)p;
+        for (size_t i = 0; i < n; ++i) {
+            h ^= c[i];
+            h *= 1099511628211ull;
+        }
+    };
+    mix(ctx->params.data(), sizeof(abp_params) * ctx->params.size());
+    mix(ctx->n_traj.data(), sizeof(int64_t) * ctx->n_traj.size());
+    mix(ctx->n_steps.data(), sizeof(int64_t) * ctx->n_steps.size());
+    return h;
+}
+
+// The state arrays of an image, in order, with their sizes.
+std::vector<std::pair<DevBuf *, size_t>> image_parts(abp_ctx *ctx) {
+    const size_t T = (size_t)ctx->total_traj, rsz = ctx->cfg.state_fp64 ? sizeof(double) : sizeof(float);
+    return {{&ctx->d_y, rsz * T},    {&ctx->d_yacc, rsz * T}, {&ctx->d_ylo, rsz * T},
+            {&ctx->d_v, rsz * T},    {&ctx->d_e, rsz * T},    {&ctx->d_y0, rsz * T},
+            {&ctx->d_cell, 4 * T},   {&ctx->d_hx, ctx->d_hx.bytes}, {&ctx->d_hv, ctx->d_hv.bytes}};
+}
+
+}  // namespace
+
+extern "C" {
+
+abp_status abp_save(abp_ctx *ctx, void *buf, size_t *bytes) {
+    if (!ctx || !bytes) return ABP_EINVAL;
+    if (!ctx->have_batch) return fail(ctx, ABP_ESTATE, "abp_save before abp_set_params");
+    size_t need = sizeof(SaveHeader);
+    for (auto &pt : image_parts(ctx)) need += pt.second;
+    if (!buf) {
+        *bytes = need;
+        return ABP_OK;
+    }
+    if (*bytes < need) return fail(ctx, ABP_EINVAL, "abp_save: buffer of %zu bytes, %zu needed", *bytes, need);
+    SaveHeader hd{};
+    memcpy(hd.magic, "ABPSAVE1", 8);
+    hd.version = 1;
+    hd.fp64 = ctx->cfg.state_fp64 ? 1 : 0;
+    hd.g = ctx->g;
+    hd.total_traj = ctx->total_traj;
+    hd.n_sets = ctx->n_sets;
+    hd.seed = ctx->cfg.seed;
+    hd.traj_base = ctx->cfg.traj_base;
+    hd.hx_bytes = ctx->d_hx.bytes;
+    hd.hv_bytes = ctx->d_hv.bytes;
+    hd.signature = batch_signature(ctx);
+    const bool dev = is_device_ptr(buf);
+    cudaStream_t s = ctx->stream;
+    cudaError_t e = cudaMemcpyAsync(buf, &hd, sizeof(hd), dev ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, s);
+    size_t off = sizeof(hd);
+    for (auto &pt : image_parts(ctx)) {
+        if (e == cudaSuccess && pt.second)
+            e = cudaMemcpyAsync((char *)buf + off, pt.first->p, pt.second,
+                                dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
+        off += pt.second;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "abp_save");
+    *bytes = need;
+    return ABP_OK;
+}
+
+abp_status abp_load(abp_ctx *ctx, const void *buf, size_t bytes) {
+    if (!ctx || !buf) return ABP_EINVAL;
+    if (!ctx->have_batch) return fail(ctx, ABP_ESTATE, "abp_load before abp_set_params");
+    SaveHeader hd{};
+    if (bytes < sizeof(hd)) return fail(ctx, ABP_EINVAL, "abp_load: image too small");
+    const bool dev = is_device_ptr(buf);
+    cudaStream_t s = ctx->stream;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemcpy(&hd, buf, sizeof(hd), dev ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "abp_load header");
+    size_t need = sizeof(hd);
+    for (auto &pt : image_parts(ctx)) need += pt.second;
+    if (memcmp(hd.magic, "ABPSAVE1", 8) != 0 || hd.version != 1)
+        return fail(ctx, ABP_EINVAL, "abp_load: not an image written by abp_save");
+    if (hd.fp64 != (ctx->cfg.state_fp64 ? 1u : 0u) || hd.total_traj != ctx->total_traj || hd.n_sets != ctx->n_sets ||
+        hd.signature != batch_signature(ctx) || hd.hx_bytes != ctx->d_hx.bytes || hd.hv_bytes != ctx->d_hv.bytes ||
+        bytes < need || hd.g < 0 || hd.g > ctx->max_steps)
+        return fail(ctx, ABP_EINVAL, "abp_load: the image belongs to a different batch or configuration");
+    size_t off = sizeof(hd);
+    for (auto &pt : image_parts(ctx)) {
+        if (e == cudaSuccess && pt.second)
+            e = cudaMemcpyAsync(pt.first->p, (const char *)buf + off, pt.second,
+                                dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
+        off += pt.second;
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_status.p, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "abp_load");
+    ctx->g = hd.g;
+    ctx->cfg.seed = hd.seed;
+    ctx->cfg.traj_base = hd.traj_base;
+    ctx->ckpt_complete = hd.g == 0;
+    ctx->drop_graphs();
     return ABP_OK;
 }
 

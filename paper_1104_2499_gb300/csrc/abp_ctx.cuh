@@ -50,6 +50,7 @@ struct abp_ctx {
     int64_t total_traj = 0;
     int64_t max_steps = 0;
     int64_t g = 0;  // global steps issued: set s has done min(g, n_steps[s])
+    bool ckpt_complete = true;  // adjoint checkpoints cover the run from step 0 (false after abp_load)
     int ppt = 1;
     int sched = 1;                 // 1: lockstep launches, 2: work queue (autotuned when cfg.schedule = 0)
     int64_t steps_per_launch = 0;  // lockstep: steps per launch; work queue: steps per round

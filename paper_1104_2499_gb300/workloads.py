@@ -124,6 +124,16 @@ def large_snapshots(n_traj=1 << 26, n_steps=1_000_000, seed=4, snapshot_every=10
                     v_lo=-5.0, v_hi=5.0, snapshot_every=snapshot_every)
 
 
+def force_sweep(n_F=64, F_lo=-1.0, F_hi=1.0, traj_per_set=4096, n_steps=100_000, D=0.1, seed=6) -> Workload:
+    """The paper's benchmark observable, Fig. 2 and Sec. 2: mean velocity against the external
+    (opposing) force F0, one parameter set per force value, n_F values evenly spaced in
+    [F_lo, F_hi], the other parameters at their defaults."""
+    Fs = np.linspace(F_lo, F_hi, n_F)
+    sets = [_with(D=D, F0=float(F)) for F in Fs]
+    return Workload(name="force_sweep_%dx%d_%dsteps" % (n_F, traj_per_set, n_steps), sets=sets,
+                    n_traj=[traj_per_set] * n_F, n_steps=[n_steps] * n_F, dt=1e-3, seed=seed, v0_mode=0)
+
+
 def shrink(w: Workload, max_traj: int | None = None, max_steps: int | None = None, max_sets: int | None = None,
            name: str | None = None) -> Workload:
     """A smaller copy of a workload (same parameter values) for parity runs."""

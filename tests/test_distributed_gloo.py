@@ -1,0 +1,129 @@
+"""Multi-process ensemble on CPU ranks (gloo, world size 2).
+
+Each rank integrates its replica of a batch with the FP64 oracle (trajectory ids offset by
+rank, as abp_config.traj_base does on the GPU) and the per-set sums are all-reduced; the
+combined moments must equal those of the concatenated ensemble computed in one process.
+Failure detection is tested on the host: a rank that leaves before the collective makes the
+other rank's all-reduce fail after its timeout instead of hanging.
+"""
+import datetime
+import os
+import socket
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+dist = pytest.importorskip("torch.distributed")
+
+from paper_1104_2499_gb300 import shard
+from paper_1104_2499_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _batch():
+    sets = [W._with(D=0.1), W._with(D=0.3, q=2.0, asym=0.1)]
+    return W.Workload(name="gloo", sets=sets, n_traj=[40, 25], n_steps=[600, 600], dt=1e-3, seed=5, v0_mode=1)
+
+
+def _oracle_local(w, traj_base):
+    import sys
+
+    sys.path.insert(0, ROOT)
+    from oracle import oracle as O
+
+    mom = np.zeros((w.n_sets, 8))
+    per = []
+    for i, p in enumerate(w.sets):
+        r = O.run_set(p, seed=w.seed, dt=w.dt, n_traj=w.n_traj[i], n_steps=w.n_steps[i],
+                      traj_base=traj_base + w.traj_base()[i], v0_mode=w.v0_mode, want_states=True, n_threads=1)
+        mom[i, 4:] = r["sums"]
+        per.append((r["vbar"], r["x"] - r["x0"]))
+    return mom, per
+
+
+def _worker(rank, world, port, out_dir, fail_rank):
+    import sys
+
+    sys.path.insert(0, ROOT)
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=10))
+    w = _batch()
+    local, _ = _oracle_local(w, shard.replica_traj_base(rank, w.total_traj))
+    if rank == fail_rank:
+        os._exit(0)  # leaves without joining the collective (host-side failure)
+
+    def all_reduce(a):
+        t = torch.from_numpy(a)
+        dist.all_reduce(t)
+        return t.numpy()
+
+    status = "ok"
+    try:
+        res = shard.combine(local, w.n_traj, w.n_steps, w.dt, world, all_reduce)
+        np.save(os.path.join(out_dir, "rank%d.npy" % rank), res)
+    except Exception as e:  # the collective ended with an error instead of hanging
+        status = "error: " + type(e).__name__
+    with open(os.path.join(out_dir, "status%d.txt" % rank), "w") as f:
+        f.write(status)
+    if status == "ok":
+        dist.destroy_process_group()
+
+
+def _run(world, fail_rank, tmp_path):
+    import torch.multiprocessing as mp
+
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    procs = [ctx.Process(target=_worker, args=(r, world, port, str(tmp_path), fail_rank)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+        if p.is_alive():
+            p.kill()
+            pytest.fail("a rank did not finish")
+    return procs
+
+
+def test_replicas_combine_to_the_concatenated_ensemble(tmp_path):
+    procs = _run(2, -1, tmp_path)
+    assert all(p.exitcode == 0 for p in procs)
+    w = _batch()
+    r0 = np.load(tmp_path / "rank0.npy")
+    r1 = np.load(tmp_path / "rank1.npy")
+    np.testing.assert_array_equal(r0, r1)
+    # one process, both replicas, per-trajectory values concatenated
+    per = [_oracle_local(w, shard.replica_traj_base(r, w.total_traj))[1] for r in range(2)]
+    for i in range(w.n_sets):
+        vbar = np.concatenate([per[r][i][0] for r in range(2)])
+        dx = np.concatenate([per[r][i][1] for r in range(2)])
+        M = vbar.size
+        assert r0[i, 0] == pytest.approx(vbar.mean(), rel=1e-12)
+        assert r0[i, 1] == pytest.approx(vbar.std(ddof=1) / np.sqrt(M), rel=1e-9)
+        assert r0[i, 2] == pytest.approx(np.mean(dx ** 2), rel=1e-12)
+        T = w.n_steps[i] * w.dt
+        assert r0[i, 3] == pytest.approx(dx.var() / (2 * T), rel=1e-9)
+
+
+def test_a_rank_that_leaves_makes_the_collective_fail_not_hang(tmp_path):
+    procs = _run(2, 1, tmp_path)
+    status = (tmp_path / "status0.txt").read_text()
+    assert status.startswith("error"), status
+    assert not (tmp_path / "status1.txt").exists()
+
+
+def test_moments_from_sums_edge_cases():
+    m = shard.moments_from_sums([[0, 0, 0, 0], [2.0, 2.0, 4.0, 8.0]], [0, 2], [100, 0], 1e-3)
+    assert np.all(m[0] == 0)
+    assert m[1, 0] == 1.0 and m[1, 1] == 0.0 and m[1, 2] == 4.0 and m[1, 3] == 0.0
