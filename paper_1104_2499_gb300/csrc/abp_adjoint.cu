@@ -81,23 +81,26 @@ struct NoiseCursor {
 // One forward step at absolute index n, including the position fold the
 // integrator applies after every kBlockSteps-th step (y depends on y and
 // yacc only; the fold's error term and the cell index are not needed here).
-__device__ __forceinline__ void fwd(const Coef<float> &k, float nrs, float trig, int64_t n, float &y, float &yacc,
-                                   float &v, float &e) {
-    em_step_f32(k, nrs, trig, y, yacc, v, e);
-    if (((n + 1) & (kBlockSteps - 1)) == 0) {
-        float lo = 0.0f;
-        int32_t cell = 0;
-        fold_position<float>(y, yacc, lo, cell);
-    }
+__device__ __forceinline__ void fold(float &y, float &yacc, float &pb) {
+    float lo = 0.0f;
+    int32_t cell = 0;
+    fold_position<float>(y, yacc, lo, cell);
+    pb = phase_base(y);
 }
 
-// One reverse step at the pre-step state (x/L = yy, v = vv, e = ee, sigma z =
-// sz): parameter terms with lambda_{n+1}, then lambda_n = J^T lambda_{n+1} +
-// dJ/ds_n with dJ/dv_n = 1.
-__device__ __forceinline__ void reverse_step(const Coef<float> &k, float kx, float dtf, float yy, float vv, float ee,
+__device__ __forceinline__ void fwd(const Coef<float> &k, float nrs, float trig, int64_t n, float &y, float &yacc,
+                                   float &pb, float &v, float &e) {
+    em_step_f32(k, nrs, trig, pb, yacc, v, e);
+    if (((n + 1) & (kBlockSteps - 1)) == 0) fold(y, yacc, pb);
+}
+
+// One reverse step at the pre-step state (force phase ph, v = vv, e = ee,
+// sigma z = sz): parameter terms with lambda_{n+1}, then lambda_n = J^T
+// lambda_{n+1} + dJ/ds_n with dJ/dv_n = 1.
+__device__ __forceinline__ void reverse_step(const Coef<float> &k, float kx, float dtf, float ph, float vv, float ee,
                                              float sz, float &lx, float &lv, float &le, float (&acc)[6]) {
     float sphi, cphi;
-    __sincosf(fmaf(yy, kTwoPiF, (float)(2.0 * kPi * kPhaseShifted)), &sphi, &cphi);
+    __sincosf(ph, &sphi, &cphi);
     acc[0] = fmaf(lv, sz, acc[0]);                              // D
     acc[1] += le;                                               // q
     acc[2] = fmaf(le, ee, acc[2]);                              // c
@@ -147,6 +150,7 @@ __device__ __forceinline__ void reverse_segment(const AdjArgs &a, const Coef<flo
                                                 float &lx, float &lv, float &le, float (&acc)[6]) {
     const int64_t T = a.b.total_traj;
     float y = c0.x, yacc = c0.y, v = c0.z, e = c0.w;
+    float pb = phase_base(y);
     const int n_chunks = (int)((s1 - s0 + kSub - 1) / kSub);
     const bool aligned = (s0 & (kSub - 1)) == 0;
     NoiseCursor nc;
@@ -163,18 +167,14 @@ __device__ __forceinline__ void reverse_segment(const AdjArgs &a, const Coef<flo
                 float nrs[4], tr[4];
                 block_noise(k, ss, a.K, (uint32_t)(n0 >> 2) + b2, nrs, tr);
 #pragma unroll
-                for (int i = 0; i < 4; ++i) em_step_f32(k, nrs[i], tr[i], y, yacc, v, e);
+                for (int i = 0; i < 4; ++i) em_step_f32(k, nrs[i], tr[i], pb, yacc, v, e);
             }
-            if (((n0 + kSub) & (kBlockSteps - 1)) == 0) {
-                float lo = 0.0f;
-                int32_t cell = 0;
-                fold_position<float>(y, yacc, lo, cell);
-            }
+            if (((n0 + kSub) & (kBlockSteps - 1)) == 0) fold(y, yacc, pb);
         } else {
             for (int i = 0; i < len; ++i) {
                 float nrs, tr;
                 nc.at(k, ss, a.K, n0 + i, nrs, tr);
-                fwd(k, nrs, tr, n0 + i, y, yacc, v, e);
+                fwd(k, nrs, tr, n0 + i, y, yacc, pb, v, e);
             }
         }
     }
@@ -187,7 +187,8 @@ __device__ __forceinline__ void reverse_segment(const AdjArgs &a, const Coef<flo
         yacc = cj.y;
         v = cj.z;
         e = cj.w;
-        float ys[kSub], vs[kSub], es[kSub], szs[kSub];
+        pb = phase_base(y);
+        float ys[kSub], vs[kSub], es[kSub], szs[kSub];  // ys: the force phase of each step
         if (aligned && len == kSub) {
             // no fold falls inside an aligned chunk (folds come after multiples of kBlockSteps)
 #pragma unroll
@@ -197,11 +198,11 @@ __device__ __forceinline__ void reverse_segment(const AdjArgs &a, const Coef<flo
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     const int q = 4 * b2 + i;
-                    ys[q] = y + yacc;  // the position the force sees
+                    ys[q] = phase_arg(pb, yacc);
                     vs[q] = v;
                     es[q] = e;
                     szs[q] = nrs[i] * tr[i];
-                    em_step_f32(k, nrs[i], tr[i], y, yacc, v, e);
+                    em_step_f32(k, nrs[i], tr[i], pb, yacc, v, e);
                 }
             }
 #pragma unroll
@@ -213,11 +214,11 @@ __device__ __forceinline__ void reverse_segment(const AdjArgs &a, const Coef<flo
                 if (i < len) {
                     float nrs, tr;
                     nc.at(k, ss, a.K, n0 + i, nrs, tr);
-                    ys[i] = y + yacc;
+                    ys[i] = phase_arg(pb, yacc);
                     vs[i] = v;
                     es[i] = e;
                     szs[i] = nrs * tr;
-                    fwd(k, nrs, tr, n0 + i, y, yacc, v, e);
+                    fwd(k, nrs, tr, n0 + i, y, yacc, pb, v, e);
                 }
             }
 #pragma unroll

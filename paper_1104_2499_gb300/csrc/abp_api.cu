@@ -240,7 +240,7 @@ void measure_candidates(abp_ctx *ctx, TuneTable &tt) {
 }
 
 // The timing table is also kept on disk beside the library (one line per
-// device model, SM count, state type and library version), so that every
+// device model, SM count, state type and library build), so that every
 // process on the machine -- including a profiled rerun, whose own timings
 // would be distorted by the profiler -- makes the same choice.
 std::string tune_cache_path() {
@@ -259,7 +259,9 @@ std::string tune_key(const abp_ctx *ctx) {
     for (char *c = name; *c; ++c)
         if (*c == ' ' || *c == '|') *c = '_';
     char key[512];
-    snprintf(key, sizeof(key), "%s|%d|%d|%s", name, ctx->sm_count, ctx->cfg.state_fp64 ? 1 : 0, abp_version());
+    // the build time stamp: every rebuild of the library re-times the candidates
+    snprintf(key, sizeof(key), "%s|%d|%d|%s|%s_%s", name, ctx->sm_count, ctx->cfg.state_fp64 ? 1 : 0, abp_version(),
+             __DATE__, __TIME__);
     for (char *c = key; *c; ++c)
         if (*c == ' ') *c = '_';
     return key;

@@ -150,6 +150,7 @@ __global__ void __launch_bounds__(kThreads) init_kernel(Batch b, State st, Hist 
 template <typename R, int PPT>
 struct Slots {
     R y[PPT], yacc[PPT], ylo[PPT], v[PPT], e[PPT];
+    float pb[PPT];  // phase_base(y) of the FP32 path
     int32_t cell[PPT];
     StepStream ss[PPT];
 };
@@ -175,7 +176,7 @@ __device__ __forceinline__ void single_step(const Coef<R> &k, const RoundKeys &K
                 box_muller_f32(w.x, w.y, k.bm, nrs, cs, sn);
             else
                 box_muller_f32(w.z, w.w, k.bm, nrs, cs, sn);
-            em_step_f32(k, nrs, (j & 1) ? sn : cs, S.y[q], S.yacc[q], S.v[q], S.e[q]);
+            em_step_f32(k, nrs, (j & 1) ? sn : cs, S.pb[q], S.yacc[q], S.v[q], S.e[q]);
         } else {
             const double z = normal_from_block_f64(w, j);
             em_step<double>(k, k.sigma * z, S.y[q], S.yacc[q], S.v[q], S.e[q]);
@@ -194,15 +195,15 @@ __device__ __forceinline__ void group_step(const Coef<R> &k, const RoundKeys &K,
 #pragma unroll
         for (int q = 0; q < PPT; ++q) box_muller_f32(w[q].x, w[q].y, k.bm, nr[q], cs[q], sn[q]);
 #pragma unroll
-        for (int q = 0; q < PPT; ++q) em_step_f32(k, nr[q], cs[q], S.y[q], S.yacc[q], S.v[q], S.e[q]);
+        for (int q = 0; q < PPT; ++q) em_step_f32(k, nr[q], cs[q], S.pb[q], S.yacc[q], S.v[q], S.e[q]);
 #pragma unroll
-        for (int q = 0; q < PPT; ++q) em_step_f32(k, nr[q], sn[q], S.y[q], S.yacc[q], S.v[q], S.e[q]);
+        for (int q = 0; q < PPT; ++q) em_step_f32(k, nr[q], sn[q], S.pb[q], S.yacc[q], S.v[q], S.e[q]);
 #pragma unroll
         for (int q = 0; q < PPT; ++q) box_muller_f32(w[q].z, w[q].w, k.bm, nr[q], cs[q], sn[q]);
 #pragma unroll
-        for (int q = 0; q < PPT; ++q) em_step_f32(k, nr[q], cs[q], S.y[q], S.yacc[q], S.v[q], S.e[q]);
+        for (int q = 0; q < PPT; ++q) em_step_f32(k, nr[q], cs[q], S.pb[q], S.yacc[q], S.v[q], S.e[q]);
 #pragma unroll
-        for (int q = 0; q < PPT; ++q) em_step_f32(k, nr[q], sn[q], S.y[q], S.yacc[q], S.v[q], S.e[q]);
+        for (int q = 0; q < PPT; ++q) em_step_f32(k, nr[q], sn[q], S.pb[q], S.yacc[q], S.v[q], S.e[q]);
     } else {
 #pragma unroll
         for (int q = 0; q < PPT; ++q) {
@@ -241,7 +242,10 @@ __device__ __forceinline__ void advance(const Coef<R> &k, const RoundKeys &K, Sl
         }
         if ((blk_end & (kBlockSteps - 1)) == 0) {
 #pragma unroll
-            for (int q = 0; q < PPT; ++q) fold_position<R>(S.y[q], S.yacc[q], S.ylo[q], S.cell[q]);
+            for (int q = 0; q < PPT; ++q) {
+                fold_position<R>(S.y[q], S.yacc[q], S.ylo[q], S.cell[q]);
+                if constexpr (sizeof(R) == 4) S.pb[q] = phase_base(S.y[q]);
+            }
         }
     }
 }
@@ -281,6 +285,7 @@ __device__ __forceinline__ void run_tile(const Batch &b, const State &st, const 
         S.v[q] = __ldcg(&s.v[idx[q]]);
         S.e[q] = __ldcg(&s.e[idx[q]]);
         S.cell[q] = __ldcg(&s.cell[idx[q]]);
+        if constexpr (sizeof(R) == 4) S.pb[q] = phase_base(S.y[q]);
         S.ss[q] = step_stream((uint64_t)idx[q] + nz.traj_base, K);
     }
 
