@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--small", action="store_true",
                     help="the sweep grid at 2,000 steps (profiling and quick checks; not a bench line)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the pathwise-adjoint leg")
+    ap.add_argument("--visualisation", action="store_true",
+                    help="also measure the per-cycle cost of reading intermediate results (iterations lost)")
     return ap.parse_args()
 
 
@@ -292,6 +294,50 @@ def adjoint_leg(A, stream, small=False):
             "accuracy": acc}
 
 
+# ----------------------------------------------------------------------------- visualisation leg
+
+def visualisation_leg(A, stream):
+    """The cost of looking at intermediate results, in the form of the paper's Table 1
+    (Sec. 3.2): the number of iterations that could have run in the time a display cycle
+    spends outside the integration.  Work items = parameter sets of the load sweep (one
+    trajectory each, as the paper's work items); a cycle integrates T steps, reduces the
+    ensemble (the mean-velocity-versus-load curve, Fig. 2) and waits for it.  'device': the
+    result stays in device memory (the analogue of shared CL/GL buffers); 'host': it is copied
+    into pinned host memory every cycle (the analogue of the non-shared method).  Cycle time
+    is fitted linearly in T; offset / slope = iterations lost."""
+    import numpy as np
+    import torch
+    from paper_1104_2499_gb300 import workloads as W
+
+    out = {}
+    Ts = [250, 500, 1000, 2000, 4000]
+    reps = 20
+    for n_items in (64, 8192):
+        w = W.force_sweep(n_F=n_items, traj_per_set=1, n_steps=(sum(Ts) * reps) + 1000)
+        res = {}
+        with A.Ensemble(w, stream=stream) as ens, torch.cuda.stream(stream):
+            ens.set_params()
+            ens.integrate(1000)  # warm-up
+            mom_d = torch.empty((n_items, 8), dtype=torch.float64, device="cuda")
+            mom_h = torch.empty((n_items, 8), dtype=torch.float64, pin_memory=True)
+            for method, dst in (("device", mom_d), ("host", mom_h)):
+                xs, ys = [], []
+                for T in Ts:
+                    stream.synchronize()
+                    t0 = time.perf_counter()
+                    for _ in range(reps // 2):
+                        A.abp_integrate(ens.ctx, T)
+                        A.abp_reduce(ens.ctx, dst, None, None)
+                        stream.synchronize()
+                    xs.append(T)
+                    ys.append((time.perf_counter() - t0) / (reps // 2))
+                slope, offset = np.polyfit(np.array(xs, float), np.array(ys), 1)
+                res[method] = {"us_per_iteration": slope * 1e6, "offset_us": offset * 1e6,
+                               "iterations_lost": offset / slope}
+        out["%d_work_items" % n_items] = res
+    return out
+
+
 # ----------------------------------------------------------------------------- GPU arm
 
 def main():
@@ -455,6 +501,7 @@ def main():
     adj = None
     if rank == 0 and world == 1 and not args.no_adjoint:
         adj = adjoint_leg(A, stream, small=args.small)
+    vis = visualisation_leg(A, stream) if (rank == 0 and args.visualisation) else None
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -467,7 +514,7 @@ def main():
                                                 "integrator_launches_per_step": n_launch,
                                                 "parallelism": "dp%d (independent replicas)" % world}),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
-                "adjoint": adj,
+                "adjoint": adj, "visualisation": vis,
                 "wall_s_timed": wall, "sm_count": n_sm, "device": props.name}
         print(json.dumps(line), flush=True)
     ens.close()
