@@ -209,6 +209,10 @@ ABP_API abp_status abp_test_hold_tile(abp_ctx *ctx, int32_t tile);
 ABP_API abp_status abp_tuning(const abp_ctx *ctx, int32_t *schedule, int32_t *particles_per_thread,
                               int64_t *steps_per_item, int32_t *blocks);
 
+/* Tiling of the current batch (host outputs, any may be NULL): tiles in all, and
+ * how many of them are packed (several small sets sharing one block). */
+ABP_API abp_status abp_tiles(const abp_ctx *ctx, int32_t *n_tiles, int32_t *n_packed);
+
 /* Number of kernels this context has enqueued since it was created (host output). */
 ABP_API abp_status abp_kernel_launches(const abp_ctx *ctx, int64_t *launches);
 

@@ -89,6 +89,8 @@ def lib():
         L.abp_tuning.argtypes = [_VP, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int64),
                                  C.POINTER(C.c_int32)]
         L.abp_tuning.restype = st
+        L.abp_tiles.argtypes = [_VP, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+        L.abp_tiles.restype = st
         L.abp_integrate.argtypes = [_VP, C.c_int64]
         L.abp_integrate.restype = st
         L.abp_progress.argtypes = [_VP, C.POINTER(C.c_int64)]
@@ -187,6 +189,12 @@ def abp_tuning(ctx):
     sc, p, s, b = C.c_int32(), C.c_int32(), C.c_int64(), C.c_int32()
     _check(lib().abp_tuning(ctx, C.byref(sc), C.byref(p), C.byref(s), C.byref(b)), ctx)
     return {"schedule": sc.value, "particles_per_thread": p.value, "steps_per_item": s.value, "blocks": b.value}
+
+
+def abp_tiles(ctx):
+    t, p = C.c_int32(), C.c_int32()
+    _check(lib().abp_tiles(ctx, C.byref(t), C.byref(p)), ctx)
+    return {"tiles": t.value, "packed": p.value}
 
 
 def abp_integrate(ctx, max_steps: int = -1):
@@ -330,6 +338,9 @@ class Ensemble:
 
     def tuning(self) -> dict:
         return abp_tuning(self.ctx)
+
+    def tiles(self) -> dict:
+        return abp_tiles(self.ctx)
 
     def integrate(self, max_steps: int = -1):
         abp_integrate(self.ctx, max_steps)

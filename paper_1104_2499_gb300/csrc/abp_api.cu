@@ -192,6 +192,9 @@ void measure_candidates(abp_ctx *ctx, TuneTable &tt) {
         Batch b;
         b.n_sets = 1;
         b.n_tiles = nt;
+        b.n_single = nt;
+        b.set_first = nullptr;
+        b.set_packed = nullptr;
         b.total_traj = T;
         b.params = d_prm;
         b.set_steps = d_steps;
@@ -470,23 +473,60 @@ abp_status abp_set_params(abp_ctx *ctx, int32_t n_sets, const abp_params *sets, 
     ctx->g = 0;
     ctx->ckpt_complete = true;
 
-    // Tiles: contiguous runs of at most kThreads * ppt trajectories of one set.
+    // Tiles: contiguous runs of at most kThreads * ppt trajectories of one set,
+    // then -- lockstep schedule, no adjoint checkpoints -- packed tiles: groups of
+    // consecutive small sets (fewer than kThreads trajectories each, equal step
+    // counts) sharing one block, one trajectory per thread.
     autotune(ctx);
     const int64_t tile = (int64_t)kThreads * ctx->ppt;
+    const bool can_pack = ctx->sched == 1 && ctx->cfg.checkpoint_every == 0;
+    ctx->set_first.assign((size_t)n_sets + 1, 0);
+    for (int32_t i = 0; i < n_sets; ++i) ctx->set_first[i + 1] = ctx->set_first[i] + n_traj[i];
+    ctx->set_packed.assign((size_t)n_sets, 0);
+    std::vector<std::pair<int32_t, int32_t>> groups;  // [first set, end set) of each packed tile
+    if (can_pack) {
+        int32_t i = 0;
+        while (i < n_sets) {
+            if (n_traj[i] <= 0 || n_traj[i] >= kThreads) {
+                ++i;
+                continue;
+            }
+            int32_t j = i, nonempty = 0;
+            int64_t cnt = 0;
+            while (j < n_sets && (n_traj[j] == 0 || (n_traj[j] < kThreads && n_steps[j] == n_steps[i])) &&
+                   cnt + n_traj[j] <= kThreads) {
+                cnt += n_traj[j];
+                nonempty += n_traj[j] > 0 ? 1 : 0;
+                ++j;
+            }
+            if (nonempty >= 2) {
+                groups.emplace_back(i, j);
+                for (int32_t k = i; k < j; ++k) ctx->set_packed[k] = n_traj[k] > 0 ? 1 : 0;
+            }
+            i = j > i ? j : i + 1;
+        }
+    }
     ctx->set_tile_begin.assign(1, 0);
     ctx->tile_first.clear();
     ctx->tile_count.clear();
     ctx->tile_set.clear();
-    int64_t base = 0;
     for (int32_t i = 0; i < n_sets; ++i) {
-        for (int64_t off = 0; off < n_traj[i]; off += tile) {
-            ctx->tile_first.push_back(base + off);
-            ctx->tile_count.push_back((int32_t)std::min(tile, n_traj[i] - off));
-            ctx->tile_set.push_back(i);
-        }
-        if (ctx->tile_first.size() > (size_t)INT32_MAX - 1) return fail(ctx, ABP_EINVAL, "too many tiles");
+        if (!ctx->set_packed[i])
+            for (int64_t off = 0; off < n_traj[i]; off += tile) {
+                ctx->tile_first.push_back(ctx->set_first[i] + off);
+                ctx->tile_count.push_back((int32_t)std::min(tile, n_traj[i] - off));
+                ctx->tile_set.push_back(i);
+            }
+        if (ctx->tile_first.size() > (size_t)INT32_MAX / 2) return fail(ctx, ABP_EINVAL, "too many tiles");
         ctx->set_tile_begin.push_back((int32_t)ctx->tile_first.size());
-        base += n_traj[i];
+    }
+    ctx->n_single = (int32_t)ctx->tile_first.size();
+    for (const auto &gr : groups) {
+        int32_t lead = gr.first;
+        while (n_traj[lead] == 0) ++lead;  // the first non-empty set carries the group's step count
+        ctx->tile_first.push_back(ctx->set_first[gr.first]);
+        ctx->tile_count.push_back((int32_t)(ctx->set_first[gr.second] - ctx->set_first[gr.first]));
+        ctx->tile_set.push_back(lead);
     }
     ctx->n_tiles = (int32_t)ctx->tile_first.size();
     const abp_config &c = ctx->cfg;
@@ -540,6 +580,8 @@ abp_status abp_set_params(abp_ctx *ctx, int32_t n_sets, const abp_params *sets, 
     ALLOC(d_moments, sizeof(double) * 8 * (size_t)std::max(n_sets, 1), "moments");
     ALLOC(d_queue, sizeof(int32_t) * ((size_t)ctx->n_tiles + 1), "work queue");
     ALLOC(d_perm, sizeof(int32_t) * (size_t)std::max(ctx->n_tiles, 1), "work queue order");
+    ALLOC(d_set_first, sizeof(int64_t) * ((size_t)n_sets + 1), "set offsets");
+    ALLOC(d_set_packed, sizeof(int32_t) * (size_t)std::max(n_sets, 1), "packed sets");
 #undef ALLOC
 
     cudaStream_t s = ctx->stream;
@@ -553,6 +595,8 @@ abp_status abp_set_params(abp_ctx *ctx, int32_t n_sets, const abp_params *sets, 
     if (e == cudaSuccess) e = up(ctx->d_tile_count, ctx->tile_count.data(), sizeof(int32_t) * ctx->n_tiles);
     if (e == cudaSuccess) e = up(ctx->d_tile_set, ctx->tile_set.data(), sizeof(int32_t) * ctx->n_tiles);
     if (e == cudaSuccess) e = up(ctx->d_perm, ctx->perm.data(), sizeof(int32_t) * ctx->n_tiles);
+    if (e == cudaSuccess) e = up(ctx->d_set_first, ctx->set_first.data(), sizeof(int64_t) * (n_sets + 1));
+    if (e == cudaSuccess) e = up(ctx->d_set_packed, ctx->set_packed.data(), sizeof(int32_t) * n_sets);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_status.p, 0, sizeof(int32_t), s);
     if (e == cudaSuccess && ctx->d_hx.bytes) e = cudaMemsetAsync(ctx->d_hx.p, 0, ctx->d_hx.bytes, s);
     if (e == cudaSuccess && ctx->d_hv.bytes) e = cudaMemsetAsync(ctx->d_hv.p, 0, ctx->d_hv.bytes, s);
@@ -728,6 +772,13 @@ abp_status abp_integrate(abp_ctx *ctx, int64_t max_steps) {
     const abp_status st = run_window(ctx, ctx->g, target);
     if (st != ABP_OK) return st;
     ctx->g = target;
+    return ABP_OK;
+}
+
+abp_status abp_tiles(const abp_ctx *ctx, int32_t *n_tiles, int32_t *n_packed) {
+    if (!ctx) return ABP_EINVAL;
+    if (n_tiles) *n_tiles = ctx->n_tiles;
+    if (n_packed) *n_packed = ctx->n_tiles - ctx->n_single;
     return ABP_OK;
 }
 

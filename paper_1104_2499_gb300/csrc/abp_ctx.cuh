@@ -78,11 +78,12 @@ struct abp_ctx {
     int64_t launches = 0;  // kernels enqueued by this context
     std::vector<abp_params> params;
     std::vector<int64_t> n_traj, n_steps;
-    std::vector<int32_t> set_tile_begin, tile_count, tile_set;
-    std::vector<int64_t> tile_first;
+    std::vector<int32_t> set_tile_begin, tile_count, tile_set, set_packed;
+    std::vector<int64_t> tile_first, set_first;
+    int32_t n_single = 0;  // tiles [n_single, n_tiles) are packed
 
     // device
-    DevBuf d_params, d_steps, d_set_tile_begin, d_tile_first, d_tile_count, d_tile_set;
+    DevBuf d_params, d_steps, d_set_tile_begin, d_tile_first, d_tile_count, d_tile_set, d_set_first, d_set_packed;
     DevBuf d_y, d_yacc, d_ylo, d_v, d_e, d_y0, d_cell;
     DevBuf d_hx, d_hv, d_ckpt, d_partials, d_moments, d_status;
     DevBuf d_queue, d_round, d_perm;  // work queue: head + done[n_tiles]; round starts; tile order
@@ -92,7 +93,10 @@ struct abp_ctx {
         Batch b;
         b.n_sets = n_sets;
         b.n_tiles = n_tiles;
+        b.n_single = n_single;
         b.total_traj = total_traj;
+        b.set_first = n_single < n_tiles ? (const int64_t *)d_set_first.p : nullptr;
+        b.set_packed = n_single < n_tiles ? (const int32_t *)d_set_packed.p : nullptr;
         b.params = (const abp_params *)d_params.p;
         b.set_steps = (const int64_t *)d_steps.p;
         b.set_tile_begin = (const int32_t *)d_set_tile_begin.p;
@@ -157,7 +161,7 @@ struct abp_ctx {
     }
     void release_all() {
         drop_graphs();
-        for (DevBuf *b : {&d_queue, &d_round, &d_perm, &d_params, &d_steps, &d_set_tile_begin, &d_tile_first, &d_tile_count, &d_tile_set, &d_y,
+        for (DevBuf *b : {&d_queue, &d_round, &d_perm, &d_set_first, &d_set_packed, &d_params, &d_steps, &d_set_tile_begin, &d_tile_first, &d_tile_count, &d_tile_set, &d_y,
                           &d_yacc, &d_ylo, &d_v, &d_e, &d_y0, &d_cell, &d_hx, &d_hv, &d_ckpt, &d_partials,
                           &d_moments, &d_adj})
             b->release();

@@ -17,19 +17,24 @@ constexpr int kThreads = 256;
 // bitwise identical arithmetic.
 constexpr int kBlockSteps = 64;
 
-// One batch of parameter sets, tiled for the device.  A tile is a contiguous
-// run of at most kThreads * ppt trajectories of one set; tiles of a set are
-// consecutive.
+// One batch of parameter sets, tiled for the device.  Tiles [0, n_single) are
+// contiguous runs of at most kThreads * ppt trajectories of one set (the tiles
+// of a set are consecutive).  Tiles [n_single, n_tiles) are packed: each holds
+// at most kThreads trajectories of several small sets with equal step counts
+// (whole sets, consecutive in set order), one trajectory per thread.
 struct Batch {
     int32_t n_sets;
     int32_t n_tiles;
+    int32_t n_single;
     int64_t total_traj;
+    const int64_t *set_first;      // [n_sets + 1] first trajectory of each set (packed batches; else NULL)
+    const int32_t *set_packed;     // [n_sets] 1 if the set lives in a packed tile (else NULL)
     const abp_params *params;      // [n_sets]
     const int64_t *set_steps;      // [n_sets] steps to run
     const int32_t *set_tile_begin; // [n_sets + 1]
     const int64_t *tile_first;     // [n_tiles] first global trajectory id (= state index)
     const int32_t *tile_count;     // [n_tiles] trajectories in the tile (>= 1)
-    const int32_t *tile_set;       // [n_tiles]
+    const int32_t *tile_set;       // [n_tiles] the set (packed tile: its first set)
 };
 
 // Structure-of-arrays trajectory state.  Element type is float (fp64 = false)
@@ -90,7 +95,7 @@ cudaError_t launch_init(const Batch &b, const State &s, const Hist &h, const Ckp
                         cudaStream_t st);
 cudaError_t launch_integrate(const Batch &b, const State &s, const Hist &h, const Ckpt &c, const Noise &nz,
                              int ppt, int64_t g0, int64_t g1, cudaStream_t st);
-// partials: [n_tiles][4] scratch; sums: [n_sets][4]; moments: [n_sets][8] (may alias nothing).
+// partials: [n_tiles][4] scratch; moments: [n_sets][8].
 cudaError_t launch_reduce(const Batch &b, const State &s, const Noise &nz, int64_t g, double *partials,
                           double *moments, cudaStream_t st);
 cudaError_t launch_get_state(const Batch &b, const State &s, double dt, int64_t g, double *x, double *x0, double *v,

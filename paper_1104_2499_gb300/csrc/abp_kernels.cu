@@ -56,6 +56,20 @@ __device__ __forceinline__ double disp_periods(const SV<R> &s, int64_t t) {
     return (((double)s.cell[t] + (double)s.y[t]) + ((double)s.yacc[t] + (double)s.ylo[t])) - (double)s.y0[t];
 }
 
+// Set of trajectory t in a batch with packed tiles: the last set whose first
+// trajectory is <= t (empty sets share their first index with the next set).
+__device__ __forceinline__ int find_set(const Batch &b, int64_t t) {
+    int lo = 0, hi = b.n_sets - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (b.set_first[mid] <= t)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
 // ---------------------------------------------------------------- snapshots
 
 // Bin of the position fraction y (any real; wrapped here) into [0, bx).
@@ -101,17 +115,19 @@ __global__ void __launch_bounds__(kThreads) init_kernel(Batch b, State st, Hist 
     const SV<R> s = view<R>(st);
     const int tile = blockIdx.x;
     const int set = b.tile_set[tile];
+    const bool packed = tile >= b.n_single;  // several sets, one trajectory per thread
     const int64_t first = b.tile_first[tile];
     const int count = b.tile_count[tile];
-    const abp_params p = b.params[set];
     const bool snap0 = h.snap_every <= 0 && b.set_steps[set] == 0 && (h.bx > 0 || h.bv > 0);
     const int nb = h.bx + (h.bv > 0 ? h.bv + 2 : 0);
-    if (snap0) {
+    if (snap0 && !packed) {
         for (int i = threadIdx.x; i < nb; i += blockDim.x) sh[i] = 0;
         __syncthreads();
     }
     for (int li = threadIdx.x; li < count; li += blockDim.x) {
         const int64_t t = first + li;
+        const int my_set = packed ? find_set(b, t) : set;
+        const abp_params p = b.params[my_set];
         const uint4 w = noise_block(kInitCounter, (uint64_t)t + nz.traj_base, nz.k0, nz.k1);
         const R y0 = (R)(w.x >> 8) * (R)0x1p-24;
         R v0 = 0;
@@ -135,14 +151,20 @@ __global__ void __launch_bounds__(kThreads) init_kernel(Batch b, State st, Hist 
         s.cell[t] = 0;
         if (ck.every > 0 && sizeof(R) == 4) ck.ck[t] = make_float4((float)y0, 0.0f, (float)v0, 0.0f);
         if (snap0) {
-            if (h.bx > 0) atomicAdd(&sh[bin_x<R>(y0, h.bx)], 1u);
-            if (h.bv > 0) {
-                const R lo = (R)h.v_lo, hi = (R)h.v_hi;
-                atomicAdd(&sh[h.bx + bin_v<R>(v0, lo, hi, (R)(h.bv / (h.v_hi - h.v_lo)), h.bv)], 1u);
+            const R lo = (R)h.v_lo, hi = (R)h.v_hi;
+            if (!packed) {
+                if (h.bx > 0) atomicAdd(&sh[bin_x<R>(y0, h.bx)], 1u);
+                if (h.bv > 0) atomicAdd(&sh[h.bx + bin_v<R>(v0, lo, hi, (R)(h.bv / (h.v_hi - h.v_lo)), h.bv)], 1u);
+            } else {
+                if (h.bx > 0) atomicAdd(&h.x[(size_t)my_set * h.bx + bin_x<R>(y0, h.bx)], 1u);
+                if (h.bv > 0)
+                    atomicAdd(&h.v[(size_t)my_set * (h.bv + 2) +
+                                   bin_v<R>(v0, lo, hi, (R)(h.bv / (h.v_hi - h.v_lo)), h.bv)],
+                              1u);
             }
         }
     }
-    if (snap0) flush_hist(sh, h, 0, set, b.n_sets);
+    if (snap0 && !packed) flush_hist(sh, h, 0, set, b.n_sets);
 }
 
 // ---------------------------------------------------------------- integrator
@@ -255,21 +277,26 @@ __device__ __forceinline__ void advance(const Coef<R> &k, const RoundKeys &K, Sl
 // state), step it in registers, fill snapshot histograms and checkpoints, and
 // store it back.  Must be reached by every thread of the block; `sh` holds
 // zeros on entry (when histograms are on) and on exit.
-template <typename R, int PPT>
+// PACKED: a packed tile (several sets of equal step count, PPT 1): each thread
+// takes the coefficients of its own trajectory's set, and histograms go to
+// global memory directly.
+template <typename R, int PPT, bool PACKED = false>
 __device__ __forceinline__ void run_tile(const Batch &b, const State &st, const Hist &h, const Ckpt &ck,
                                          const Noise &nz, const RoundKeys &K, uint32_t *sh, int tile, int64_t w0,
                                          int64_t w1) {
-    const int set = b.tile_set[tile];
-    const int64_t N = b.set_steps[set];
+    static_assert(!PACKED || PPT == 1, "packed tiles hold one trajectory per thread");
+    const int64_t first = b.tile_first[tile];
+    const int count = b.tile_count[tile];
+    const int set_t = b.tile_set[tile];
+    const int64_t N = b.set_steps[set_t];
     const int64_t n_begin = min(w0, N);
     const int64_t n_end = min(w1, N);
     if (n_begin >= n_end) return;  // uniform over the block
 
     const SV<R> s = view<R>(st);
+    const int set = PACKED ? find_set(b, first + min((int)threadIdx.x, count - 1)) : set_t;
     const abp_params p = b.params[set];
     const Coef<R> k = make_coef<R>(p.q, p.c, p.d, p.gamma0, p.F0, p.D, p.h, p.L, p.asym, nz.dt);
-    const int64_t first = b.tile_first[tile];
-    const int count = b.tile_count[tile];
 
     Slots<R, PPT> S;
     int64_t idx[PPT];
@@ -308,13 +335,22 @@ __device__ __forceinline__ void run_tile(const Batch &b, const State &st, const 
         n = seg_end;
         if (hist && (h.snap_every > 0 ? (n % h.snap_every == 0) : (n == N))) {
             const int64_t snap = h.snap_every > 0 ? n / h.snap_every - 1 : 0;
+            if constexpr (PACKED) {
+                if (act[0]) {
+                    const size_t row = (size_t)snap * b.n_sets + set;
+                    if (h.bx > 0) atomicAdd(&h.x[row * h.bx + bin_x<R>(S.y[0] + S.yacc[0], h.bx)], 1u);
+                    if (h.bv > 0)
+                        atomicAdd(&h.v[row * (h.bv + 2) + bin_v<R>(S.v[0], v_lo, v_hi, v_scale, h.bv)], 1u);
+                }
+            } else {
 #pragma unroll
-            for (int q = 0; q < PPT; ++q) {
-                if (!act[q]) continue;
-                if (h.bx > 0) atomicAdd(&sh[bin_x<R>(S.y[q] + S.yacc[q], h.bx)], 1u);
-                if (h.bv > 0) atomicAdd(&sh[h.bx + bin_v<R>(S.v[q], v_lo, v_hi, v_scale, h.bv)], 1u);
+                for (int q = 0; q < PPT; ++q) {
+                    if (!act[q]) continue;
+                    if (h.bx > 0) atomicAdd(&sh[bin_x<R>(S.y[q] + S.yacc[q], h.bx)], 1u);
+                    if (h.bv > 0) atomicAdd(&sh[h.bx + bin_v<R>(S.v[q], v_lo, v_hi, v_scale, h.bv)], 1u);
+                }
+                flush_hist(sh, h, snap, set, b.n_sets);
             }
-            flush_hist(sh, h, snap, set, b.n_sets);
         }
         if (ck.every > 0 && n % ck.every == 0 && sizeof(R) == 4) {
             const int64_t slot = n / ck.every;
@@ -347,12 +383,12 @@ __device__ __forceinline__ void zero_hist(uint32_t *sh, const Hist &h) {
 }
 
 // Lockstep schedule: one block per tile, every tile over the window [g0, g1).
-template <typename R, int PPT>
+template <typename R, int PPT, bool PACKED>
 __global__ void ABP_INTEGRATE_BOUNDS integrate_kernel(Batch b, State st, Hist h, Ckpt ck, Noise nz,
                                                      KeyParam kp, int64_t g0, int64_t g1) {
     extern __shared__ uint32_t sh[];
-    zero_hist(sh, h);
-    run_tile<R, PPT>(b, st, h, ck, nz, kp.K, sh, blockIdx.x, g0, g1);
+    if constexpr (!PACKED) zero_hist(sh, h);
+    run_tile<R, PPT, PACKED>(b, st, h, ck, nz, kp.K, sh, (PACKED ? b.n_single : 0) + (int)blockIdx.x, g0, g1);
 }
 
 __device__ __forceinline__ uint64_t global_ns() {
@@ -467,6 +503,7 @@ __global__ void __launch_bounds__(kThreads) tile_reduce_kernel(Batch b, State st
     __shared__ double red[kThreads / 32][4];
     const SV<R> s = view<R>(st);
     const int tile = blockIdx.x;
+    if (tile >= b.n_single) return;  // packed sets are reduced directly by set_reduce_kernel
     const int set = b.tile_set[tile];
     const int64_t n = min(g, b.set_steps[set]);
     const double L = b.params[set].L;
@@ -490,20 +527,39 @@ __global__ void __launch_bounds__(kThreads) tile_reduce_kernel(Batch b, State st
 }
 
 // Per set: fixed-order sum of its tiles' partials and the derived moments.
-__global__ void __launch_bounds__(kThreads) set_reduce_kernel(Batch b, double dt, int64_t g, const double *partials,
-                                                              double *moments) {
+// Per set: fixed-order sum of its tiles' partials -- or, for a set in a packed
+// tile, of its trajectories directly -- and the derived moments.
+template <typename R>
+__global__ void __launch_bounds__(kThreads) set_reduce_kernel(Batch b, State st, double dt, int64_t g,
+                                                              const double *partials, double *moments) {
     __shared__ double red[kThreads / 32][4];
     const int set = blockIdx.x;
-    const int t0 = b.set_tile_begin[set], t1 = b.set_tile_begin[set + 1];
+    const int64_t n = min(g, b.set_steps[set]);
     double a[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x)
+    int64_t M = 0;
+    if (b.set_packed && b.set_packed[set]) {
+        const SV<R> s = view<R>(st);
+        const double L = b.params[set].L;
+        const double inv_T = n > 0 ? 1.0 / ((double)n * dt) : 0.0;
+        const int64_t t0 = b.set_first[set], t1 = b.set_first[set + 1];
+        M = t1 - t0;
+        for (int64_t t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+            const double dx = L * disp_periods<R>(s, t);
+            const double vbar = dx * inv_T;
+            a[0] += vbar;
+            a[1] += vbar * vbar;
+            a[2] += dx;
+            a[3] += dx * dx;
+        }
+    } else {
+        const int t0 = b.set_tile_begin[set], t1 = b.set_tile_begin[set + 1];
+        for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) a[j] += partials[(size_t)t * 4 + j];
+            for (int j = 0; j < 4; ++j) a[j] += partials[(size_t)t * 4 + j];
+        for (int t = t0; t < t1; ++t) M += b.tile_count[t];
+    }
     block_sum4(a, red);
     if (threadIdx.x == 0) {
-        int64_t M = 0;
-        for (int t = t0; t < t1; ++t) M += b.tile_count[t];
-        const int64_t n = min(g, b.set_steps[set]);
         double *o = moments + (size_t)set * 8;
         const double Md = (double)M;
         const double mean_v = M > 0 ? a[0] / Md : 0.0;
@@ -525,13 +581,14 @@ __global__ void __launch_bounds__(kThreads) get_state_kernel(Batch b, State st, 
                                                              double *x0, double *v, double *e, double *vbar) {
     const SV<R> s = view<R>(st);
     const int tile = blockIdx.x;
-    const int set = b.tile_set[tile];
-    const int64_t n = min(g, b.set_steps[set]);
-    const double L = b.params[set].L;
+    const bool packed = tile >= b.n_single;
     const int64_t first = b.tile_first[tile];
     const int count = b.tile_count[tile];
     for (int li = threadIdx.x; li < count; li += blockDim.x) {
         const int64_t t = first + li;
+        const int set = packed ? find_set(b, t) : b.tile_set[tile];
+        const int64_t n = min(g, b.set_steps[set]);
+        const double L = b.params[set].L;
         const double x0t = L * (double)s.y0[t];
         const double dx = L * disp_periods<R>(s, t);
         if (x) x[t] = x0t + dx;
@@ -594,12 +651,15 @@ template <typename R, int PPT>
 cudaError_t launch_integrate_t(const Batch &b, const State &s, const Hist &h, const Ckpt &c, const Noise &nz,
                                int64_t g0, int64_t g1, cudaStream_t st) {
     const size_t smem = hist_smem(h);
-    auto kern = integrate_kernel<R, PPT>;
+    auto kern = integrate_kernel<R, PPT, false>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    kern<<<b.n_tiles, kThreads, smem, st>>>(b, s, h, c, nz, key_param(nz.k0, nz.k1), g0, g1);
+    if (b.n_single > 0) kern<<<b.n_single, kThreads, smem, st>>>(b, s, h, c, nz, key_param(nz.k0, nz.k1), g0, g1);
+    if (b.n_tiles > b.n_single)  // packed tiles: one trajectory per thread, histograms in global memory
+        integrate_kernel<R, 1, true><<<b.n_tiles - b.n_single, kThreads, 0, st>>>(b, s, h, c, nz,
+                                                                                  key_param(nz.k0, nz.k1), g0, g1);
     return cudaGetLastError();
 }
 
@@ -687,7 +747,10 @@ cudaError_t launch_reduce(const Batch &b, const State &s, const Noise &nz, int64
         else
             tile_reduce_kernel<float><<<b.n_tiles, kThreads, 0, st>>>(b, s, nz.dt, g, partials);
     }
-    set_reduce_kernel<<<b.n_sets, kThreads, 0, st>>>(b, nz.dt, g, partials, moments);
+    if (s.fp64)
+        set_reduce_kernel<double><<<b.n_sets, kThreads, 0, st>>>(b, s, nz.dt, g, partials, moments);
+    else
+        set_reduce_kernel<float><<<b.n_sets, kThreads, 0, st>>>(b, s, nz.dt, g, partials, moments);
     return cudaGetLastError();
 }
 

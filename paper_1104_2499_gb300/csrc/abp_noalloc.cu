@@ -177,6 +177,9 @@ extern "C" abp_status abp_run_set_noalloc(const abp_params *params, const abp_co
     Batch b;
     b.n_sets = 1;
     b.n_tiles = n_tiles;
+    b.n_single = n_tiles;
+    b.set_first = nullptr;
+    b.set_packed = nullptr;
     b.total_traj = n_traj;
     b.params = (const abp_params *)(base + kOffParams);
     b.set_steps = (const int64_t *)(base + kOffSteps);

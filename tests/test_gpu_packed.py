@@ -1,0 +1,102 @@
+"""Packed tiles: many small parameter sets (the paper's work items, one or a few
+trajectories per parameter value) share blocks.  The packed layout must give bitwise the
+state, moments and histograms of the one-set-per-tile layout (the work-queue schedule never
+packs), and packed sets must match the FP64 oracle trajectory by trajectory."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1104_2499_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def abp():
+    from paper_1104_2499_gb300 import abp as A
+    from paper_1104_2499_gb300 import build as B
+
+    B.build()
+    A.lib()
+    return A
+
+
+def mixed_batch(seed=3, steps=1200):
+    rng = np.random.default_rng(seed)
+    sets, M, N = [], [], []
+    for i in range(260):  # small sets, a few step counts, some empty
+        sets.append(W._with(D=float(np.exp(rng.uniform(-5, 0))), F0=float(rng.uniform(-0.5, 0.5)),
+                            asym=float(rng.uniform(0, 0.5))))
+        M.append(int(rng.integers(0, 40)) if i % 17 else 0)
+        N.append(steps if i < 200 else steps // 2)
+    sets += [W._with(D=0.1), W._with(D=0.3, q=2.0)]  # two large sets
+    M += [700, 300]
+    N += [steps, steps - 7]
+    return W.Workload(name="mixed", sets=sets, n_traj=M, n_steps=N, dt=1e-3, seed=seed, v0_mode=1,
+                      hist_x_bins=16, hist_v_bins=8, v_lo=-2.0, v_hi=2.0, snapshot_every=400)
+
+
+def run(A, w, **kw):
+    with A.Ensemble(w, **kw) as ens:
+        ens.run()
+        res, st, tiles = ens.results(), ens.state(), ens.tiles()
+        torch.cuda.synchronize()
+        return res, st, tiles
+
+
+def test_packed_layout_is_bitwise_the_unpacked_one(abp):
+    w = mixed_batch()
+    ra, sa, ta = run(abp, w, schedule=1)
+    rb, sb, tb = run(abp, w, schedule=2)
+    assert ta["packed"] > 0 and tb["packed"] == 0
+    for k in sa:
+        assert torch.equal(sa[k], sb[k]), k
+    for k in ra:
+        assert torch.equal(ra[k], rb[k]), k
+
+
+def test_packed_sets_against_oracle(abp):
+    w = mixed_batch(seed=4, steps=1000)
+    res, st, t = run(abp, w, schedule=1)
+    assert t["packed"] > 0
+    gs = {k: a.cpu().numpy() for k, a in st.items()}
+    hx = res["hist_x"].cpu().numpy()
+    base = w.traj_base()
+    checked = 0
+    for i in range(0, 200, 7):
+        if w.n_traj[i] == 0:
+            continue
+        p = w.sets[i]
+        r = O.run_set(p, seed=w.seed, dt=w.dt, n_traj=w.n_traj[i], n_steps=w.n_steps[i], traj_base=base[i],
+                      v0_mode=w.v0_mode, want_states=True, snapshot_every=w.snapshot_every, hist_x_bins=16)
+        sl = slice(base[i], base[i] + w.n_traj[i])
+        sv = math.sqrt(p["D"] / p["gamma0"])
+        for key, sc in (("x", p["L"]), ("x0", p["L"]), ("v", sv), ("e", p["q"] / p["c"])):
+            err = np.abs(gs[key][sl] - r[key]) / np.maximum(np.abs(r[key]), sc)
+            assert np.all(err <= 1e-4), (i, key, err.max())
+        bound = 1e-4 * max(sv, float(np.max(np.abs(r["vbar"]))))
+        assert np.all(np.abs(gs["vbar"][sl] - r["vbar"]) <= bound), i
+        assert np.all(hx[:, i].sum(1) == w.n_traj[i])
+        mv = res["moments"][i, 0].item()
+        if w.n_traj[i] > 1:  # mean over the same paths: FP32 against FP64 only
+            assert abs(mv - r["mean_v"]) <= 1e-4 * max(1.0, abs(r["mean_v"]))
+        checked += 1
+    assert checked >= 10
+
+
+def test_packed_zero_step_sets_snapshot_initial_state(abp):
+    sets = [W._with(D=0.1 * (i + 1)) for i in range(6)]
+    w = W.Workload(name="zero", sets=sets, n_traj=[3, 0, 5, 1, 7, 2], n_steps=[0] * 6, dt=1e-3, seed=8, v0_mode=1,
+                   hist_x_bins=8, hist_v_bins=4, v_lo=-1.0, v_hi=1.0)
+    res, st, t = run(abp, w, schedule=1)
+    rb, sb, tb = run(abp, w, schedule=2)
+    assert t["packed"] == 1 and tb["packed"] == 0
+    assert res["hist_x"].cpu().numpy()[0].sum(1).tolist() == w.n_traj
+    assert res["hist_v"].cpu().numpy()[0].sum(1).tolist() == w.n_traj
+    for k in st:
+        assert torch.equal(st[k], sb[k]), k
+    for k in res:
+        assert torch.equal(res[k], rb[k]), k
