@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the pathwise-adjoint leg")
     ap.add_argument("--visualisation", action="store_true",
                     help="also measure the per-cycle cost of reading intermediate results (iterations lost)")
+    ap.add_argument("--configs", default="",
+                    help="also time other workloads, comma-separated: single, uneven, force, heun, snapshots, "
+                         "precision, items (or 'all'); reported under 'configs'")
     return ap.parse_args()
 
 
@@ -338,6 +341,146 @@ def visualisation_leg(A, stream):
     return out
 
 
+# ----------------------------------------------------------------------------- other workloads
+
+def time_workload(A, stream, w, reps=1, **kw):
+    """Integrate and reduce workload ``w`` ``reps`` times from a fresh initial condition (inputs
+    resident on the device), timed with CUDA events on the library's stream."""
+    import torch
+
+    with A.Ensemble(w, stream=stream, **kw) as ens, torch.cuda.stream(stream):
+        ens.set_params()
+        ens.integrate(min(512, max(w.n_steps)))  # warm-up (first launches, autotuned choice)
+        ens.results()
+        times, res = [], None
+        for _ in range(reps):
+            ens.reset(w.seed)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ens.integrate(-1)
+            res = ens.results()
+            b.record(stream)
+            b.synchronize()
+            times.append(a.elapsed_time(b) * 1e-3)
+        t = statistics.median(times)
+        out = {"workload": w.name, "sets": w.n_sets, "trajectories": w.total_traj,
+               "particle_steps": w.particle_steps, "seconds": t, "value": w.particle_steps / t, "unit": UNIT,
+               "reps": reps, "tuning": ens.tuning(), "tiles": ens.tiles()}
+        return out, res
+
+
+def precision_leg(A, stream):
+    """FP32 state against FP64 state on the same noise: 1,048,576 trajectories x 10^5 steps of the
+    large-ensemble workload's parameters (D = 0.2, x0 uniform, v0 = e0 = 0, seed 4), final
+    1,024-bin histograms of x mod L and v.  Reports the difference of the ensemble means in
+    standard errors and the two-sample chi^2 of the histograms."""
+    import numpy as np
+    from paper_1104_2499_gb300 import workloads as W
+
+    w = W.shrink(W.large_snapshots(), max_traj=1 << 20, max_steps=100_000, name="precision_1Mx1e5")
+    w.snapshot_every = 0
+    r32, m32 = time_workload(A, stream, w, 1)
+    r64, m64 = time_workload(A, stream, w, 1, state_fp64=True)
+    a, b = m32["moments"].cpu().numpy()[0], m64["moments"].cpu().numpy()[0]
+    out = {"fp32": {"value": r32["value"], "mean_v": a[0], "se": a[1], "d_eff": a[3]},
+           "fp64": {"value": r64["value"], "mean_v": b[0], "se": b[1], "d_eff": b[3]},
+           "delta_mean_v_in_se": abs(a[0] - b[0]) / b[1], "d_eff_rel_diff": abs(a[3] - b[3]) / abs(b[3])}
+    for key in ("hist_x", "hist_v"):
+        h32 = m32[key].cpu().numpy()[-1, 0].astype(float)
+        h64 = m64[key].cpu().numpy()[-1, 0].astype(float)
+        k = (h32 + h64) > 0
+        chi2 = float((((h32 - h64) ** 2)[k] / (h32 + h64)[k]).sum())
+        out[key + "_chi2"] = {"chi2": chi2, "dof": int(k.sum()) - 1}
+        try:
+            from scipy import stats
+
+            out[key + "_chi2"]["p"] = float(stats.chi2.sf(chi2, int(k.sum()) - 1))
+        except Exception:
+            pass
+    return out
+
+
+def items_leg(A, stream):
+    """Time against the number of work items with the paper's protocol (Sec. 3.1): for every
+    power of two from 2^0 to 2^16 parameter sets of the load sweep (one trajectory each, the
+    paper's work items), 20 cycles of T steps each followed by the device reduction; the mean of
+    the last 15 cycles is reported, for T = 10^3 and T = 10^4."""
+    import torch
+    from paper_1104_2499_gb300 import workloads as W
+
+    out = []
+    for T in (1000, 10_000):
+        for k in range(0, 17):
+            n = 1 << k
+            w = W.force_sweep(n_F=n, traj_per_set=1, n_steps=20 * T)
+            with A.Ensemble(w, stream=stream) as ens, torch.cuda.stream(stream):
+                ens.set_params()
+                mom = torch.empty((n, 8), dtype=torch.float64, device="cuda")
+                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(20)]
+                for a, b in ev:
+                    a.record(stream)
+                    A.abp_integrate(ens.ctx, T)
+                    A.abp_reduce(ens.ctx, mom, None, None)
+                    b.record(stream)
+                stream.synchronize()
+                ms = statistics.mean(a.elapsed_time(b) for a, b in ev[5:])
+                tl = ens.tiles()
+            out.append({"steps": T, "work_items": n, "ms_per_cycle": ms, "value": n * T / (ms * 1e-3),
+                        "tiles": tl["tiles"], "packed_tiles": tl["packed"], "narrow": tl["narrow"]})
+    return out
+
+
+def force_leg(A, stream):
+    """The paper's benchmark observable (Fig. 2): mean velocity against the load F0, 64 values in
+    [-1, 1], 4,096 trajectories x 10^5 steps each.  Reports the curve, the stall force (where
+    <v> crosses zero, linear interpolation) and the efficiency -F0 <v> / q (power delivered
+    against the load per unit energy influx into the depot)."""
+    import numpy as np
+    from paper_1104_2499_gb300 import workloads as W
+
+    w = W.force_sweep()
+    r, res = time_workload(A, stream, w, 1)
+    mom = res["moments"].cpu().numpy()
+    F = np.array([p["F0"] for p in w.sets])
+    v, se = mom[:, 0], mom[:, 1]
+    stall = []
+    for i in range(len(F) - 1):
+        if v[i] == 0.0 or (v[i] < 0.0) != (v[i + 1] < 0.0):
+            stall.append(float(F[i] - v[i] * (F[i + 1] - F[i]) / (v[i + 1] - v[i])) if v[i + 1] != v[i] else float(F[i]))
+    eff = -F * v / np.array([p["q"] for p in w.sets])
+    r.update({"F0": F.tolist(), "mean_v": v.tolist(), "se": se.tolist(), "stall_force": stall,
+              "max_efficiency": float(eff.max()), "F0_at_max_efficiency": float(F[int(eff.argmax())])})
+    return r
+
+
+def configs_leg(A, stream, names):
+    from paper_1104_2499_gb300 import workloads as W
+
+    if names == ["all"]:
+        names = ["single", "uneven", "force", "heun", "precision", "items", "snapshots"]
+    out = {}
+    for name in names:
+        if name == "single":
+            out[name] = time_workload(A, stream, W.single_set(), 5)[0]
+        elif name == "uneven":
+            out[name] = time_workload(A, stream, W.uneven_batch(), 1)[0]
+        elif name == "force":
+            out[name] = force_leg(A, stream)
+        elif name == "snapshots":
+            out[name] = time_workload(A, stream, W.large_snapshots(), 1)[0]
+        elif name == "heun":
+            w = W.sweep_grid()
+            w.scheme, w.name = 1, w.name + "_heun"
+            out[name] = time_workload(A, stream, w, 1)[0]
+        elif name == "precision":
+            out[name] = precision_leg(A, stream)
+        elif name == "items":
+            out[name] = items_leg(A, stream)
+        else:
+            raise SystemExit("unknown workload in --configs: " + name)
+    return out
+
+
 # ----------------------------------------------------------------------------- GPU arm
 
 def main():
@@ -502,6 +645,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_adjoint:
         adj = adjoint_leg(A, stream, small=args.small)
     vis = visualisation_leg(A, stream) if (rank == 0 and args.visualisation) else None
+    cfgs = configs_leg(A, stream, [c for c in args.configs.split(",") if c]) if (rank == 0 and args.configs) else None
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -514,7 +658,7 @@ def main():
                                                 "integrator_launches_per_step": n_launch,
                                                 "parallelism": "dp%d (independent replicas)" % world}),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
-                "adjoint": adj, "visualisation": vis,
+                "adjoint": adj, "visualisation": vis, "configs": cfgs,
                 "wall_s_timed": wall, "sm_count": n_sm, "device": props.name}
         print(json.dumps(line), flush=True)
     ens.close()

@@ -111,6 +111,13 @@ typedef struct {
     uint64_t traj_base;          /* added to every global trajectory id: a process that runs
                                     one shard of a larger ensemble passes the id of its first
                                     trajectory, so every trajectory keeps its own noise */
+    int32_t scheme;              /* 0: explicit Euler-Maruyama, the step of Fig. 1 (all
+                                    right-hand sides at step n); 1: stochastic Heun -- predictor
+                                    s~ = s + a(s) dt + w, corrector s' = s + (a(s) + a(s~)) dt/2 + w
+                                    with the same noise increment w of the step (weak order 2 for
+                                    this additive noise; a variant the paper does not use).
+                                    Heun needs state_fp64 = 0 and checkpoint_every = 0 (no adjoint) */
+    int32_t reserved;            /* must be 0 */
 } abp_config;
 
 /* Create a context on the current CUDA device.  cuda_stream is a cudaStream_t
@@ -209,9 +216,12 @@ ABP_API abp_status abp_test_hold_tile(abp_ctx *ctx, int32_t tile);
 ABP_API abp_status abp_tuning(const abp_ctx *ctx, int32_t *schedule, int32_t *particles_per_thread,
                               int64_t *steps_per_item, int32_t *blocks);
 
-/* Tiling of the current batch (host outputs, any may be NULL): tiles in all, and
- * how many of them are packed (several small sets sharing one block). */
-ABP_API abp_status abp_tiles(const abp_ctx *ctx, int32_t *n_tiles, int32_t *n_packed);
+/* Tiling of the current batch (host outputs, any may be NULL): tiles in all, how
+ * many of them are packed (several small sets sharing one block), and the block
+ * width of a narrow lockstep launch (a batch with fewer tiles than SMs runs its
+ * tiles as several blocks of `narrow` threads each; 0 when not narrow).  The
+ * tiling never changes a result: state, moments and histograms are the same bits. */
+ABP_API abp_status abp_tiles(const abp_ctx *ctx, int32_t *n_tiles, int32_t *n_packed, int32_t *narrow);
 
 /* Number of kernels this context has enqueued since it was created (host output). */
 ABP_API abp_status abp_kernel_launches(const abp_ctx *ctx, int64_t *launches);

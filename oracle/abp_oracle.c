@@ -19,7 +19,9 @@
  *   kinematics        dx/dt = v
  * integrated by explicit Euler-Maruyama (all right-hand sides taken at step n),
  * with the Gaussian noise of Fig. 1 (a Box-Muller transformation) drawn from a
- * counter-based Philox4x32-10 stream keyed by (seed, trajectory, step).
+ * counter-based Philox4x32-10 stream keyed by (seed, trajectory, step); or, as
+ * a higher-order variant the paper does not use, by the stochastic Heun
+ * predictor-corrector on the same noise (or_heun_step).
  *
  * Readings of the paper taken where it is silent or garbled:
  *   - the trailing "{v}" after xi(t) in Eq. (velocity) is a typesetting
@@ -184,6 +186,42 @@ void or_em_step(const or_params *p, double dt, double z, double s[3])
     s[2] = e + dt * e_rate;
 }
 
+/* Right-hand side of the drift of Eqs. (ereservoir), (velocity) and dx/dt = v at
+ * s = (x, v, e): rate = (dx/dt, dv/dt, de/dt) without the noise. */
+static void drift(const or_params *p, const double s[3], double rate[3])
+{
+    const double x = s[0], v = s[1], e = s[2];
+    rate[0] = v;
+    rate[1] = p->F0 + p->d * e * v - p->gamma0 * v - or_potential_dx(p, x);
+    rate[2] = p->q - p->c * e - p->d * e * v * v;
+}
+
+/* One stochastic Heun step (the predictor-corrector, or improved Euler, scheme
+ * for an SDE with additive noise; Kloeden & Platen, Numerical Solution of
+ * Stochastic Differential Equations, 1992, Sec. 15.1): with the drift a(s) and
+ * the velocity's noise increment w = sqrt(2 D dt) z of step n (one Gaussian
+ * number, the same one the Euler-Maruyama step uses),
+ *   predictor  s~ = s + a(s) dt + (0, w, 0)
+ *   corrector  s' = s + (a(s) + a(s~)) dt / 2 + (0, w, 0).
+ * Not the paper's scheme (Fig. 1 names none); offered beside it as a
+ * higher-order variant.  *v_pred (may be NULL) receives the predictor's
+ * velocity, so that x advances by (v + v~) dt / 2. */
+void or_heun_step(const or_params *p, double dt, double z, double s[3], double *v_pred)
+{
+    const double w = sqrt(2.0 * p->D * dt) * z;
+    double a0[3], a1[3], sp[3];
+    drift(p, s, a0);
+    sp[0] = s[0] + dt * a0[0];
+    sp[1] = s[1] + dt * a0[1] + w;
+    sp[2] = s[2] + dt * a0[2];
+    drift(p, sp, a1);
+    s[0] = s[0] + 0.5 * dt * (a0[0] + a1[0]);
+    s[1] = s[1] + 0.5 * dt * (a0[1] + a1[1]) + w;
+    s[2] = s[2] + 0.5 * dt * (a0[2] + a1[2]);
+    if (v_pred)
+        *v_pred = sp[1];
+}
+
 /* Tangent-linear of or_em_step along parameter direction dth =
  * (dD, dq, dc, dd, dgamma0, dasym), acting on the tangent state t = (dx, dv, de)
  * at the (pre-step) primal state s. */
@@ -236,8 +274,8 @@ typedef struct {
     int32_t hist_x_bins;    /* 0: no position histogram */
     int32_t hist_v_bins;    /* 0: no velocity histogram */
     double v_lo, v_hi;
-    int32_t want_grad;
-    int32_t reserved;
+    int32_t want_grad;      /* Euler-Maruyama only */
+    int32_t scheme;         /* 0: Euler-Maruyama (the paper's), 1: stochastic Heun */
 } or_run_args;
 
 typedef struct {
@@ -320,14 +358,22 @@ static void *run_range(void *arg)
             snapshot(a, snap++, s, wk->hx, wk->hv);
         for (int64_t n = 0; n < a->n_steps; ++n) {
             const double z = or_normal(a->seed, traj, (uint64_t)n);
-            vsum += s[1];
-            if (a->want_grad) {
-                for (int j = 0; j < 6; ++j) {
-                    tsum[j] += t[j][1];
-                    tangent_step(p, a->dt, z, s, unit[j], t[j]);
+            if (a->scheme == 1) {
+                /* x advances by (v + v~) dt / 2: that is the step's velocity */
+                const double v_n = s[1];
+                double v_pred;
+                or_heun_step(p, a->dt, z, s, &v_pred);
+                vsum += 0.5 * (v_n + v_pred);
+            } else {
+                vsum += s[1];
+                if (a->want_grad) {
+                    for (int j = 0; j < 6; ++j) {
+                        tsum[j] += t[j][1];
+                        tangent_step(p, a->dt, z, s, unit[j], t[j]);
+                    }
                 }
+                or_em_step(p, a->dt, z, s);
             }
-            or_em_step(p, a->dt, z, s);
             const int64_t done = n + 1;
             if (a->snapshot_every > 0 ? (done % a->snapshot_every == 0) : (done == a->n_steps))
                 snapshot(a, snap++, s, wk->hx, wk->hv);
@@ -355,7 +401,8 @@ int or_run_set(const or_run_args *a, or_run_out *o)
 {
     if (!a || !o || a->n_traj < 0 || a->n_steps < 0 || !(a->dt > 0.0) || !(a->p.L > 0.0)
         || a->p.D < 0.0 || a->hist_x_bins < 0 || a->hist_v_bins < 0
-        || (a->hist_v_bins > 0 && !(a->v_hi > a->v_lo)))
+        || (a->hist_v_bins > 0 && !(a->v_hi > a->v_lo)) || a->scheme < 0 || a->scheme > 1
+        || (a->scheme == 1 && a->want_grad))
         return -1;
     const int64_t M = a->n_traj;
     const int64_t n_snap = or_n_snapshots(a->n_steps, a->snapshot_every);

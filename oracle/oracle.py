@@ -49,7 +49,7 @@ class RunArgs(C.Structure):
         ("v_lo", C.c_double),
         ("v_hi", C.c_double),
         ("want_grad", C.c_int32),
-        ("reserved", C.c_int32),
+        ("scheme", C.c_int32),
     ]
 
 
@@ -94,6 +94,7 @@ def lib():
         L.or_potential_dx.argtypes = [C.POINTER(Params), C.c_double]
         L.or_potential_dx.restype = C.c_double
         L.or_em_step.argtypes = [C.POINTER(Params), C.c_double, C.c_double, _PD]
+        L.or_heun_step.argtypes = [C.POINTER(Params), C.c_double, C.c_double, _PD, _PD]
         L.or_initial_state.argtypes = [C.POINTER(Params), C.c_uint64, C.c_int32, C.c_uint64, _PD]
         L.or_n_snapshots.argtypes = [C.c_int64, C.c_int64]
         L.or_n_snapshots.restype = C.c_int64
@@ -151,6 +152,14 @@ def em_step(params: dict, dt: float, z: float, state):
     return s[0], s[1], s[2]
 
 
+def heun_step(params: dict, dt: float, z: float, state):
+    """One stochastic Heun step; returns the new (x, v, e) and the predictor's velocity."""
+    s = (C.c_double * 3)(*state)
+    vp = C.c_double()
+    lib().or_heun_step(C.byref(make_params(**params)), dt, z, s, C.byref(vp))
+    return (s[0], s[1], s[2]), vp.value
+
+
 def initial_state(params: dict, seed: int, v0_mode: int, traj: int):
     s = (C.c_double * 3)()
     lib().or_initial_state(C.byref(make_params(**params)), seed, v0_mode, traj, s)
@@ -166,8 +175,11 @@ def n_snapshots(n_steps: int, snapshot_every: int) -> int:
 def run_set(params: dict, *, seed: int, dt: float, n_traj: int, n_steps: int, traj_base: int = 0,
             v0_mode: int = 0, snapshot_every: int = 0, hist_x_bins: int = 0, hist_v_bins: int = 0,
             v_lo: float = -5.0, v_hi: float = 5.0, want_states: bool = False, want_grad: bool = False,
-            want_traj_grad: bool = False, n_threads: int | None = None) -> dict:
+            want_traj_grad: bool = False, n_threads: int | None = None, scheme: int = 0) -> dict:
     """Integrate one parameter set's ensemble in FP64 and reduce it.
+
+    ``scheme`` 0 is the paper's explicit Euler-Maruyama step, 1 the stochastic Heun
+    predictor-corrector on the same noise (no gradient for it).
 
     Returns a dict with ``sums`` = (sum vbar, sum vbar^2, sum dx, sum dx^2), the derived
     ``mean_v``, ``se_v``, ``msd``, ``d_eff``, per-trajectory ``vbar`` and (optionally) the
@@ -182,6 +194,7 @@ def run_set(params: dict, *, seed: int, dt: float, n_traj: int, n_steps: int, tr
     a.n_threads = n_threads if n_threads else (os.cpu_count() or 1)
     a.hist_x_bins, a.hist_v_bins, a.v_lo, a.v_hi = hist_x_bins, hist_v_bins, v_lo, v_hi
     a.want_grad = 1 if (want_grad or want_traj_grad) else 0
+    a.scheme = int(scheme)
     o = RunOut()
     out: dict = {}
     keep = []

@@ -54,6 +54,8 @@ class abp_config(C.Structure):
         ("schedule", C.c_int32),
         ("steps_per_launch", C.c_int64),
         ("traj_base", C.c_uint64),
+        ("scheme", C.c_int32),
+        ("reserved", C.c_int32),
     ]
 
 
@@ -89,7 +91,7 @@ def lib():
         L.abp_tuning.argtypes = [_VP, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int64),
                                  C.POINTER(C.c_int32)]
         L.abp_tuning.restype = st
-        L.abp_tiles.argtypes = [_VP, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+        L.abp_tiles.argtypes = [_VP, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
         L.abp_tiles.restype = st
         L.abp_integrate.argtypes = [_VP, C.c_int64]
         L.abp_integrate.restype = st
@@ -192,9 +194,9 @@ def abp_tuning(ctx):
 
 
 def abp_tiles(ctx):
-    t, p = C.c_int32(), C.c_int32()
-    _check(lib().abp_tiles(ctx, C.byref(t), C.byref(p)), ctx)
-    return {"tiles": t.value, "packed": p.value}
+    t, p, n = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(lib().abp_tiles(ctx, C.byref(t), C.byref(p), C.byref(n)), ctx)
+    return {"tiles": t.value, "packed": p.value, "narrow": n.value}
 
 
 def abp_integrate(ctx, max_steps: int = -1):
@@ -270,7 +272,8 @@ def abp_version() -> str:
 # ----------------------------------------------------------------------- convenience
 
 def make_config(w: "W.Workload", *, state_fp64: bool = False, particles_per_thread: int = 0,
-                steps_per_launch: int = 0, traj_base: int = 0, schedule: int = 0) -> abp_config:
+                steps_per_launch: int = 0, traj_base: int = 0, schedule: int = 0,
+                scheme: int | None = None) -> abp_config:
     c = abp_config()
     c.seed = int(w.seed)
     c.dt = float(w.dt)
@@ -286,6 +289,7 @@ def make_config(w: "W.Workload", *, state_fp64: bool = False, particles_per_thre
     c.schedule = int(schedule)
     c.steps_per_launch = int(steps_per_launch)
     c.traj_base = int(traj_base)
+    c.scheme = int(w.scheme if scheme is None else scheme)
     return c
 
 
@@ -296,7 +300,7 @@ class Ensemble:
     """
 
     def __init__(self, w: "W.Workload", *, stream=None, state_fp64=False, particles_per_thread=0,
-                 steps_per_launch=0, traj_base=0, schedule=0, device=None):
+                 steps_per_launch=0, traj_base=0, schedule=0, scheme=None, device=None):
         import torch
 
         self.torch = torch
@@ -306,7 +310,7 @@ class Ensemble:
         with torch.cuda.device(self.device):
             self.ctx = abp_create(make_config(w, state_fp64=state_fp64, particles_per_thread=particles_per_thread,
                                               steps_per_launch=steps_per_launch, traj_base=traj_base,
-                                              schedule=schedule), stream)
+                                              schedule=schedule, scheme=scheme), stream)
         self._params_set = False
 
     def close(self):

@@ -25,7 +25,14 @@
 namespace abp {
 namespace {
 
-constexpr int kSub = 8;  // steps per register-resident sub-chunk
+#ifndef ABP_ADJ_SUB
+#define ABP_ADJ_SUB 8
+#endif
+#ifndef ABP_ADJ_MIN_BLOCKS
+#define ABP_ADJ_MIN_BLOCKS 2
+#endif
+constexpr int kSub = ABP_ADJ_SUB;  // steps per register-resident sub-chunk (a multiple of 4)
+static_assert(kSub % 4 == 0 && (kBlockSteps % kSub) == 0, "sub-chunks hold whole Philox blocks");
 
 struct AdjArgs {
     Batch b;
@@ -228,7 +235,7 @@ __device__ __forceinline__ void reverse_segment(const AdjArgs &a, const Coef<flo
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 2) adjoint_kernel(AdjArgs a) {
+__global__ void __launch_bounds__(kThreads, ABP_ADJ_MIN_BLOCKS) adjoint_kernel(AdjArgs a) {
     __shared__ double red[kThreads / 32][6];
     const Batch &b = a.b;
     const int tile = blockIdx.x;

@@ -115,10 +115,15 @@ struct TuneTable {
     bool done = false;
     float ms[3][3] = {};  // [schedule 1 = lockstep, 2 = work queue][ppt 1, 2, 4]
 };
-TuneTable g_tune[64][2];
+TuneTable g_tune[64][3];
+
+// Kind of integrator a timing table belongs to: 0 FP32 Euler-Maruyama, 1 FP64
+// state, 2 FP32 stochastic Heun.
+int tune_kind(const abp_ctx *ctx) { return ctx->cfg.state_fp64 ? 1 : (ctx->cfg.scheme == 1 ? 2 : 0); }
 
 void measure_candidates(abp_ctx *ctx, TuneTable &tt) {
     const int fp = ctx->cfg.state_fp64 ? 1 : 0;
+    const bool heun = ctx->cfg.scheme == 1;
     const int64_t T = (int64_t)std::max(ctx->sm_count, 1) * 4096;
     const int64_t warm = 256, steps = 2048;
     const size_t rsz = fp ? sizeof(double) : sizeof(float);
@@ -163,6 +168,7 @@ void measure_candidates(abp_ctx *ctx, TuneTable &tt) {
     Ckpt ck{};
     Noise nz{};
     nz.dt = 1e-3;
+    nz.scheme = heun ? 1 : 0;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -194,7 +200,10 @@ void measure_candidates(abp_ctx *ctx, TuneTable &tt) {
         b.n_tiles = nt;
         b.n_single = nt;
         b.set_first = nullptr;
-        b.set_packed = nullptr;
+        b.set_order = nullptr;
+        b.n_unpacked = 1;
+        b.narrow = 0;
+        b.sub_single = b.sub_packed = 1;
         b.total_traj = T;
         b.params = d_prm;
         b.set_steps = d_steps;
@@ -203,7 +212,7 @@ void measure_candidates(abp_ctx *ctx, TuneTable &tt) {
         b.tile_count = d_count;
         b.tile_set = d_tset;
         int bps = 0;
-        persistent_occupancy(fp != 0, c, 0, &bps);
+        persistent_occupancy(fp != 0, c, 0, &bps, heun);
         Queue q;
         q.head = d_queue;
         q.done = d_queue + 1;
@@ -263,8 +272,8 @@ std::string tune_key(const abp_ctx *ctx) {
         if (*c == ' ' || *c == '|') *c = '_';
     char key[512];
     // the build time stamp: every rebuild of the library re-times the candidates
-    snprintf(key, sizeof(key), "%s|%d|%d|%s|%s_%s", name, ctx->sm_count, ctx->cfg.state_fp64 ? 1 : 0, abp_version(),
-             __DATE__, __TIME__);
+    snprintf(key, sizeof(key), "%s|%d|%d|%s|%s_%s", name, ctx->sm_count, tune_kind(ctx), abp_version(), __DATE__,
+             __TIME__);
     for (char *c = key; *c; ++c)
         if (*c == ' ') *c = '_';
     return key;
@@ -323,9 +332,9 @@ void autotune(abp_ctx *ctx) {
         ctx->ppt = want_ppt;
         return;
     }
-    const int dev = ctx->device, fp = ctx->cfg.state_fp64 ? 1 : 0;
+    const int dev = ctx->device, kind = tune_kind(ctx);
     TuneTable local;
-    TuneTable &tt = (dev >= 0 && dev < 64) ? g_tune[dev][fp] : local;
+    TuneTable &tt = (dev >= 0 && dev < 64) ? g_tune[dev][kind] : local;
     if (!tt.done && !load_tune(ctx, tt)) {
         measure_candidates(ctx, tt);
         if (tt.done) save_tune(ctx, tt);
@@ -410,6 +419,9 @@ abp_status abp_create(abp_ctx **out, const abp_config *cfg, void *cuda_stream) {
         return ABP_EINVAL;
     if (cfg->schedule < 0 || cfg->schedule > 2) return ABP_EINVAL;
     if (cfg->checkpoint_every > 0 && cfg->state_fp64) return ABP_EINVAL;  // adjoint runs on the FP32 path
+    if (cfg->scheme != 0 && cfg->scheme != 1) return ABP_EINVAL;
+    if (cfg->scheme == 1 && (cfg->state_fp64 || cfg->checkpoint_every > 0)) return ABP_EINVAL;  // FP32, no adjoint
+    if (cfg->reserved != 0) return ABP_EINVAL;
     abp_ctx *ctx = new (std::nothrow) abp_ctx();
     if (!ctx) return ABP_ENOMEM;
     ctx->cfg = *cfg;
@@ -529,6 +541,32 @@ abp_status abp_set_params(abp_ctx *ctx, int32_t n_sets, const abp_params *sets, 
         ctx->tile_set.push_back(lead);
     }
     ctx->n_tiles = (int32_t)ctx->tile_first.size();
+    ctx->set_order.clear();
+    for (int32_t i = 0; i < n_sets; ++i)
+        if (!ctx->set_packed[i]) ctx->set_order.push_back(i);
+    ctx->n_unpacked = (int32_t)ctx->set_order.size();
+    for (int32_t i = 0; i < n_sets; ++i)
+        if (ctx->set_packed[i]) ctx->set_order.push_back(i);
+    // A lockstep batch with fewer tiles than SMs is launched narrow: blocks of
+    // the widest w in {256, 128, 64} that still gives every SM a block (else 32),
+    // one trajectory per thread, so its warps spread over the SMs.
+    ctx->narrow = 0;
+    ctx->sub_single = ctx->sub_packed = 1;
+    if (ctx->sched == 1 && ctx->n_tiles > 0 && ctx->n_tiles < ctx->sm_count) {
+        int w = 32;
+        for (int cand : {256, 128, 64}) {
+            if (cand >= tile) continue;
+            int64_t blocks = 0;
+            for (int32_t t = 0; t < ctx->n_tiles; ++t) blocks += (ctx->tile_count[t] + cand - 1) / cand;
+            if (blocks >= ctx->sm_count) {
+                w = cand;
+                break;
+            }
+        }
+        ctx->narrow = w;
+        ctx->sub_single = (int32_t)((tile + w - 1) / w);
+        ctx->sub_packed = kThreads / w;
+    }
     const abp_config &c = ctx->cfg;
     const bool any_hist = c.hist_x_bins > 0 || c.hist_v_bins > 0;
     ctx->n_snap = any_hist ? (c.snapshot_every > 0 ? max_n / c.snapshot_every : 1) : 0;
@@ -545,7 +583,7 @@ abp_status abp_set_params(abp_ctx *ctx, int32_t n_sets, const abp_params *sets, 
         int bps = 0;
         const size_t smem = sizeof(uint32_t) * (size_t)(std::max(c.hist_x_bins, 0) +
                                                         (c.hist_v_bins > 0 ? c.hist_v_bins + 2 : 0));
-        cudaError_t oe = persistent_occupancy(c.state_fp64 != 0, ctx->ppt, smem, &bps);
+        cudaError_t oe = persistent_occupancy(c.state_fp64 != 0, ctx->ppt, smem, &bps, c.scheme == 1);
         if (oe != cudaSuccess) return cuda_fail(ctx, oe, "occupancy query");
         ctx->grid = std::max(bps, 1) * std::max(ctx->sm_count, 1);
     }
@@ -581,7 +619,7 @@ abp_status abp_set_params(abp_ctx *ctx, int32_t n_sets, const abp_params *sets, 
     ALLOC(d_queue, sizeof(int32_t) * ((size_t)ctx->n_tiles + 1), "work queue");
     ALLOC(d_perm, sizeof(int32_t) * (size_t)std::max(ctx->n_tiles, 1), "work queue order");
     ALLOC(d_set_first, sizeof(int64_t) * ((size_t)n_sets + 1), "set offsets");
-    ALLOC(d_set_packed, sizeof(int32_t) * (size_t)std::max(n_sets, 1), "packed sets");
+    ALLOC(d_set_order, sizeof(int32_t) * (size_t)std::max(n_sets, 1), "set order");
 #undef ALLOC
 
     cudaStream_t s = ctx->stream;
@@ -596,7 +634,7 @@ abp_status abp_set_params(abp_ctx *ctx, int32_t n_sets, const abp_params *sets, 
     if (e == cudaSuccess) e = up(ctx->d_tile_set, ctx->tile_set.data(), sizeof(int32_t) * ctx->n_tiles);
     if (e == cudaSuccess) e = up(ctx->d_perm, ctx->perm.data(), sizeof(int32_t) * ctx->n_tiles);
     if (e == cudaSuccess) e = up(ctx->d_set_first, ctx->set_first.data(), sizeof(int64_t) * (n_sets + 1));
-    if (e == cudaSuccess) e = up(ctx->d_set_packed, ctx->set_packed.data(), sizeof(int32_t) * n_sets);
+    if (e == cudaSuccess) e = up(ctx->d_set_order, ctx->set_order.data(), sizeof(int32_t) * n_sets);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_status.p, 0, sizeof(int32_t), s);
     if (e == cudaSuccess && ctx->d_hx.bytes) e = cudaMemsetAsync(ctx->d_hx.p, 0, ctx->d_hx.bytes, s);
     if (e == cudaSuccess && ctx->d_hv.bytes) e = cudaMemsetAsync(ctx->d_hv.p, 0, ctx->d_hv.bytes, s);
@@ -672,7 +710,7 @@ cudaError_t enqueue_window(abp_ctx *ctx, int64_t g0, int64_t g1, const int32_t *
         for (int64_t g = g0; g < g1; g += ctx->steps_per_launch) {
             cudaError_t e = launch_integrate(b, st, h, c, nz, ctx->ppt, g, std::min(g1, g + ctx->steps_per_launch), s);
             if (e != cudaSuccess) return e;
-            *kernels += b.n_tiles > 0 ? 1 : 0;
+            *kernels += (b.n_single > 0 ? 1 : 0) + (b.n_tiles > b.n_single ? 1 : 0);
         }
         return cudaSuccess;
     }
@@ -775,10 +813,11 @@ abp_status abp_integrate(abp_ctx *ctx, int64_t max_steps) {
     return ABP_OK;
 }
 
-abp_status abp_tiles(const abp_ctx *ctx, int32_t *n_tiles, int32_t *n_packed) {
+abp_status abp_tiles(const abp_ctx *ctx, int32_t *n_tiles, int32_t *n_packed, int32_t *narrow) {
     if (!ctx) return ABP_EINVAL;
     if (n_tiles) *n_tiles = ctx->n_tiles;
     if (n_packed) *n_packed = ctx->n_tiles - ctx->n_single;
+    if (narrow) *narrow = ctx->narrow;
     return ABP_OK;
 }
 
@@ -826,7 +865,8 @@ abp_status abp_reduce(abp_ctx *ctx, double *moments, uint32_t *hist_x, uint32_t 
         cudaError_t e = launch_reduce(ctx->batch(), ctx->state(), ctx->noise(), ctx->g, (double *)ctx->d_partials.p,
                                       (double *)ctx->d_moments.p, ctx->stream);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "reduction launch");
-        ctx->launches += (ctx->n_tiles > 0 ? 1 : 0) + (ctx->n_sets > 0 ? 1 : 0);
+        ctx->launches += (ctx->n_sets > 0 && ctx->n_single > 0 ? 1 : 0) + (ctx->n_unpacked > 0 ? 1 : 0) +
+                         (ctx->n_sets > ctx->n_unpacked ? 1 : 0);
         if ((st = deliver(ctx, moments, ctx->d_moments.p, sizeof(double) * 8 * ctx->n_sets, &synced)) != ABP_OK)
             return st;
     }
@@ -846,7 +886,7 @@ struct SaveHeader {
     char magic[8];  // "ABPSAVE1"
     uint32_t version, fp64;
     int64_t g, total_traj;
-    int32_t n_sets, reserved;
+    int32_t n_sets, scheme;  // scheme: 0 Euler-Maruyama, 1 stochastic Heun
     uint64_t seed, traj_base;
     uint64_t hx_bytes, hv_bytes;
     uint64_t signature;  // FNV-1a of the sets' parameters, sizes and step counts
@@ -896,6 +936,7 @@ abp_status abp_save(abp_ctx *ctx, void *buf, size_t *bytes) {
     hd.g = ctx->g;
     hd.total_traj = ctx->total_traj;
     hd.n_sets = ctx->n_sets;
+    hd.scheme = ctx->cfg.scheme;
     hd.seed = ctx->cfg.seed;
     hd.traj_base = ctx->cfg.traj_base;
     hd.hx_bytes = ctx->d_hx.bytes;
@@ -931,7 +972,8 @@ abp_status abp_load(abp_ctx *ctx, const void *buf, size_t bytes) {
     for (auto &pt : image_parts(ctx)) need += pt.second;
     if (memcmp(hd.magic, "ABPSAVE1", 8) != 0 || hd.version != 1)
         return fail(ctx, ABP_EINVAL, "abp_load: not an image written by abp_save");
-    if (hd.fp64 != (ctx->cfg.state_fp64 ? 1u : 0u) || hd.total_traj != ctx->total_traj || hd.n_sets != ctx->n_sets ||
+    if (hd.fp64 != (ctx->cfg.state_fp64 ? 1u : 0u) || hd.scheme != ctx->cfg.scheme || hd.total_traj != ctx->total_traj ||
+        hd.n_sets != ctx->n_sets ||
         hd.signature != batch_signature(ctx) || hd.hx_bytes != ctx->d_hx.bytes || hd.hv_bytes != ctx->d_hv.bytes ||
         bytes < need || hd.g < 0 || hd.g > ctx->max_steps)
         return fail(ctx, ABP_EINVAL, "abp_load: the image belongs to a different batch or configuration");

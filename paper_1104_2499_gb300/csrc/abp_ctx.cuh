@@ -78,12 +78,14 @@ struct abp_ctx {
     int64_t launches = 0;  // kernels enqueued by this context
     std::vector<abp_params> params;
     std::vector<int64_t> n_traj, n_steps;
-    std::vector<int32_t> set_tile_begin, tile_count, tile_set, set_packed;
+    std::vector<int32_t> set_tile_begin, tile_count, tile_set, set_packed, set_order;
     std::vector<int64_t> tile_first, set_first;
     int32_t n_single = 0;  // tiles [n_single, n_tiles) are packed
+    int32_t n_unpacked = 0;  // sets in one-set tiles
+    int32_t narrow = 0, sub_single = 1, sub_packed = 1;  // narrow lockstep launch (small batches)
 
     // device
-    DevBuf d_params, d_steps, d_set_tile_begin, d_tile_first, d_tile_count, d_tile_set, d_set_first, d_set_packed;
+    DevBuf d_params, d_steps, d_set_tile_begin, d_tile_first, d_tile_count, d_tile_set, d_set_first, d_set_order;
     DevBuf d_y, d_yacc, d_ylo, d_v, d_e, d_y0, d_cell;
     DevBuf d_hx, d_hv, d_ckpt, d_partials, d_moments, d_status;
     DevBuf d_queue, d_round, d_perm;  // work queue: head + done[n_tiles]; round starts; tile order
@@ -96,7 +98,11 @@ struct abp_ctx {
         b.n_single = n_single;
         b.total_traj = total_traj;
         b.set_first = n_single < n_tiles ? (const int64_t *)d_set_first.p : nullptr;
-        b.set_packed = n_single < n_tiles ? (const int32_t *)d_set_packed.p : nullptr;
+        b.set_order = n_unpacked < n_sets ? (const int32_t *)d_set_order.p : nullptr;
+        b.n_unpacked = n_unpacked;
+        b.narrow = narrow;
+        b.sub_single = sub_single;
+        b.sub_packed = sub_packed;
         b.params = (const abp_params *)d_params.p;
         b.set_steps = (const int64_t *)d_steps.p;
         b.set_tile_begin = (const int32_t *)d_set_tile_begin.p;
@@ -143,6 +149,7 @@ struct abp_ctx {
         n.dt = cfg.dt;
         n.v0_mode = cfg.v0_mode;
         n.traj_base = cfg.traj_base;
+        n.scheme = cfg.scheme;
         return n;
     }
     void drop_graphs() {
@@ -161,7 +168,7 @@ struct abp_ctx {
     }
     void release_all() {
         drop_graphs();
-        for (DevBuf *b : {&d_queue, &d_round, &d_perm, &d_set_first, &d_set_packed, &d_params, &d_steps, &d_set_tile_begin, &d_tile_first, &d_tile_count, &d_tile_set, &d_y,
+        for (DevBuf *b : {&d_queue, &d_round, &d_perm, &d_set_first, &d_set_order, &d_params, &d_steps, &d_set_tile_begin, &d_tile_first, &d_tile_count, &d_tile_set, &d_y,
                           &d_yacc, &d_ylo, &d_v, &d_e, &d_y0, &d_cell, &d_hx, &d_hv, &d_ckpt, &d_partials,
                           &d_moments, &d_adj})
             b->release();

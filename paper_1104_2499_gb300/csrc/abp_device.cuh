@@ -179,6 +179,7 @@ struct Coef {
     R Cq;    // dt q
     R G;     // 1 - dt gamma0
     R Gd;    // -dt gamma0
+    R Cm;    // -dt c
     R sigma; // sqrt(2 D dt)
     R bm;    // -2 ln(2) sigma^2: Box-Muller constant of the scaled radius
     R F;     // dt F0 - 2 a K
@@ -202,6 +203,7 @@ __device__ __forceinline__ Coef<R> make_coef(double q, double c, double d, doubl
     k.Cq = (R)(dt * q);
     k.G = (R)(1.0 - dt * gamma0);
     k.Gd = (R)(-dt * gamma0);
+    k.Cm = (R)(-dt * c);
     k.sigma = (R)sqrt(2.0 * D * dt);
     k.bm = (R)(-2.0 * 0.69314718055994530942 * 2.0 * D * dt);
     k.F = (R)(dt * F0 - 2.0 * a * K);
@@ -254,6 +256,30 @@ __device__ __forceinline__ void em_step_f32(const Coef<float> &k, float nrs, flo
     yacc = fmaf(v, k.dtL, yacc);
     e = fmaf(e, t1, k.Cq);
     v = v + dv;
+}
+
+// One stochastic Heun step, FP32 (predictor-corrector for additive noise;
+// Kloeden & Platen 1992, Sec. 15.1), on the same sigma z_n = nrs * trig as
+// the Euler-Maruyama step.  With the drift increments of step n
+//   dv = dt (d e - gamma0) v + dt F0 - 2aK + c (K + 4aK c),  de = dt (q - c e - d e v^2)
+// the predictor is (x + v dt, v + dv + sigma z, e + de); its increments dv~,
+// de~ give v' = v + (dv + dv~)/2 + sigma z, e' = e + (de + de~)/2 and
+// x' = x + (v + v~) dt / 2.  Increments are formed on their own and added to
+// the state once, as in em_step_f32.
+__device__ __forceinline__ void heun_step_f32(const Coef<float> &k, float nrs, float trig, float pb, float &yacc,
+                                              float &v, float &e) {
+    const float sz = nrs * trig;
+    const float c0 = __cosf(phase_arg(pb, yacc));
+    const float dv0 = fmaf(fmaf(k.A4, c0, k.K), c0, fmaf(fmaf(k.Bd, e, k.Gd), v, k.F));
+    const float de0 = fmaf(e, fmaf(-k.Bd, v * v, k.Cm), k.Cq);
+    const float vp = v + (dv0 + sz);
+    const float ep = e + de0;
+    const float c1 = __cosf(phase_arg(pb, fmaf(v, k.dtL, yacc)));
+    const float dv1 = fmaf(fmaf(k.A4, c1, k.K), c1, fmaf(fmaf(k.Bd, ep, k.Gd), vp, k.F));
+    const float de1 = fmaf(ep, fmaf(-k.Bd, vp * vp, k.Cm), k.Cq);
+    yacc = fmaf(0.5f * (v + vp), k.dtL, yacc);
+    v = v + fmaf(0.5f, dv0 + dv1, sz);
+    e = e + 0.5f * (de0 + de1);
 }
 
 template <typename R>

@@ -28,7 +28,12 @@ struct Batch {
     int32_t n_single;
     int64_t total_traj;
     const int64_t *set_first;      // [n_sets + 1] first trajectory of each set (packed batches; else NULL)
-    const int32_t *set_packed;     // [n_sets] 1 if the set lives in a packed tile (else NULL)
+    const int32_t *set_order;      // [n_sets] sets in one-set tiles, then sets in packed tiles (NULL: all one-set, in order)
+    int32_t n_unpacked;            // sets in one-set tiles (the first n_unpacked entries of set_order)
+    // Narrow launch of the lockstep integrator (small batches): blocks of `narrow`
+    // threads (0: off), one trajectory per thread, sub_single blocks per one-set
+    // tile and sub_packed per packed tile.  Tiles, and so every result, are the same.
+    int32_t narrow, sub_single, sub_packed;
     const abp_params *params;      // [n_sets]
     const int64_t *set_steps;      // [n_sets] steps to run
     const int32_t *set_tile_begin; // [n_sets + 1]
@@ -76,6 +81,7 @@ struct Noise {
     int32_t v0_mode;
     uint64_t traj_base;  // added to every state index to give the global trajectory id
     uint32_t rk[20];     // round keys: rk[2r], rk[2r+1] = (k0 + r W0, k1 + r W1)
+    int32_t scheme;      // 0 Euler-Maruyama, 1 stochastic Heun (FP32 state)
 };
 
 // Work queue of the persistent integrator (device buffers owned by the context).
@@ -109,6 +115,6 @@ cudaError_t launch_persistent(const Batch &b, const State &s, const Hist &h, con
                               const Queue &q, int ppt, int grid, int64_t g0, int64_t g1, int64_t seg,
                               cudaStream_t st);
 // Resident blocks per SM of the persistent integrator (sets its shared-memory limit too).
-cudaError_t persistent_occupancy(bool fp64, int ppt, size_t smem, int *blocks_per_sm);
+cudaError_t persistent_occupancy(bool fp64, int ppt, size_t smem, int *blocks_per_sm, bool heun = false);
 
 }  // namespace abp

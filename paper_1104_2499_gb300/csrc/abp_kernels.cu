@@ -6,7 +6,7 @@
 //                     with the state in registers for thousands of steps,
 //                     block-compensated position, shared-memory snapshot
 //                     histograms and adjoint checkpoints
-//   tile_reduce_kernel / set_reduce_kernel
+//   tile_reduce_kernel / set_reduce_kernel / packed_reduce_kernel
 //                     fixed-order FP64 ensemble reduction (mean velocity,
 //                     standard error, MSD, D_eff)
 //   get_state_kernel  per-trajectory readback in FP64
@@ -182,10 +182,20 @@ struct KeyParam {
     RoundKeys K;
 };
 
+// The FP32 step of the configured scheme.
+template <bool HEUN>
+__device__ __forceinline__ void step_f32(const Coef<float> &k, float nrs, float trig, float pb, float &yacc, float &v,
+                                         float &e) {
+    if constexpr (HEUN)
+        heun_step_f32(k, nrs, trig, pb, yacc, v, e);
+    else
+        em_step_f32(k, nrs, trig, pb, yacc, v, e);
+}
+
 // One Euler-Maruyama step of every slot at an arbitrary step index n (the
 // unaligned head / tail of a range): the counter block of n is generated for
 // this step alone.
-template <typename R, int PPT>
+template <typename R, int PPT, bool HEUN = false>
 __device__ __forceinline__ void single_step(const Coef<R> &k, const RoundKeys &K, Slots<R, PPT> &S, int64_t n) {
     const uint32_t j = (uint32_t)(n & 3);
     const uint32_t m = (uint32_t)(n >> 2);
@@ -198,7 +208,7 @@ __device__ __forceinline__ void single_step(const Coef<R> &k, const RoundKeys &K
                 box_muller_f32(w.x, w.y, k.bm, nrs, cs, sn);
             else
                 box_muller_f32(w.z, w.w, k.bm, nrs, cs, sn);
-            em_step_f32(k, nrs, (j & 1) ? sn : cs, S.pb[q], S.yacc[q], S.v[q], S.e[q]);
+            step_f32<HEUN>(k, nrs, (j & 1) ? sn : cs, S.pb[q], S.yacc[q], S.v[q], S.e[q]);
         } else {
             const double z = normal_from_block_f64(w, j);
             em_step<double>(k, k.sigma * z, S.y[q], S.yacc[q], S.v[q], S.e[q]);
@@ -207,7 +217,7 @@ __device__ __forceinline__ void single_step(const Coef<R> &k, const RoundKeys &K
 }
 
 // Four steps 4m .. 4m+3 of every slot from one counter block each.
-template <typename R, int PPT>
+template <typename R, int PPT, bool HEUN = false>
 __device__ __forceinline__ void group_step(const Coef<R> &k, const RoundKeys &K, Slots<R, PPT> &S, uint32_t m) {
     uint4 w[PPT];
 #pragma unroll
@@ -217,15 +227,15 @@ __device__ __forceinline__ void group_step(const Coef<R> &k, const RoundKeys &K,
 #pragma unroll
         for (int q = 0; q < PPT; ++q) box_muller_f32(w[q].x, w[q].y, k.bm, nr[q], cs[q], sn[q]);
 #pragma unroll
-        for (int q = 0; q < PPT; ++q) em_step_f32(k, nr[q], cs[q], S.pb[q], S.yacc[q], S.v[q], S.e[q]);
+        for (int q = 0; q < PPT; ++q) step_f32<HEUN>(k, nr[q], cs[q], S.pb[q], S.yacc[q], S.v[q], S.e[q]);
 #pragma unroll
-        for (int q = 0; q < PPT; ++q) em_step_f32(k, nr[q], sn[q], S.pb[q], S.yacc[q], S.v[q], S.e[q]);
+        for (int q = 0; q < PPT; ++q) step_f32<HEUN>(k, nr[q], sn[q], S.pb[q], S.yacc[q], S.v[q], S.e[q]);
 #pragma unroll
         for (int q = 0; q < PPT; ++q) box_muller_f32(w[q].z, w[q].w, k.bm, nr[q], cs[q], sn[q]);
 #pragma unroll
-        for (int q = 0; q < PPT; ++q) em_step_f32(k, nr[q], cs[q], S.pb[q], S.yacc[q], S.v[q], S.e[q]);
+        for (int q = 0; q < PPT; ++q) step_f32<HEUN>(k, nr[q], cs[q], S.pb[q], S.yacc[q], S.v[q], S.e[q]);
 #pragma unroll
-        for (int q = 0; q < PPT; ++q) em_step_f32(k, nr[q], sn[q], S.pb[q], S.yacc[q], S.v[q], S.e[q]);
+        for (int q = 0; q < PPT; ++q) step_f32<HEUN>(k, nr[q], sn[q], S.pb[q], S.yacc[q], S.v[q], S.e[q]);
     } else {
 #pragma unroll
         for (int q = 0; q < PPT; ++q) {
@@ -242,24 +252,24 @@ __device__ __forceinline__ void group_step(const Coef<R> &k, const RoundKeys &K,
 
 // Steps [n, n_end) of every slot.  Folds happen after absolute multiples of
 // kBlockSteps steps; counter blocks are absolute multiples of 4.
-template <typename R, int PPT>
+template <typename R, int PPT, bool HEUN = false>
 __device__ __forceinline__ void advance(const Coef<R> &k, const RoundKeys &K, Slots<R, PPT> &S, int64_t n,
                                         int64_t n_end) {
     while (n < n_end) {
         const int64_t blk_end = min(n_end, (n | (int64_t)(kBlockSteps - 1)) + 1);
         while (n < blk_end && (n & 3)) {
-            single_step<R, PPT>(k, K, S, n);
+            single_step<R, PPT, HEUN>(k, K, S, n);
             ++n;
         }
         if (n < blk_end) {
             const uint32_t m_end = (uint32_t)(blk_end >> 2);
             uint32_t m = (uint32_t)(n >> 2);
 #pragma unroll kGroupUnroll
-            for (; m < m_end; ++m) group_step<R, PPT>(k, K, S, m);
+            for (; m < m_end; ++m) group_step<R, PPT, HEUN>(k, K, S, m);
             n = (int64_t)m << 2;
         }
         while (n < blk_end) {
-            single_step<R, PPT>(k, K, S, n);
+            single_step<R, PPT, HEUN>(k, K, S, n);
             ++n;
         }
         if ((blk_end & (kBlockSteps - 1)) == 0) {
@@ -280,10 +290,10 @@ __device__ __forceinline__ void advance(const Coef<R> &k, const RoundKeys &K, Sl
 // PACKED: a packed tile (several sets of equal step count, PPT 1): each thread
 // takes the coefficients of its own trajectory's set, and histograms go to
 // global memory directly.
-template <typename R, int PPT, bool PACKED = false>
+template <typename R, int PPT, bool PACKED = false, bool HEUN = false>
 __device__ __forceinline__ void run_tile(const Batch &b, const State &st, const Hist &h, const Ckpt &ck,
                                          const Noise &nz, const RoundKeys &K, uint32_t *sh, int tile, int64_t w0,
-                                         int64_t w1) {
+                                         int64_t w1, int lane_base = 0) {
     static_assert(!PACKED || PPT == 1, "packed tiles hold one trajectory per thread");
     const int64_t first = b.tile_first[tile];
     const int count = b.tile_count[tile];
@@ -294,7 +304,7 @@ __device__ __forceinline__ void run_tile(const Batch &b, const State &st, const 
     if (n_begin >= n_end) return;  // uniform over the block
 
     const SV<R> s = view<R>(st);
-    const int set = PACKED ? find_set(b, first + min((int)threadIdx.x, count - 1)) : set_t;
+    const int set = PACKED ? find_set(b, first + min(lane_base + (int)threadIdx.x, count - 1)) : set_t;
     const abp_params p = b.params[set];
     const Coef<R> k = make_coef<R>(p.q, p.c, p.d, p.gamma0, p.F0, p.D, p.h, p.L, p.asym, nz.dt);
 
@@ -303,7 +313,7 @@ __device__ __forceinline__ void run_tile(const Batch &b, const State &st, const 
     bool act[PPT];
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
-        const int li = threadIdx.x + q * kThreads;
+        const int li = lane_base + threadIdx.x + q * kThreads;
         act[q] = li < count;
         idx[q] = first + (act[q] ? li : count - 1);
         S.y[q] = __ldcg(&s.y[idx[q]]);
@@ -331,7 +341,7 @@ __device__ __forceinline__ void run_tile(const Batch &b, const State &st, const 
         int64_t seg_end = n_end;
         if (hist && h.snap_every > 0) seg_end = min(seg_end, (n / h.snap_every + 1) * h.snap_every);
         if (ck.every > 0) seg_end = min(seg_end, (n / ck.every + 1) * ck.every);
-        if (warp_live) advance<R, PPT>(k, K, S, n, seg_end);
+        if (warp_live) advance<R, PPT, HEUN>(k, K, S, n, seg_end);
         n = seg_end;
         if (hist && (h.snap_every > 0 ? (n % h.snap_every == 0) : (n == N))) {
             const int64_t snap = h.snap_every > 0 ? n / h.snap_every - 1 : 0;
@@ -382,13 +392,18 @@ __device__ __forceinline__ void zero_hist(uint32_t *sh, const Hist &h) {
     }
 }
 
-// Lockstep schedule: one block per tile, every tile over the window [g0, g1).
-template <typename R, int PPT, bool PACKED>
+// Lockstep schedule: one block per tile (narrow launch: `sub` blocks per tile,
+// each taking blockDim.x consecutive trajectories of it), every tile over the
+// window [g0, g1).
+template <typename R, int PPT, bool PACKED, bool HEUN>
 __global__ void ABP_INTEGRATE_BOUNDS integrate_kernel(Batch b, State st, Hist h, Ckpt ck, Noise nz,
                                                      KeyParam kp, int64_t g0, int64_t g1) {
     extern __shared__ uint32_t sh[];
     if constexpr (!PACKED) zero_hist(sh, h);
-    run_tile<R, PPT, PACKED>(b, st, h, ck, nz, kp.K, sh, (PACKED ? b.n_single : 0) + (int)blockIdx.x, g0, g1);
+    const int sub = b.narrow ? (PACKED ? b.sub_packed : b.sub_single) : 1;
+    const int tile = (PACKED ? b.n_single : 0) + (int)blockIdx.x / sub;
+    const int lane_base = ((int)blockIdx.x % sub) * (int)blockDim.x;
+    run_tile<R, PPT, PACKED, HEUN>(b, st, h, ck, nz, kp.K, sh, tile, g0, g1, lane_base);
 }
 
 __device__ __forceinline__ uint64_t global_ns() {
@@ -415,7 +430,7 @@ __device__ __forceinline__ void store_release(int32_t *p, int v) {
 // before it, so the earliest unfinished item is always runnable.  The wait is
 // bounded: past q.wait_limit_ns the block records status 1 and every block
 // leaves at its next check, without touching the item.
-template <typename R, int PPT>
+template <typename R, int PPT, bool HEUN>
 __global__ void ABP_INTEGRATE_BOUNDS persistent_kernel(Batch b, State st, Hist h, Ckpt ck, Noise nz, KeyParam kp,
                                                       Queue q, int64_t g0, int64_t g1, int64_t seg) {
     extern __shared__ uint32_t sh[];
@@ -459,7 +474,7 @@ __global__ void ABP_INTEGRATE_BOUNDS persistent_kernel(Batch b, State st, Hist h
         if (s_tile < 0) break;
         {
             const int64_t w0 = g0 + (int64_t)s_round * seg;
-            run_tile<R, PPT>(b, st, h, ck, nz, kp.K, sh, s_tile, w0, min(w0 + seg, g1));
+            run_tile<R, PPT, false, HEUN>(b, st, h, ck, nz, kp.K, sh, s_tile, w0, min(w0 + seg, g1));
         }
         __syncthreads();  // every thread's state stores precede the publication
         if (threadIdx.x == 0 && s_tile != q.hold_tile) {
@@ -494,6 +509,19 @@ __device__ __forceinline__ void block_sum4(double (&a)[4], double (*red)[4]) {
     }
 }
 
+// Adds the four terms of trajectory t to a.  Each square is rounded on its
+// own before the addition (no fused multiply-add), as in a tree whose leaves
+// are single trajectories.
+template <typename R>
+__device__ __forceinline__ void traj_terms(const SV<R> &s, int64_t t, double L, double inv_T, double (&a)[4]) {
+    const double dx = L * disp_periods<R>(s, t);
+    const double vbar = dx * inv_T;
+    a[0] = __dadd_rn(a[0], vbar);
+    a[1] = __dadd_rn(a[1], __dmul_rn(vbar, vbar));
+    a[2] = __dadd_rn(a[2], dx);
+    a[3] = __dadd_rn(a[3], __dmul_rn(dx, dx));
+}
+
 // Per tile: sum vbar, sum vbar^2, sum dx, sum dx^2 with dx = x_n - x_0 and
 // vbar = dx / (n dt), n = min(g, N) steps done (the scheme advances x by
 // v_k dt at every step, so dx / (n dt) is the time average of v_0 .. v_{n-1}).
@@ -503,7 +531,6 @@ __global__ void __launch_bounds__(kThreads) tile_reduce_kernel(Batch b, State st
     __shared__ double red[kThreads / 32][4];
     const SV<R> s = view<R>(st);
     const int tile = blockIdx.x;
-    if (tile >= b.n_single) return;  // packed sets are reduced directly by set_reduce_kernel
     const int set = b.tile_set[tile];
     const int64_t n = min(g, b.set_steps[set]);
     const double L = b.params[set].L;
@@ -511,69 +538,112 @@ __global__ void __launch_bounds__(kThreads) tile_reduce_kernel(Batch b, State st
     const int64_t first = b.tile_first[tile];
     const int count = b.tile_count[tile];
     double a[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int li = threadIdx.x; li < count; li += blockDim.x) {
-        const int64_t t = first + li;
-        const double dx = L * disp_periods<R>(s, t);
-        const double vbar = dx * inv_T;
-        a[0] += vbar;
-        a[1] += vbar * vbar;
-        a[2] += dx;
-        a[3] += dx * dx;
-    }
+    for (int li = threadIdx.x; li < count; li += blockDim.x) traj_terms<R>(s, first + li, L, inv_T, a);
     block_sum4(a, red);
     if (threadIdx.x == 0)
 #pragma unroll
         for (int j = 0; j < 4; ++j) partials[(size_t)tile * 4 + j] = a[j];
 }
 
-// Per set: fixed-order sum of its tiles' partials and the derived moments.
-// Per set: fixed-order sum of its tiles' partials -- or, for a set in a packed
-// tile, of its trajectories directly -- and the derived moments.
+// Derived moments of a set from its four FP64 sums over M trajectories of n steps.
+__device__ __forceinline__ void write_moments(double *o, const double (&a)[4], int64_t M, int64_t n, double dt) {
+    const double Md = (double)M;
+    const double mean_v = M > 0 ? a[0] / Md : 0.0;
+    const double var_v = M > 1 ? (a[1] - Md * mean_v * mean_v) / (Md - 1.0) : 0.0;
+    const double msd = M > 0 ? a[3] / Md : 0.0;
+    const double mdx = M > 0 ? a[2] / Md : 0.0;
+    const double T = (double)n * dt;
+    o[0] = mean_v;
+    o[1] = M > 0 ? sqrt(fmax(var_v, 0.0) / Md) : 0.0;
+    o[2] = msd;
+    o[3] = T > 0.0 ? (msd - mdx * mdx) / (2.0 * T) : 0.0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) o[4 + j] = a[j];
+}
+
+// Per set in one-set tiles: fixed-order sum of its tiles' partials and the
+// derived moments.  Block i takes set set_order[i] (or i).
 template <typename R>
-__global__ void __launch_bounds__(kThreads) set_reduce_kernel(Batch b, State st, double dt, int64_t g,
-                                                              const double *partials, double *moments) {
+__global__ void __launch_bounds__(kThreads) set_reduce_kernel(Batch b, double dt, int64_t g, const double *partials,
+                                                              double *moments) {
     __shared__ double red[kThreads / 32][4];
-    const int set = blockIdx.x;
+    const int set = b.set_order ? b.set_order[blockIdx.x] : (int)blockIdx.x;
     const int64_t n = min(g, b.set_steps[set]);
     double a[4] = {0.0, 0.0, 0.0, 0.0};
     int64_t M = 0;
-    if (b.set_packed && b.set_packed[set]) {
-        const SV<R> s = view<R>(st);
-        const double L = b.params[set].L;
-        const double inv_T = n > 0 ? 1.0 / ((double)n * dt) : 0.0;
-        const int64_t t0 = b.set_first[set], t1 = b.set_first[set + 1];
-        M = t1 - t0;
-        for (int64_t t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
-            const double dx = L * disp_periods<R>(s, t);
-            const double vbar = dx * inv_T;
-            a[0] += vbar;
-            a[1] += vbar * vbar;
-            a[2] += dx;
-            a[3] += dx * dx;
-        }
-    } else {
-        const int t0 = b.set_tile_begin[set], t1 = b.set_tile_begin[set + 1];
-        for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x)
+    const int t0 = b.set_tile_begin[set], t1 = b.set_tile_begin[set + 1];
+    for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) a[j] += partials[(size_t)t * 4 + j];
-        for (int t = t0; t < t1; ++t) M += b.tile_count[t];
-    }
+        for (int j = 0; j < 4; ++j) a[j] += partials[(size_t)t * 4 + j];
+    for (int t = t0; t < t1; ++t) M += b.tile_count[t];
     block_sum4(a, red);
-    if (threadIdx.x == 0) {
-        double *o = moments + (size_t)set * 8;
-        const double Md = (double)M;
-        const double mean_v = M > 0 ? a[0] / Md : 0.0;
-        const double var_v = M > 1 ? (a[1] - Md * mean_v * mean_v) / (Md - 1.0) : 0.0;
-        const double msd = M > 0 ? a[3] / Md : 0.0;
-        const double mdx = M > 0 ? a[2] / Md : 0.0;
-        const double T = (double)n * dt;
-        o[0] = mean_v;
-        o[1] = M > 0 ? sqrt(fmax(var_v, 0.0) / Md) : 0.0;
-        o[2] = msd;
-        o[3] = T > 0.0 ? (msd - mdx * mdx) / (2.0 * T) : 0.0;
+    if (threadIdx.x == 0) write_moments(moments + (size_t)set * 8, a, M, n, dt);
+}
+
+// Sets in packed tiles (fewer than kThreads trajectories each): one lane per
+// set, 32 sets per warp, so the FP64 work of the moments (divisions, square
+// root: slow on this GPU's FP64 pipe) is shared by 32 sets per instruction.
+// A set must reduce to the same bits whether or not it was packed, i.e. in
+// the order block_sum4 gives a one-tile set: a lane tree over each group of 32
+// trajectories, then a lane tree over the groups' results.  For one or two
+// trajectories that tree is the plain running sum (every other addition adds
+// an exact zero), which the set's own lane does; larger sets are summed by the
+// whole warp in the tree order, skipping the stages that only add zeros.
+template <typename R>
+__global__ void __launch_bounds__(kThreads) packed_reduce_kernel(Batch b, State st, double dt, int64_t g,
+                                                                 double *moments) {
+    const int n_packed = b.n_sets - b.n_unpacked;
+    const int k = (int)(blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+    if ((k & ~31) >= n_packed) return;  // whole warps
+    const int lane = threadIdx.x & 31;
+    const bool mine = k < n_packed;
+    const int set = mine ? b.set_order[b.n_unpacked + k] : 0;
+    const SV<R> s = view<R>(st);
+    const int64_t n = min(g, b.set_steps[set]);
+    const double L = b.params[set].L;
+    const double inv_T = n > 0 ? 1.0 / ((double)n * dt) : 0.0;
+    const int64_t t0 = b.set_first[set], t1 = mine ? b.set_first[set + 1] : t0;
+    const int m = (int)(t1 - t0);
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    if (m <= 2)
+        for (int64_t t = t0; t < t1; ++t) traj_terms<R>(s, t, L, inv_T, a);
+    unsigned big = __ballot_sync(0xffffffffu, m > 2);
+    while (big) {
+        const int src = __ffs(big) - 1;
+        big &= big - 1;
+        const int64_t u0 = __shfl_sync(0xffffffffu, t0, src);
+        const int mu = __shfl_sync(0xffffffffu, m, src);
+        const double Lu = __shfl_sync(0xffffffffu, L, src);
+        const double iu = __shfl_sync(0xffffffffu, inv_T, src);
+        const int groups = (mu + 31) >> 5;
+        double part[4] = {0.0, 0.0, 0.0, 0.0};  // lane w: the tree sum of trajectories [32w, 32w + 32)
+        for (int w = 0; w < groups; ++w) {
+            double c[4] = {0.0, 0.0, 0.0, 0.0};
+            if (w * 32 + lane < mu) traj_terms<R>(s, u0 + w * 32 + lane, Lu, iu, c);
+            const int live = min(mu - w * 32, 32);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) o[4 + j] = a[j];
+            for (int o = 16; o > 0; o >>= 1)
+                if (o < live)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) c[j] += __shfl_down_sync(0xffffffffu, c[j], o);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const double r = __shfl_sync(0xffffffffu, c[j], 0);
+                if (lane == w) part[j] = r;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            if (o < groups)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) part[j] += __shfl_down_sync(0xffffffffu, part[j], o);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const double r = __shfl_sync(0xffffffffu, part[j], 0);
+            if (lane == src) a[j] = r;
+        }
     }
+    if (mine) write_moments(moments + (size_t)set * 8, a, m, n, dt);
 }
 
 template <typename R>
@@ -634,11 +704,11 @@ KeyParam key_param(uint32_t k0, uint32_t k1) {
     return kp;
 }
 
-template <typename R, int PPT>
+template <typename R, int PPT, bool HEUN = false>
 cudaError_t launch_persistent_t(const Batch &b, const State &s, const Hist &h, const Ckpt &c, const Noise &nz,
                                 const Queue &q, int grid, int64_t g0, int64_t g1, int64_t seg, cudaStream_t st) {
     const size_t smem = hist_smem(h);
-    auto kern = persistent_kernel<R, PPT>;
+    auto kern = persistent_kernel<R, PPT, HEUN>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -647,19 +717,22 @@ cudaError_t launch_persistent_t(const Batch &b, const State &s, const Hist &h, c
     return cudaGetLastError();
 }
 
-template <typename R, int PPT>
+template <typename R, int PPT, bool HEUN = false>
 cudaError_t launch_integrate_t(const Batch &b, const State &s, const Hist &h, const Ckpt &c, const Noise &nz,
                                int64_t g0, int64_t g1, cudaStream_t st) {
     const size_t smem = hist_smem(h);
-    auto kern = integrate_kernel<R, PPT, false>;
+    auto kern = integrate_kernel<R, PPT, false, HEUN>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    if (b.n_single > 0) kern<<<b.n_single, kThreads, smem, st>>>(b, s, h, c, nz, key_param(nz.k0, nz.k1), g0, g1);
+    const int threads = b.narrow ? b.narrow : kThreads;
+    const int64_t sub_s = b.narrow ? b.sub_single : 1, sub_p = b.narrow ? b.sub_packed : 1;
+    if (b.n_single > 0)
+        kern<<<(unsigned)(b.n_single * sub_s), threads, smem, st>>>(b, s, h, c, nz, key_param(nz.k0, nz.k1), g0, g1);
     if (b.n_tiles > b.n_single)  // packed tiles: one trajectory per thread, histograms in global memory
-        integrate_kernel<R, 1, true><<<b.n_tiles - b.n_single, kThreads, 0, st>>>(b, s, h, c, nz,
-                                                                                  key_param(nz.k0, nz.k1), g0, g1);
+        integrate_kernel<R, 1, true, HEUN><<<(unsigned)((b.n_tiles - b.n_single) * sub_p), threads, 0, st>>>(
+            b, s, h, c, nz, key_param(nz.k0, nz.k1), g0, g1);
     return cudaGetLastError();
 }
 
@@ -686,11 +759,18 @@ cudaError_t launch_init(const Batch &b, const State &s, const Hist &h, const Ckp
 cudaError_t launch_integrate(const Batch &b, const State &s, const Hist &h, const Ckpt &c, const Noise &nz, int ppt,
                              int64_t g0, int64_t g1, cudaStream_t st) {
     if (b.n_tiles == 0 || g1 <= g0) return cudaSuccess;
+    if (b.narrow) ppt = 1;
     if (s.fp64) {
         switch (ppt) {
             case 1: return launch_integrate_t<double, 1>(b, s, h, c, nz, g0, g1, st);
             case 2: return launch_integrate_t<double, 2>(b, s, h, c, nz, g0, g1, st);
             case 4: return launch_integrate_t<double, 4>(b, s, h, c, nz, g0, g1, st);
+        }
+    } else if (nz.scheme == 1) {
+        switch (ppt) {
+            case 1: return launch_integrate_t<float, 1, true>(b, s, h, c, nz, g0, g1, st);
+            case 2: return launch_integrate_t<float, 2, true>(b, s, h, c, nz, g0, g1, st);
+            case 4: return launch_integrate_t<float, 4, true>(b, s, h, c, nz, g0, g1, st);
         }
     } else {
         switch (ppt) {
@@ -712,6 +792,12 @@ cudaError_t launch_persistent(const Batch &b, const State &s, const Hist &h, con
             case 2: return launch_persistent_t<double, 2>(b, s, h, c, nz, q, grid, g0, g1, seg, st);
             case 4: return launch_persistent_t<double, 4>(b, s, h, c, nz, q, grid, g0, g1, seg, st);
         }
+    } else if (nz.scheme == 1) {
+        switch (ppt) {
+            case 1: return launch_persistent_t<float, 1, true>(b, s, h, c, nz, q, grid, g0, g1, seg, st);
+            case 2: return launch_persistent_t<float, 2, true>(b, s, h, c, nz, q, grid, g0, g1, seg, st);
+            case 4: return launch_persistent_t<float, 4, true>(b, s, h, c, nz, q, grid, g0, g1, seg, st);
+        }
     } else {
         switch (ppt) {
             case 1: return launch_persistent_t<float, 1>(b, s, h, c, nz, q, grid, g0, g1, seg, st);
@@ -722,14 +808,17 @@ cudaError_t launch_persistent(const Batch &b, const State &s, const Hist &h, con
     return cudaErrorInvalidValue;
 }
 
-cudaError_t persistent_occupancy(bool fp64, int ppt, size_t smem, int *blocks_per_sm) {
+cudaError_t persistent_occupancy(bool fp64, int ppt, size_t smem, int *blocks_per_sm, bool heun) {
     const void *f = nullptr;
     if (fp64) {
-        f = ppt == 1 ? (const void *)persistent_kernel<double, 1>
-                     : ppt == 2 ? (const void *)persistent_kernel<double, 2> : (const void *)persistent_kernel<double, 4>;
+        f = ppt == 1 ? (const void *)persistent_kernel<double, 1, false>
+            : ppt == 2 ? (const void *)persistent_kernel<double, 2, false> : (const void *)persistent_kernel<double, 4, false>;
+    } else if (heun) {
+        f = ppt == 1 ? (const void *)persistent_kernel<float, 1, true>
+            : ppt == 2 ? (const void *)persistent_kernel<float, 2, true> : (const void *)persistent_kernel<float, 4, true>;
     } else {
-        f = ppt == 1 ? (const void *)persistent_kernel<float, 1>
-                     : ppt == 2 ? (const void *)persistent_kernel<float, 2> : (const void *)persistent_kernel<float, 4>;
+        f = ppt == 1 ? (const void *)persistent_kernel<float, 1, false>
+            : ppt == 2 ? (const void *)persistent_kernel<float, 2, false> : (const void *)persistent_kernel<float, 4, false>;
     }
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -741,16 +830,26 @@ cudaError_t persistent_occupancy(bool fp64, int ppt, size_t smem, int *blocks_pe
 cudaError_t launch_reduce(const Batch &b, const State &s, const Noise &nz, int64_t g, double *partials,
                           double *moments, cudaStream_t st) {
     if (b.n_sets == 0) return cudaSuccess;
-    if (b.n_tiles > 0) {
+    if (b.n_single > 0) {
         if (s.fp64)
-            tile_reduce_kernel<double><<<b.n_tiles, kThreads, 0, st>>>(b, s, nz.dt, g, partials);
+            tile_reduce_kernel<double><<<b.n_single, kThreads, 0, st>>>(b, s, nz.dt, g, partials);
         else
-            tile_reduce_kernel<float><<<b.n_tiles, kThreads, 0, st>>>(b, s, nz.dt, g, partials);
+            tile_reduce_kernel<float><<<b.n_single, kThreads, 0, st>>>(b, s, nz.dt, g, partials);
     }
-    if (s.fp64)
-        set_reduce_kernel<double><<<b.n_sets, kThreads, 0, st>>>(b, s, nz.dt, g, partials, moments);
-    else
-        set_reduce_kernel<float><<<b.n_sets, kThreads, 0, st>>>(b, s, nz.dt, g, partials, moments);
+    if (b.n_unpacked > 0) {
+        if (s.fp64)
+            set_reduce_kernel<double><<<b.n_unpacked, kThreads, 0, st>>>(b, nz.dt, g, partials, moments);
+        else
+            set_reduce_kernel<float><<<b.n_unpacked, kThreads, 0, st>>>(b, nz.dt, g, partials, moments);
+    }
+    const int n_packed = b.n_sets - b.n_unpacked;
+    if (n_packed > 0) {
+        const int grid = (int)(((int64_t)n_packed + kThreads - 1) / kThreads);
+        if (s.fp64)
+            packed_reduce_kernel<double><<<grid, kThreads, 0, st>>>(b, s, nz.dt, g, moments);
+        else
+            packed_reduce_kernel<float><<<grid, kThreads, 0, st>>>(b, s, nz.dt, g, moments);
+    }
     return cudaGetLastError();
 }
 

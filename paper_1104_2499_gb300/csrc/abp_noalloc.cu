@@ -136,6 +136,8 @@ extern "C" abp_status abp_run_set_noalloc(const abp_params *params, const abp_co
         return say(err, err_len, ABP_EINVAL, "histogram bins must be in [0, 8192]");
     if (cfg->hist_v_bins > 0 && !(cfg->v_hi > cfg->v_lo))
         return say(err, err_len, ABP_EINVAL, "v_hi must exceed v_lo");
+    if (cfg->scheme != 0 && cfg->scheme != 1) return say(err, err_len, ABP_EINVAL, "scheme must be 0 or 1");
+    if (cfg->reserved != 0) return say(err, err_len, ABP_EINVAL, "reserved must be 0");
     if (cfg->snapshot_every < 0 || cfg->steps_per_launch < 0 || (cfg->schedule < 0 || cfg->schedule > 2))
         return say(err, err_len, ABP_EINVAL, "invalid snapshot_every / steps_per_launch / schedule");
     const int ppt = cfg->particles_per_thread ? cfg->particles_per_thread : 1;
@@ -179,7 +181,10 @@ extern "C" abp_status abp_run_set_noalloc(const abp_params *params, const abp_co
     b.n_tiles = n_tiles;
     b.n_single = n_tiles;
     b.set_first = nullptr;
-    b.set_packed = nullptr;
+    b.set_order = nullptr;
+    b.n_unpacked = b.n_sets;
+    b.narrow = 0;
+    b.sub_single = b.sub_packed = 1;
     b.total_traj = n_traj;
     b.params = (const abp_params *)(base + kOffParams);
     b.set_steps = (const int64_t *)(base + kOffSteps);
@@ -216,6 +221,7 @@ extern "C" abp_status abp_run_set_noalloc(const abp_params *params, const abp_co
     nz.dt = cfg->dt;
     nz.v0_mode = cfg->v0_mode;
     nz.traj_base = cfg->traj_base;
+    nz.scheme = cfg->scheme;
 
     e = cudaGetLastError();
     if (e == cudaSuccess) e = launch_init(b, s, h, c, nz, st);

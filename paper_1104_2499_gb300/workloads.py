@@ -42,6 +42,7 @@ class Workload:
     v_hi: float = 5.0
     snapshot_every: int = 0     # 0: one snapshot after the last step
     checkpoint_every: int = 0
+    scheme: int = 0             # 0: Euler-Maruyama (the paper's step), 1: stochastic Heun
     notes: str = ""
     extra: dict = field(default_factory=dict)
 

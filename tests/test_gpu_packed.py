@@ -49,8 +49,8 @@ def run(A, w, **kw):
 
 def test_packed_layout_is_bitwise_the_unpacked_one(abp):
     w = mixed_batch()
-    ra, sa, ta = run(abp, w, schedule=1)
-    rb, sb, tb = run(abp, w, schedule=2)
+    ra, sa, ta = run(abp, w, schedule=1, particles_per_thread=1)
+    rb, sb, tb = run(abp, w, schedule=2, particles_per_thread=1)
     assert ta["packed"] > 0 and tb["packed"] == 0
     for k in sa:
         assert torch.equal(sa[k], sb[k]), k
@@ -60,7 +60,7 @@ def test_packed_layout_is_bitwise_the_unpacked_one(abp):
 
 def test_packed_sets_against_oracle(abp):
     w = mixed_batch(seed=4, steps=1000)
-    res, st, t = run(abp, w, schedule=1)
+    res, st, t = run(abp, w, schedule=1, particles_per_thread=1)
     assert t["packed"] > 0
     gs = {k: a.cpu().numpy() for k, a in st.items()}
     hx = res["hist_x"].cpu().numpy()
@@ -91,8 +91,8 @@ def test_packed_zero_step_sets_snapshot_initial_state(abp):
     sets = [W._with(D=0.1 * (i + 1)) for i in range(6)]
     w = W.Workload(name="zero", sets=sets, n_traj=[3, 0, 5, 1, 7, 2], n_steps=[0] * 6, dt=1e-3, seed=8, v0_mode=1,
                    hist_x_bins=8, hist_v_bins=4, v_lo=-1.0, v_hi=1.0)
-    res, st, t = run(abp, w, schedule=1)
-    rb, sb, tb = run(abp, w, schedule=2)
+    res, st, t = run(abp, w, schedule=1, particles_per_thread=1)
+    rb, sb, tb = run(abp, w, schedule=2, particles_per_thread=1)
     assert t["packed"] == 1 and tb["packed"] == 0
     assert res["hist_x"].cpu().numpy()[0].sum(1).tolist() == w.n_traj
     assert res["hist_v"].cpu().numpy()[0].sum(1).tolist() == w.n_traj
@@ -100,3 +100,30 @@ def test_packed_zero_step_sets_snapshot_initial_state(abp):
         assert torch.equal(st[k], sb[k]), k
     for k in res:
         assert torch.equal(res[k], rb[k]), k
+
+
+@pytest.mark.parametrize("n_traj,ppt", [(4096, 1), (4096, 2), (777, 1)])
+def test_narrow_launch_is_bitwise_the_wide_one(abp, n_traj, ppt):
+    # a batch with fewer tiles than SMs runs narrow blocks; the work queue never does
+    w = W.single_set(n_traj=n_traj, n_steps=900, hist_x_bins=32)
+    w.hist_v_bins, w.v_lo, w.v_hi, w.snapshot_every = 16, -2.0, 2.0, 300
+    ra, sa, ta = run(abp, w, schedule=1, particles_per_thread=ppt)
+    rb, sb, tb = run(abp, w, schedule=2, particles_per_thread=ppt)
+    assert ta["narrow"] in (32, 64, 128, 256) and tb["narrow"] == 0
+    for k in sa:
+        assert torch.equal(sa[k], sb[k]), k
+    for k in ra:
+        assert torch.equal(ra[k], rb[k]), k
+
+
+def test_narrow_packed_items_against_wide(abp):
+    # 300 one-trajectory work items: two packed tiles, launched narrow
+    w = W.force_sweep(n_F=300, traj_per_set=1, n_steps=640)
+    w.hist_x_bins = 8
+    ra, sa, ta = run(abp, w, schedule=1, particles_per_thread=1)
+    rb, sb, tb = run(abp, w, schedule=2, particles_per_thread=1)
+    assert ta["packed"] == 2 and ta["narrow"] > 0 and tb["packed"] == 0
+    for k in sa:
+        assert torch.equal(sa[k], sb[k]), k
+    for k in ra:
+        assert torch.equal(ra[k], rb[k]), k
