@@ -31,6 +31,11 @@ namespace {
 #ifndef ABP_ADJ_MIN_BLOCKS
 #define ABP_ADJ_MIN_BLOCKS 2
 #endif
+#ifndef ABP_ADJ_REV_THREADS
+#define ABP_ADJ_REV_THREADS 256
+#endif
+// Threads per block of the register-heavy reverse kernel (a multiple of 32).
+constexpr int kRevThreads = ABP_ADJ_REV_THREADS;
 constexpr int kSub = ABP_ADJ_SUB;  // steps per register-resident sub-chunk (a multiple of 4)
 static_assert(kSub % 4 == 0 && (kBlockSteps % kSub) == 0, "sub-chunks hold whole Philox blocks");
 
@@ -148,13 +153,13 @@ __device__ __forceinline__ void block_sum6(double (&a)[6], double (*red)[6]) {
     }
 }
 
-// Segment [s0, s1) of one trajectory in reverse, from its checkpoint (y,
-// yacc, v, e) = c0.  Segments that start on a multiple of kSub steps run in
-// whole kSub-step chunks whose noise comes two Philox blocks at a time (the
-// forward's own path); others step one at a time.
-__device__ __forceinline__ void reverse_segment(const AdjArgs &a, const Coef<float> &k, const StepStream &ss,
-                                                float kx, float dtf, int64_t idx, int64_t s0, int64_t s1, float4 c0,
-                                                float &lx, float &lv, float &le, float (&acc)[6]) {
+// Level 1 of segment [s0, s1) of one trajectory: re-run from its checkpoint
+// (y, yacc, v, e) = c0, leaving the state at s0, s0 + kSub, ... in the
+// sub-checkpoint scratch.  Segments that start on a multiple of kSub steps run
+// in whole kSub-step chunks whose noise comes one Philox block per four steps
+// (the forward's own path); others step one at a time.
+__device__ __forceinline__ void level1_segment(const AdjArgs &a, const Coef<float> &k, const StepStream &ss,
+                                               int64_t idx, int64_t s0, int64_t s1, float4 c0) {
     const int64_t T = a.b.total_traj;
     float y = c0.x, yacc = c0.y, v = c0.z, e = c0.w;
     float pb = phase_base(y);
@@ -163,7 +168,6 @@ __device__ __forceinline__ void reverse_segment(const AdjArgs &a, const Coef<flo
     NoiseCursor nc;
     nc.valid = false;
     nc.m = 0;
-    // level 1: sub-checkpoints at s0, s0 + kSub, ...
     for (int j = 0; j < n_chunks; ++j) {
         const int64_t n0 = s0 + (int64_t)j * kSub;
         a.sub[(size_t)j * T + idx] = make_float4(y, yacc, v, e);
@@ -185,16 +189,29 @@ __device__ __forceinline__ void reverse_segment(const AdjArgs &a, const Coef<flo
             }
         }
     }
-    // level 2: chunks in reverse, re-run into registers and swept backwards
+}
+
+// Level 2 and the reverse sweep of segment [s0, s1): its kSub-step chunks in
+// reverse order, each re-run from its sub-checkpoint into registers and swept
+// backwards.  Each chunk's sub-checkpoint is loaded one chunk ahead, so its
+// memory latency overlaps the previous chunk's arithmetic.
+__device__ __forceinline__ void reverse_chunks(const AdjArgs &a, const Coef<float> &k, const StepStream &ss, float kx,
+                                               float dtf, int64_t idx, int64_t s0, int64_t s1, float &lx, float &lv,
+                                               float &le, float (&acc)[6]) {
+    const int64_t T = a.b.total_traj;
+    const int n_chunks = (int)((s1 - s0 + kSub - 1) / kSub);
+    const bool aligned = (s0 & (kSub - 1)) == 0;
+    NoiseCursor nc;
+    nc.valid = false;
+    nc.m = 0;
+    float4 c_next = a.sub[(size_t)(n_chunks - 1) * T + idx];
     for (int j = n_chunks - 1; j >= 0; --j) {
         const int64_t n0 = s0 + (int64_t)j * kSub;
         const int len = (int)(s1 - n0 < kSub ? s1 - n0 : kSub);
-        const float4 cj = a.sub[(size_t)j * T + idx];
-        y = cj.x;
-        yacc = cj.y;
-        v = cj.z;
-        e = cj.w;
-        pb = phase_base(y);
+        const float4 cj = c_next;
+        if (j > 0) c_next = a.sub[(size_t)(j - 1) * T + idx];
+        float y = cj.x, yacc = cj.y, v = cj.z, e = cj.w;
+        float pb = phase_base(y);
         float ys[kSub], vs[kSub], es[kSub], szs[kSub];  // ys: the force phase of each step
         if (aligned && len == kSub) {
             // no fold falls inside an aligned chunk (folds come after multiples of kBlockSteps)
@@ -235,48 +252,90 @@ __device__ __forceinline__ void reverse_segment(const AdjArgs &a, const Coef<flo
     }
 }
 
-__global__ void __launch_bounds__(kThreads, ABP_ADJ_MIN_BLOCKS) adjoint_kernel(AdjArgs a) {
+// One launch per segment index and level, segments in reverse order: level 1
+// (a plain forward re-run, light on registers, so it runs at the integrator's
+// occupancy) for segment `seg` of every trajectory, then level 2 and the
+// reverse sweep (register-heavy) for the same segment.  Between launches each
+// trajectory keeps its adjoint state lambda = (x, v, e) and its six gradient
+// sums in global memory.  Trajectories of sets shorter than seg K skip.
+struct SegView {
+    float4 *lam;  // [total_traj] (lambda_x, lambda_v, lambda_e, -)
+    double *G;    // [6][total_traj] gradient sums
+};
+
+__global__ void __launch_bounds__(kThreads) adjoint_level1_kernel(AdjArgs a, int64_t seg) {
+    const Batch &b = a.b;
+    const int tile = blockIdx.x;
+    const int set = b.tile_set[tile];
+    const int64_t N = b.set_steps[set], K = a.ck.every, T = b.total_traj;
+    const int64_t s0 = seg * K;
+    if (s0 >= N) return;  // uniform over the block
+    const int64_t s1 = min(s0 + K, N);
+    const abp_params p = b.params[set];
+    const Coef<float> k = make_coef<float>(p.q, p.c, p.d, p.gamma0, p.F0, p.D, p.h, p.L, p.asym, a.nz.dt);
+    const int64_t first = b.tile_first[tile];
+    const int count = b.tile_count[tile];
+    for (int li = threadIdx.x; li < count; li += blockDim.x) {
+        const int64_t idx = first + li;
+        const StepStream ss = step_stream((uint64_t)idx + a.nz.traj_base, a.K);
+        level1_segment(a, k, ss, idx, s0, s1, a.ck.ck[(size_t)seg * T + idx]);
+    }
+}
+
+__global__ void __launch_bounds__(kRevThreads, ABP_ADJ_MIN_BLOCKS) adjoint_reverse_kernel(AdjArgs a, SegView sv,
+                                                                                          int64_t seg) {
+    const Batch &b = a.b;
+    const int tile = blockIdx.x;
+    const int set = b.tile_set[tile];
+    const int64_t N = b.set_steps[set], K = a.ck.every, T = b.total_traj;
+    const int64_t s0 = seg * K;
+    if (s0 >= N) return;  // uniform over the block
+    const int64_t s1 = min(s0 + K, N);
+    const abp_params p = b.params[set];
+    const Coef<float> k = make_coef<float>(p.q, p.c, p.d, p.gamma0, p.F0, p.D, p.h, p.L, p.asym, a.nz.dt);
+    const float dtf = (float)a.nz.dt;
+    const float kx = (float)(-2.0 * kPi / p.L);  // d phi / dx with the sign of d cos / d phi
+    const int64_t first = b.tile_first[tile];
+    const int count = b.tile_count[tile];
+    for (int li = threadIdx.x; li < count; li += blockDim.x) {
+        const int64_t idx = first + li;
+        const StepStream ss = step_stream((uint64_t)idx + a.nz.traj_base, a.K);
+        const float4 l0 = sv.lam[idx];
+        float lx = l0.x, lv = l0.y, le = l0.z;
+        float acc[6] = {0, 0, 0, 0, 0, 0};
+        reverse_chunks(a, k, ss, kx, dtf, idx, s0, s1, lx, lv, le, acc);
+        sv.lam[idx] = make_float4(lx, lv, le, 0.0f);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) sv.G[(size_t)q * T + idx] += (double)acc[q];
+    }
+}
+
+// Per tile: the initial-condition term, the parameter scales and the caller's
+// weights, summed in FP64 over the tile's trajectories.
+__global__ void __launch_bounds__(kThreads) adjoint_final_kernel(AdjArgs a, SegView sv) {
     __shared__ double red[kThreads / 32][6];
     const Batch &b = a.b;
     const int tile = blockIdx.x;
     const int set = b.tile_set[tile];
-    const int64_t N = b.set_steps[set];
-    const int64_t K = a.ck.every;
-    const int64_t T = b.total_traj;
+    const int64_t N = b.set_steps[set], T = b.total_traj;
     const abp_params p = b.params[set];
     const double dt = a.nz.dt;
-    const Coef<float> k = make_coef<float>(p.q, p.c, p.d, p.gamma0, p.F0, p.D, p.h, p.L, p.asym, dt);
-    const float dtf = (float)dt;
-    const float kx = (float)(-2.0 * kPi / p.L);  // d phi / dx with the sign of d cos / d phi
     const int64_t first = b.tile_first[tile];
     const int count = b.tile_count[tile];
     int64_t M = 0;
     for (int t = b.set_tile_begin[set]; t < b.set_tile_begin[set + 1]; ++t) M += b.tile_count[t];
-
     double gsum[6] = {0, 0, 0, 0, 0, 0};
-    for (int li0 = 0; li0 < count; li0 += kThreads) {  // uniform loop over the tile's slots
-        const int li = li0 + threadIdx.x;
-        const bool act = li < count && N > 0;
-        const int64_t idx = first + (li < count ? li : count - 1);
-        const StepStream ss = step_stream((uint64_t)idx + a.nz.traj_base, a.K);
-        float lx = 0.0f, lv = 0.0f, le = 0.0f;
-        double G[6] = {0, 0, 0, 0, 0, 0};
-        if (act) {
-            const int64_t n_seg = (N + K - 1) / K;
-            for (int64_t seg = n_seg - 1; seg >= 0; --seg) {
-                const int64_t s0 = seg * K, s1 = min(s0 + K, N);
-                float acc[6] = {0, 0, 0, 0, 0, 0};
-                reverse_segment(a, k, ss, kx, dtf, idx, s0, s1, a.ck.ck[(size_t)seg * T + idx], lx, lv, le, acc);
+    if (N > 0) {
+        // dmean_v/dtheta = (1 / (M N)) dJ_i/dtheta, scaled by the caller's weight
+        const double wgt = (a.w ? a.w[set] : 1.0) / ((double)M * (double)N);
+        const double Kd = dt * p.h * 0.453 * (2.0 * kPi / p.L);
+        for (int li = threadIdx.x; li < count; li += blockDim.x) {
+            const int64_t idx = first + li;
+            double G[6];
 #pragma unroll
-                for (int q = 0; q < 6; ++q) G[q] += (double)acc[q];
-            }
+            for (int q = 0; q < 6; ++q) G[q] = sv.G[(size_t)q * T + idx];
             // initial condition: v0 = sqrt(D) z depends on D
-            if (a.nz.v0_mode == 1) G[0] += (double)lv * (double)a.ck.ck[idx].z;
-        }
-        if (act) {
-            // dmean_v/dtheta = (1 / (M N)) dJ_i/dtheta, scaled by the caller's weight
-            const double wgt = (a.w ? a.w[set] : 1.0) / ((double)M * (double)N);
-            const double Kd = dt * p.h * 0.453 * (2.0 * kPi / p.L);
+            if (a.nz.v0_mode == 1) G[0] += (double)sv.lam[idx].y * (double)a.ck.ck[idx].z;
             gsum[0] += wgt * (p.D > 0.0 ? G[0] / (2.0 * p.D) : NAN);
             gsum[1] += wgt * dt * G[1];
             gsum[2] += wgt * (-dt) * G[2];
@@ -343,7 +402,9 @@ extern "C" abp_status abp_backward(abp_ctx *ctx, const double *dJ_dmean_v, doubl
     const size_t part_bytes = sizeof(double) * 6 * (size_t)std::max(ctx->n_tiles, 1);
     const size_t grad_bytes = sizeof(double) * 6 * (size_t)std::max(ctx->n_sets, 1);
     const size_t w_bytes = sizeof(double) * (size_t)std::max(ctx->n_sets, 1);
-    const size_t need = sub_bytes + part_bytes + grad_bytes + w_bytes + 4 * 256;
+    const size_t lam_bytes = sizeof(float4) * (size_t)std::max<int64_t>(T, 1);
+    const size_t g_bytes = sizeof(double) * 6 * (size_t)std::max<int64_t>(T, 1);
+    const size_t need = sub_bytes + part_bytes + grad_bytes + w_bytes + lam_bytes + g_bytes + 6 * 256;
     DevBuf &sc = ctx->d_adj;
     if (!sc.p || sc.cap < need) {
         sc.release();
@@ -362,6 +423,9 @@ extern "C" abp_status abp_backward(abp_ctx *ctx, const double *dJ_dmean_v, doubl
     double *partials = (double *)(base + align(sub_bytes));
     double *gdev = (double *)(base + align(sub_bytes) + align(part_bytes));
     double *wdev = (double *)(base + align(sub_bytes) + align(part_bytes) + align(grad_bytes));
+    SegView sv;
+    sv.lam = (float4 *)(base + align(sub_bytes) + align(part_bytes) + align(grad_bytes) + align(w_bytes));
+    sv.G = (double *)((char *)sv.lam + align(lam_bytes));
     cudaStream_t s = ctx->stream;
     cudaError_t e = cudaSuccess;
     const double *w = nullptr;
@@ -389,7 +453,17 @@ extern "C" abp_status abp_backward(abp_ctx *ctx, const double *dJ_dmean_v, doubl
             a.K.rk[2 * r] = a.nz.k0 + (uint32_t)r * kPhiloxW0;
             a.K.rk[2 * r + 1] = a.nz.k1 + (uint32_t)r * kPhiloxW1;
         }
-        adjoint_kernel<<<ctx->n_tiles, kThreads, 0, s>>>(a);
+        e = cudaMemsetAsync(sv.lam, 0, lam_bytes, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(sv.G, 0, g_bytes, s);
+        if (e != cudaSuccess) return set_err(ctx, ABP_ECUDA, "abp_backward: clear", e);
+        const int64_t Kc = ctx->cfg.checkpoint_every;
+        const int64_t n_seg = (ctx->max_steps + Kc - 1) / Kc;
+        for (int64_t seg = n_seg - 1; seg >= 0; --seg) {
+            adjoint_level1_kernel<<<ctx->n_tiles, kThreads, 0, s>>>(a, seg);
+            adjoint_reverse_kernel<<<ctx->n_tiles, kRevThreads, 0, s>>>(a, sv, seg);
+            ctx->launches += 2;
+        }
+        adjoint_final_kernel<<<ctx->n_tiles, kThreads, 0, s>>>(a, sv);
         ctx->launches += 1;
     }
     adjoint_set_kernel<<<ctx->n_sets, kThreads, 0, s>>>(ctx->batch(), partials, gdev);
