@@ -35,7 +35,7 @@ LANES_PER_SM = 128
 # DRAM bytes (read + write) per launch of the integrator on the 2,097,152-trajectory sweep grid,
 # from one ncu capture of that kernel (dram__bytes_read.sum + dram__bytes_write.sum); the traffic
 # is the state load/store, independent of the steps per launch.
-TRAFFIC_PER_LAUNCH = {"integrate_kernel<float,1>": (52555776 + 1594368, 2097152)}
+TRAFFIC_PER_LAUNCH = {"integrate_kernel<float,2>": (52503552 + 1617408, 2097152)}
 
 
 def parse():
@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the pathwise-adjoint leg")
     ap.add_argument("--visualisation", action="store_true",
                     help="also measure the per-cycle cost of reading intermediate results (iterations lost)")
+    ap.add_argument("--adjoint-only", default="",
+                    help="N_TRAJ,N_STEPS: time only the forward and backward of the differentiation workload at "
+                         "this size (profiling; prints one JSON line without the bench keys)")
     ap.add_argument("--configs", default="",
                     help="also time other workloads, comma-separated: single, uneven, force, heun, snapshots, "
                          "precision, items (or 'all'); reported under 'configs'")
@@ -168,7 +171,14 @@ def oracle_sample(w, budget_s: float, gpu_moments=None):
     parity = None
     if z:
         parity = {"sets_checked": len(z), "max_abs_dmean_over_se": max(z), "bar": 3.0, "pass": max(z) <= 3.0}
-    return done_ps / t_used, cores, desc, parity
+    # the same oracle on one core: 64 trajectories of the first set, all its steps
+    i = order[0]
+    m1 = min(64, w.n_traj[i])
+    t0 = time.perf_counter()
+    O.run_set(w.sets[i], seed=w.seed, dt=w.dt, n_traj=m1, n_steps=w.n_steps[i], traj_base=base[i], v0_mode=w.v0_mode,
+              n_threads=1)
+    one_core = m1 * w.n_steps[i] / (time.perf_counter() - t0)
+    return done_ps / t_used, cores, desc, parity, one_core
 
 
 def run_reference(args, rank, world):
@@ -235,7 +245,7 @@ def config_dict(w, args, extra=None):
 
 # ----------------------------------------------------------------------------- adjoint leg
 
-def adjoint_leg(A, stream, small=False):
+def adjoint_leg(A, stream, small=False, size=None, accuracy=True):
     """Pathwise adjoint of <v> w.r.t. (D, q, c, d, gamma0, a).
 
     Cost: forward (with checkpoints every 1,000 steps) and backward on the differentiation
@@ -252,7 +262,10 @@ def adjoint_leg(A, stream, small=False):
     from oracle import oracle as O
     from paper_1104_2499_gb300 import workloads as W
 
-    w = W.differentiation(n_traj=1 << 16, n_steps=20_000) if small else W.differentiation()
+    if size is not None:
+        w = W.differentiation(n_traj=size[0], n_steps=size[1])
+    else:
+        w = W.differentiation(n_traj=1 << 16, n_steps=20_000) if small else W.differentiation()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     with A.Ensemble(w, stream=stream) as ens, torch.cuda.stream(stream):
         ens.set_params()
@@ -290,7 +303,7 @@ def adjoint_leg(A, stream, small=False):
                 "max_err_vs_tangent_linear_over_largest": float(np.max(np.abs(g_gpu - g_tl)) / scale),
                 "bar": 1e-3, "fd": "oracle FP64, common random numbers"}
 
-    acc = [check(1000, 1e-4, 200), check(2000, 1e-6, 1000)]
+    acc = [check(1000, 1e-4, 200), check(2000, 1e-6, 1000)] if accuracy else None
     return {"workload": w.name, "particle_steps": w.particle_steps, "checkpoint_every": w.checkpoint_every,
             "forward_ms": fwd_ms, "backward_ms": bwd_ms, "backward_over_forward": bwd_ms / fwd_ms,
             "max_abs_pathwise_grad_full_horizon": float(np.max(np.abs(g_full))),
@@ -307,7 +320,10 @@ def visualisation_leg(A, stream):
     ensemble (the mean-velocity-versus-load curve, Fig. 2) and waits for it.  'device': the
     result stays in device memory (the analogue of shared CL/GL buffers); 'host': it is copied
     into pinned host memory every cycle (the analogue of the non-shared method).  Cycle time
-    is fitted linearly in T; offset / slope = iterations lost."""
+    is fitted linearly in T; offset / slope = iterations lost.  'live_T*': the library streams a
+    snapshot (moments of every set) every T steps to pinned host memory on its own stream while
+    the integration goes on (abp_live); iterations lost = the extra time per snapshot over the
+    same run without live results, in iterations."""
     import numpy as np
     import torch
     from paper_1104_2499_gb300 import workloads as W
@@ -337,6 +353,31 @@ def visualisation_leg(A, stream):
                 slope, offset = np.polyfit(np.array(xs, float), np.array(ys), 1)
                 res[method] = {"us_per_iteration": slope * 1e6, "offset_us": offset * 1e6,
                                "iterations_lost": offset / slope}
+        # live results: snapshots every T steps streamed to pinned host memory by the library
+        # while the integration continues; cost = extra time per snapshot over the same steps
+        # integrated without live results
+        for T in (250, 1000):
+            n_cycles = 40
+            wl = W.force_sweep(n_F=n_items, traj_per_set=1, n_steps=n_cycles * T)
+            wl.snapshot_every = T
+            with A.Ensemble(wl, stream=stream) as ens, torch.cuda.stream(stream):
+                ens.set_params()
+                mom_l = torch.empty((ens.n_snapshots(), n_items, 8), dtype=torch.float64, pin_memory=True)
+                times = {}
+                for mode in ("plain", "live", "plain", "live"):
+                    A.abp_live(ens.ctx, mom_l if mode == "live" else None, None, None)
+                    ens.reset()
+                    ens.synchronize()
+                    t0 = time.perf_counter()
+                    ens.integrate(-1)
+                    ens.synchronize()
+                    times[mode] = time.perf_counter() - t0
+                assert A.abp_live_ready(ens.ctx) == n_cycles
+                A.abp_live(ens.ctx, None, None, None)
+            per_it = times["plain"] / (n_cycles * T)
+            extra = (times["live"] - times["plain"]) / n_cycles
+            res["live_T%d" % T] = {"us_per_iteration": per_it * 1e6, "extra_us_per_snapshot": extra * 1e6,
+                                   "iterations_lost": extra / per_it}
         out["%d_work_items" % n_items] = res
     return out
 
@@ -513,8 +554,12 @@ def main():
         B.build()
     A.lib()
 
-    w = workload(args)
     stream = torch.cuda.Stream()
+    if args.adjoint_only:
+        n_traj, n_steps = (int(v) for v in args.adjoint_only.split(","))
+        print(json.dumps({"adjoint": adjoint_leg(A, stream, size=(n_traj, n_steps), accuracy=False)}), flush=True)
+        return
+    w = workload(args)
     props = torch.cuda.get_device_properties(local)
     n_sm = props.multi_processor_count
     # weak scaling: every rank integrates its own copy of the sweep with distinct trajectory ids
@@ -636,8 +681,9 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, cores, desc, parity = oracle_sample(w, args.cpu_seconds, gpu_moments=moments)
-        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+        rate, cores, desc, parity, one_core = oracle_sample(w, args.cpu_seconds, gpu_moments=moments)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
+               "value_1_core": one_core}
         if parity:
             cpu["parity_mean_v"] = parity
 

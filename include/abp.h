@@ -167,8 +167,34 @@ ABP_API abp_status abp_progress(const abp_ctx *ctx, int64_t *steps_done);
  * in a fixed order, so results are bitwise reproducible. */
 ABP_API abp_status abp_reduce(abp_ctx *ctx, double *moments, uint32_t *hist_x, uint32_t *hist_v);
 
-/* Number of snapshot slots of the current batch (host output). */
+/* Number of snapshot slots of the current batch (host output): the longest
+ * set's step count divided by snapshot_every when snapshot_every > 0; else 1
+ * when there are histograms (the final state) and 0 without. */
 ABP_API abp_status abp_num_snapshots(const abp_ctx *ctx, int64_t *n_snap);
+
+/* Live results while the integration runs (the headless counterpart of the
+ * results the paper shows during a run, Sec. 3.2 and Table 1).  After this
+ * call, abp_integrate stops its launches at every snapshot step k S (S =
+ * snapshot_every > 0), computes the ensemble moments at that step on the
+ * device, and copies snapshot k -- its moments and its histogram rows -- into
+ * the caller's host buffers on a second stream, while the next steps are
+ * already integrating.  Buffers (page-locked host memory, from cudaMallocHost
+ * or cudaHostRegister; any may be NULL; owned by the caller, who keeps them
+ * alive until abp_live_ready reports the last snapshot or the context is
+ * synchronised):
+ *   moments  [n_snap][n_sets][8] doubles, the layout of abp_reduce at step k S
+ *   hist_x   [n_snap][n_sets][hist_x_bins] uint32 (needs hist_x_bins > 0)
+ *   hist_v   [n_snap][n_sets][hist_v_bins + 2] uint32 (needs hist_v_bins > 0)
+ * n_snap = abp_num_snapshots.  All three NULL switches live results off.
+ * Requires abp_set_params first (the buffers are sized by the batch) and
+ * snapshot_every > 0; pageable memory is rejected (ABP_EINVAL), because a copy
+ * from it would stall the integration.  Snapshots completed before this call
+ * are not sent. */
+ABP_API abp_status abp_live(abp_ctx *ctx, double *moments, uint32_t *hist_x, uint32_t *hist_v);
+
+/* How many snapshots, counted from the first, have fully arrived in the live
+ * host buffers (host output; never waits). */
+ABP_API abp_status abp_live_ready(abp_ctx *ctx, int64_t *n_ready);
 
 /* Final (current) state of every trajectory, in global trajectory order
  * (host or device outputs, each of sum(n_traj) doubles; any may be NULL):
@@ -226,7 +252,8 @@ ABP_API abp_status abp_tiles(const abp_ctx *ctx, int32_t *n_tiles, int32_t *n_pa
 /* Number of kernels this context has enqueued since it was created (host output). */
 ABP_API abp_status abp_kernel_launches(const abp_ctx *ctx, int64_t *launches);
 
-/* Wait for the context's stream and report any device-side failure. */
+/* Wait for the context's stream (and its live-result copies) and report any
+ * device-side failure. */
 ABP_API abp_status abp_synchronize(abp_ctx *ctx);
 
 /* Release the context and every buffer it owns.  NULL is allowed. */

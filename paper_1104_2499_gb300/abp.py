@@ -92,6 +92,10 @@ def lib():
                                  C.POINTER(C.c_int32)]
         L.abp_tuning.restype = st
         L.abp_tiles.argtypes = [_VP, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+        L.abp_live.argtypes = [_VP, _VP, _VP, _VP]
+        L.abp_live.restype = st
+        L.abp_live_ready.argtypes = [_VP, C.POINTER(C.c_int64)]
+        L.abp_live_ready.restype = st
         L.abp_tiles.restype = st
         L.abp_integrate.argtypes = [_VP, C.c_int64]
         L.abp_integrate.restype = st
@@ -197,6 +201,18 @@ def abp_tiles(ctx):
     t, p, n = C.c_int32(), C.c_int32(), C.c_int32()
     _check(lib().abp_tiles(ctx, C.byref(t), C.byref(p), C.byref(n)), ctx)
     return {"tiles": t.value, "packed": p.value, "narrow": n.value}
+
+
+def abp_live(ctx, moments=None, hist_x=None, hist_v=None):
+    """Stream every snapshot (moments [n_snap, n_sets, 8] float64, histograms int32) into
+    page-locked host tensors while the integration runs; all None switches it off."""
+    _check(lib().abp_live(ctx, _ptr(moments), _ptr(hist_x), _ptr(hist_v)), ctx)
+
+
+def abp_live_ready(ctx) -> int:
+    n = C.c_int64()
+    _check(lib().abp_live_ready(ctx, C.byref(n)), ctx)
+    return n.value
 
 
 def abp_integrate(ctx, max_steps: int = -1):

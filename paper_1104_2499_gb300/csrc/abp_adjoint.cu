@@ -36,6 +36,10 @@ namespace {
 #endif
 // Threads per block of the register-heavy reverse kernel (a multiple of 32).
 constexpr int kRevThreads = ABP_ADJ_REV_THREADS;
+// Threads per block of the level-1 kernel: small blocks, so that one fits on
+// an SM beside the reverse kernel's blocks and fills the issue slots they
+// leave idle.
+constexpr int kL1Threads = 128;
 constexpr int kSub = ABP_ADJ_SUB;  // steps per register-resident sub-chunk (a multiple of 4)
 static_assert(kSub % 4 == 0 && (kBlockSteps % kSub) == 0, "sub-chunks hold whole Philox blocks");
 
@@ -253,19 +257,24 @@ __device__ __forceinline__ void reverse_chunks(const AdjArgs &a, const Coef<floa
 }
 
 // One launch per segment index and level, segments in reverse order: level 1
-// (a plain forward re-run, light on registers, so it runs at the integrator's
-// occupancy) for segment `seg` of every trajectory, then level 2 and the
-// reverse sweep (register-heavy) for the same segment.  Between launches each
-// trajectory keeps its adjoint state lambda = (x, v, e) and its six gradient
-// sums in global memory.  Trajectories of sets shorter than seg K skip.
+// (a plain forward re-run, light on registers) for segment `seg` of every
+// trajectory, then level 2 and the reverse sweep (register-heavy) for the same
+// segment.  The level-1 launch of segment seg - 1 runs on a second stream
+// while the reverse sweep of segment seg runs, into the other of two
+// sub-checkpoint buffers.  Between launches each trajectory keeps its adjoint
+// state lambda = (x, v, e) and its six gradient sums in global memory.
+// Trajectories of sets shorter than seg K skip.
 struct SegView {
     float4 *lam;  // [total_traj] (lambda_x, lambda_v, lambda_e, -)
     double *G;    // [6][total_traj] gradient sums
 };
 
-__global__ void __launch_bounds__(kThreads) adjoint_level1_kernel(AdjArgs a, int64_t seg) {
+// Both per-segment kernels run `sub` blocks per tile, block j of a tile taking
+// its trajectories [j blockDim, (j + 1) blockDim): one trajectory per thread.
+__global__ void __launch_bounds__(kL1Threads) adjoint_level1_kernel(AdjArgs a, int64_t seg, int sub) {
     const Batch &b = a.b;
-    const int tile = blockIdx.x;
+    const int tile = (int)blockIdx.x / sub;
+    const int li = ((int)blockIdx.x % sub) * (int)blockDim.x + (int)threadIdx.x;
     const int set = b.tile_set[tile];
     const int64_t N = b.set_steps[set], K = a.ck.every, T = b.total_traj;
     const int64_t s0 = seg * K;
@@ -273,19 +282,17 @@ __global__ void __launch_bounds__(kThreads) adjoint_level1_kernel(AdjArgs a, int
     const int64_t s1 = min(s0 + K, N);
     const abp_params p = b.params[set];
     const Coef<float> k = make_coef<float>(p.q, p.c, p.d, p.gamma0, p.F0, p.D, p.h, p.L, p.asym, a.nz.dt);
-    const int64_t first = b.tile_first[tile];
-    const int count = b.tile_count[tile];
-    for (int li = threadIdx.x; li < count; li += blockDim.x) {
-        const int64_t idx = first + li;
-        const StepStream ss = step_stream((uint64_t)idx + a.nz.traj_base, a.K);
-        level1_segment(a, k, ss, idx, s0, s1, a.ck.ck[(size_t)seg * T + idx]);
-    }
+    if (li >= b.tile_count[tile]) return;
+    const int64_t idx = b.tile_first[tile] + li;
+    const StepStream ss = step_stream((uint64_t)idx + a.nz.traj_base, a.K);
+    level1_segment(a, k, ss, idx, s0, s1, a.ck.ck[(size_t)seg * T + idx]);
 }
 
 __global__ void __launch_bounds__(kRevThreads, ABP_ADJ_MIN_BLOCKS) adjoint_reverse_kernel(AdjArgs a, SegView sv,
-                                                                                          int64_t seg) {
+                                                                                          int64_t seg, int sub) {
     const Batch &b = a.b;
-    const int tile = blockIdx.x;
+    const int tile = (int)blockIdx.x / sub;
+    const int li = ((int)blockIdx.x % sub) * (int)blockDim.x + (int)threadIdx.x;
     const int set = b.tile_set[tile];
     const int64_t N = b.set_steps[set], K = a.ck.every, T = b.total_traj;
     const int64_t s0 = seg * K;
@@ -295,19 +302,16 @@ __global__ void __launch_bounds__(kRevThreads, ABP_ADJ_MIN_BLOCKS) adjoint_rever
     const Coef<float> k = make_coef<float>(p.q, p.c, p.d, p.gamma0, p.F0, p.D, p.h, p.L, p.asym, a.nz.dt);
     const float dtf = (float)a.nz.dt;
     const float kx = (float)(-2.0 * kPi / p.L);  // d phi / dx with the sign of d cos / d phi
-    const int64_t first = b.tile_first[tile];
-    const int count = b.tile_count[tile];
-    for (int li = threadIdx.x; li < count; li += blockDim.x) {
-        const int64_t idx = first + li;
-        const StepStream ss = step_stream((uint64_t)idx + a.nz.traj_base, a.K);
-        const float4 l0 = sv.lam[idx];
-        float lx = l0.x, lv = l0.y, le = l0.z;
-        float acc[6] = {0, 0, 0, 0, 0, 0};
-        reverse_chunks(a, k, ss, kx, dtf, idx, s0, s1, lx, lv, le, acc);
-        sv.lam[idx] = make_float4(lx, lv, le, 0.0f);
+    if (li >= b.tile_count[tile]) return;
+    const int64_t idx = b.tile_first[tile] + li;
+    const StepStream ss = step_stream((uint64_t)idx + a.nz.traj_base, a.K);
+    const float4 l0 = sv.lam[idx];
+    float lx = l0.x, lv = l0.y, le = l0.z;
+    float acc[6] = {0, 0, 0, 0, 0, 0};
+    reverse_chunks(a, k, ss, kx, dtf, idx, s0, s1, lx, lv, le, acc);
+    sv.lam[idx] = make_float4(lx, lv, le, 0.0f);
 #pragma unroll
-        for (int q = 0; q < 6; ++q) sv.G[(size_t)q * T + idx] += (double)acc[q];
-    }
+    for (int q = 0; q < 6; ++q) sv.G[(size_t)q * T + idx] += (double)acc[q];
 }
 
 // Per tile: the initial-condition term, the parameter scales and the caller's
@@ -398,7 +402,8 @@ extern "C" abp_status abp_backward(abp_ctx *ctx, const double *dJ_dmean_v, doubl
         return set_err(ctx, ABP_ESTATE, "abp_backward after abp_load: the checkpoints do not cover the run from step 0");
     const int64_t T = ctx->total_traj;
     const int64_t n_sub = (ctx->cfg.checkpoint_every + kSub - 1) / kSub;
-    const size_t sub_bytes = sizeof(float4) * (size_t)n_sub * (size_t)T;
+    const size_t sub1_bytes = sizeof(float4) * (size_t)n_sub * (size_t)T;
+    const size_t sub_bytes = 2 * ((sub1_bytes + 255) & ~(size_t)255);  // two buffers, alternating by segment
     const size_t part_bytes = sizeof(double) * 6 * (size_t)std::max(ctx->n_tiles, 1);
     const size_t grad_bytes = sizeof(double) * 6 * (size_t)std::max(ctx->n_sets, 1);
     const size_t w_bytes = sizeof(double) * (size_t)std::max(ctx->n_sets, 1);
@@ -419,7 +424,7 @@ extern "C" abp_status abp_backward(abp_ctx *ctx, const double *dJ_dmean_v, doubl
     sc.bytes = need;
     auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
     char *base = (char *)sc.p;
-    float4 *sub = (float4 *)base;
+    float4 *sub[2] = {(float4 *)base, (float4 *)(base + ((sub1_bytes + 255) & ~(size_t)255))};
     double *partials = (double *)(base + align(sub_bytes));
     double *gdev = (double *)(base + align(sub_bytes) + align(part_bytes));
     double *wdev = (double *)(base + align(sub_bytes) + align(part_bytes) + align(grad_bytes));
@@ -445,7 +450,7 @@ extern "C" abp_status abp_backward(abp_ctx *ctx, const double *dJ_dmean_v, doubl
         a.b = ctx->batch();
         a.ck = ctx->ckpt();
         a.nz = ctx->noise();
-        a.sub = sub;
+        a.sub = sub[0];
         a.n_sub = n_sub;
         a.w = w;
         a.partials = partials;
@@ -456,13 +461,46 @@ extern "C" abp_status abp_backward(abp_ctx *ctx, const double *dJ_dmean_v, doubl
         e = cudaMemsetAsync(sv.lam, 0, lam_bytes, s);
         if (e == cudaSuccess) e = cudaMemsetAsync(sv.G, 0, g_bytes, s);
         if (e != cudaSuccess) return set_err(ctx, ABP_ECUDA, "abp_backward: clear", e);
+        if (!ctx->aux) {
+            e = cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking);
+            for (int i = 0; e == cudaSuccess && i < 5; ++i)
+                e = cudaEventCreateWithFlags(&ctx->adj_ev[i], cudaEventDisableTiming);
+            if (e != cudaSuccess) {
+                ctx->release_streams();
+                return set_err(ctx, ABP_ECUDA, "abp_backward: stream set-up", e);
+            }
+        }
+        cudaStream_t s2 = ctx->aux;
+        cudaEvent_t *l1_done = ctx->adj_ev, *rev_done = ctx->adj_ev + 2, start = ctx->adj_ev[4];
         const int64_t Kc = ctx->cfg.checkpoint_every;
         const int64_t n_seg = (ctx->max_steps + Kc - 1) / Kc;
-        for (int64_t seg = n_seg - 1; seg >= 0; --seg) {
-            adjoint_level1_kernel<<<ctx->n_tiles, kThreads, 0, s>>>(a, seg);
-            adjoint_reverse_kernel<<<ctx->n_tiles, kRevThreads, 0, s>>>(a, sv, seg);
+        // level 1 of segment j writes buffer j % 2; it may start once the reverse
+        // sweep of segment j + 2, the last reader of that buffer, has finished
+        e = cudaEventRecord(start, s);  // the checkpoints of the forward are complete
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s2, start, 0);
+        // blocks per tile: tiles hold up to kThreads * ppt trajectories
+        const int cap = kThreads * std::max(ctx->ppt, 1);
+        const int sub1 = (cap + kL1Threads - 1) / kL1Threads, sub2 = (cap + kRevThreads - 1) / kRevThreads;
+        auto level1 = [&](int64_t j) {
+            AdjArgs aj = a;
+            aj.sub = sub[j & 1];
+            adjoint_level1_kernel<<<(unsigned)((int64_t)ctx->n_tiles * sub1), kL1Threads, 0, s2>>>(aj, j, sub1);
+            return cudaEventRecord(l1_done[j & 1], s2);
+        };
+        if (e == cudaSuccess && n_seg > 0) e = level1(n_seg - 1);
+        for (int64_t seg = n_seg - 1; e == cudaSuccess && seg >= 0; --seg) {
+            if (seg > 0) {
+                if (seg + 1 < n_seg) e = cudaStreamWaitEvent(s2, rev_done[(seg + 1) & 1], 0);
+                if (e == cudaSuccess) e = level1(seg - 1);
+            }
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, l1_done[seg & 1], 0);
+            AdjArgs as = a;
+            as.sub = sub[seg & 1];
+            adjoint_reverse_kernel<<<(unsigned)((int64_t)ctx->n_tiles * sub2), kRevThreads, 0, s>>>(as, sv, seg, sub2);
+            if (e == cudaSuccess) e = cudaEventRecord(rev_done[seg & 1], s);
             ctx->launches += 2;
         }
+        if (e != cudaSuccess) return set_err(ctx, ABP_ECUDA, "abp_backward: launch", e);
         adjoint_final_kernel<<<ctx->n_tiles, kThreads, 0, s>>>(a, sv);
         ctx->launches += 1;
     }

@@ -450,6 +450,7 @@ void abp_destroy(abp_ctx *ctx) {
     if (!ctx) return;
     cudaStreamSynchronize(ctx->stream);
     ctx->release_all();
+    ctx->release_streams();
     ctx->d_status.release();
     delete ctx;
 }
@@ -569,7 +570,9 @@ abp_status abp_set_params(abp_ctx *ctx, int32_t n_sets, const abp_params *sets, 
     }
     const abp_config &c = ctx->cfg;
     const bool any_hist = c.hist_x_bins > 0 || c.hist_v_bins > 0;
-    ctx->n_snap = any_hist ? (c.snapshot_every > 0 ? max_n / c.snapshot_every : 1) : 0;
+    // snapshot slots: one per S steps when snapshot_every = S > 0 (histograms and live
+    // results use them), else one final histogram snapshot when there are histograms
+    ctx->n_snap = c.snapshot_every > 0 ? max_n / c.snapshot_every : (any_hist ? 1 : 0);
     ctx->n_ckpt = c.checkpoint_every > 0 ? max_n / c.checkpoint_every + 1 : 0;
     // Work-queue order: tiles by decreasing step count of their set (stable).
     ctx->perm.resize(ctx->n_tiles);
@@ -659,6 +662,8 @@ abp_status abp_reset(abp_ctx *ctx, uint64_t seed) {
     ctx->cfg.seed = seed;
     ctx->g = 0;
     ctx->ckpt_complete = true;
+    if (ctx->live_stream) cudaStreamSynchronize(ctx->live_stream);  // copies of the previous run end first
+    ctx->live_sent = ctx->live_ready = 0;
     cudaStream_t s = ctx->stream;
     cudaError_t e = cudaMemsetAsync(ctx->d_status.p, 0, sizeof(int32_t), s);
     if (e == cudaSuccess && ctx->d_hx.bytes) e = cudaMemsetAsync(ctx->d_hx.p, 0, ctx->d_hx.bytes, s);
@@ -798,6 +803,45 @@ abp_status run_window(abp_ctx *ctx, int64_t g0, int64_t g1) {
     return e == cudaSuccess ? ABP_OK : cuda_fail(ctx, e, "integrator launch");
 }
 
+// Live results: the moments at step (k + 1) S on the device, then snapshot k's
+// moments and histogram rows copied to the caller's page-locked buffers on the
+// live stream, which waits for the main stream to reach this point.  Up to
+// kLiveRing snapshots may be in flight; an older one is waited for first.
+abp_status send_snapshot(abp_ctx *ctx, int64_t k) {
+    cudaStream_t s = ctx->stream, ls = ctx->live_stream;
+    const int R = abp_ctx::kLiveRing;
+    const int slot = (int)(k % R);
+    cudaError_t e = cudaSuccess;
+    if (k - ctx->live_ready >= R) {  // the ring slot still belongs to snapshot k - R
+        e = cudaEventSynchronize(ctx->live_copied[slot]);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "live copy");
+        ctx->live_ready = k - R + 1;
+    }
+    const size_t ns = (size_t)ctx->n_sets;
+    double *dmom = ctx->live_mom ? (double *)ctx->d_live_mom.p + (size_t)k * ns * 8 : nullptr;
+    if (dmom) {
+        e = launch_reduce(ctx->batch(), ctx->state(), ctx->noise(), ctx->g, (double *)ctx->d_partials.p, dmom, s);
+        ctx->launches += (ctx->n_sets > 0 && ctx->n_single > 0 ? 1 : 0) + (ctx->n_unpacked > 0 ? 1 : 0) +
+                         (ctx->n_sets > ctx->n_unpacked ? 1 : 0);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->live_done[slot], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ls, ctx->live_done[slot], 0);
+    if (e == cudaSuccess && dmom)
+        e = cudaMemcpyAsync(ctx->live_mom + (size_t)k * ns * 8, dmom, sizeof(double) * 8 * ns, cudaMemcpyDeviceToHost,
+                            ls);
+    const size_t bx = (size_t)ctx->cfg.hist_x_bins, bv = ctx->cfg.hist_v_bins > 0 ? (size_t)ctx->cfg.hist_v_bins + 2 : 0;
+    if (e == cudaSuccess && ctx->live_hx)
+        e = cudaMemcpyAsync(ctx->live_hx + (size_t)k * ns * bx, (const uint32_t *)ctx->d_hx.p + (size_t)k * ns * bx,
+                            sizeof(uint32_t) * ns * bx, cudaMemcpyDeviceToHost, ls);
+    if (e == cudaSuccess && ctx->live_hv)
+        e = cudaMemcpyAsync(ctx->live_hv + (size_t)k * ns * bv, (const uint32_t *)ctx->d_hv.p + (size_t)k * ns * bv,
+                            sizeof(uint32_t) * ns * bv, cudaMemcpyDeviceToHost, ls);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->live_copied[slot], ls);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "live snapshot");
+    ctx->live_sent = k + 1;
+    return ABP_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -807,9 +851,84 @@ abp_status abp_integrate(abp_ctx *ctx, int64_t max_steps) {
     if (!ctx->have_batch) return fail(ctx, ABP_ESTATE, "abp_integrate before abp_set_params");
     const int64_t target = max_steps < 0 ? ctx->max_steps : std::min(ctx->max_steps, ctx->g + max_steps);
     if (target <= ctx->g) return ABP_OK;
-    const abp_status st = run_window(ctx, ctx->g, target);
-    if (st != ABP_OK) return st;
-    ctx->g = target;
+    if (!ctx->live) {
+        const abp_status st = run_window(ctx, ctx->g, target);
+        if (st != ABP_OK) return st;
+        ctx->g = target;
+        return ABP_OK;
+    }
+    // live results: windows end at the snapshot steps, each followed by its snapshot's copy
+    const int64_t S = ctx->cfg.snapshot_every;
+    while (ctx->g < target) {
+        const int64_t end = std::min(target, (ctx->g / S + 1) * S);
+        abp_status st = run_window(ctx, ctx->g, end);
+        if (st != ABP_OK) return st;
+        ctx->g = end;
+        if (end % S == 0 && end / S - 1 < ctx->n_snap && end / S - 1 == ctx->live_sent)
+            if ((st = send_snapshot(ctx, end / S - 1)) != ABP_OK) return st;
+    }
+    return ABP_OK;
+}
+
+abp_status abp_live(abp_ctx *ctx, double *moments, uint32_t *hist_x, uint32_t *hist_v) {
+    if (!ctx) return ABP_EINVAL;
+    if (!ctx->have_batch) return fail(ctx, ABP_ESTATE, "abp_live before abp_set_params");
+    if (ctx->live_stream) {
+        cudaError_t e = cudaStreamSynchronize(ctx->live_stream);  // copies into the previous buffers end first
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "live stream synchronise");
+    }
+    if (!moments && !hist_x && !hist_v) {
+        ctx->live = false;
+        ctx->live_mom = nullptr;
+        ctx->live_hx = ctx->live_hv = nullptr;
+        return ABP_OK;
+    }
+    if (ctx->cfg.snapshot_every <= 0) return fail(ctx, ABP_EINVAL, "abp_live needs snapshot_every > 0");
+    if (hist_x && ctx->cfg.hist_x_bins <= 0) return fail(ctx, ABP_EINVAL, "abp_live: hist_x given, hist_x_bins = 0");
+    if (hist_v && ctx->cfg.hist_v_bins <= 0) return fail(ctx, ABP_EINVAL, "abp_live: hist_v given, hist_v_bins = 0");
+    for (const void *p : {(const void *)moments, (const void *)hist_x, (const void *)hist_v}) {
+        if (!p) continue;
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, p) != cudaSuccess || a.type != cudaMemoryTypeHost) {
+            cudaGetLastError();
+            return fail(ctx, ABP_EINVAL, "abp_live: buffers must be page-locked host memory");
+        }
+    }
+    cudaError_t e = cudaSuccess;
+    if (!ctx->live_stream) {
+        e = cudaStreamCreateWithFlags(&ctx->live_stream, cudaStreamNonBlocking);
+        for (int i = 0; e == cudaSuccess && i < abp_ctx::kLiveRing; ++i) {
+            e = cudaEventCreateWithFlags(&ctx->live_done[i], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->live_copied[i], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) {
+            ctx->release_streams();
+            return cuda_fail(ctx, e, "live stream set-up");
+        }
+    }
+    if (moments) {
+        const abp_status st =
+            alloc(ctx, ctx->d_live_mom, sizeof(double) * 8 * (size_t)std::max<int64_t>(ctx->n_snap, 1) *
+                                            (size_t)std::max(ctx->n_sets, 1), "live moments");
+        if (st != ABP_OK) return st;
+    }
+    ctx->live = true;
+    ctx->live_mom = moments;
+    ctx->live_hx = hist_x;
+    ctx->live_hv = hist_v;
+    ctx->live_sent = ctx->live_ready = std::min(ctx->g / ctx->cfg.snapshot_every, ctx->n_snap);
+    return ABP_OK;
+}
+
+abp_status abp_live_ready(abp_ctx *ctx, int64_t *n_ready) {
+    if (!ctx || !n_ready) return ABP_EINVAL;
+    while (ctx->live && ctx->live_ready < ctx->live_sent) {
+        const cudaError_t e = cudaEventQuery(ctx->live_copied[ctx->live_ready % abp_ctx::kLiveRing]);
+        if (e == cudaErrorNotReady) break;
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "live copy");
+        ++ctx->live_ready;
+    }
+    *n_ready = ctx->live_ready;
     return ABP_OK;
 }
 
@@ -1033,6 +1152,7 @@ abp_status abp_get_state(abp_ctx *ctx, double *x, double *x0, double *v, double 
 abp_status abp_synchronize(abp_ctx *ctx) {
     if (!ctx) return ABP_EINVAL;
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess && ctx->live_stream) e = cudaStreamSynchronize(ctx->live_stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "stream synchronise");
     int32_t status = 0;
     e = cudaMemcpy(&status, ctx->d_status.p, sizeof(int32_t), cudaMemcpyDeviceToHost);

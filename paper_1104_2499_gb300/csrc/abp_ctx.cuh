@@ -90,6 +90,19 @@ struct abp_ctx {
     DevBuf d_hx, d_hv, d_ckpt, d_partials, d_moments, d_status;
     DevBuf d_queue, d_round, d_perm;  // work queue: head + done[n_tiles]; round starts; tile order
     DevBuf d_adj;  // adjoint scratch
+    cudaStream_t aux = nullptr;  // second stream of abp_backward (level-1 re-runs beside the reverse sweep)
+    cudaEvent_t adj_ev[5] = {};  // its ordering events
+
+    // Live results (abp_live): snapshot k is copied to the caller's page-locked
+    // buffers on live_stream once the main stream has passed step (k + 1) S.
+    static constexpr int kLiveRing = 64;  // events kept for snapshots in flight
+    bool live = false;
+    double *live_mom = nullptr;
+    uint32_t *live_hx = nullptr, *live_hv = nullptr;
+    int64_t live_sent = 0, live_ready = 0;  // snapshots enqueued / known to have arrived
+    cudaStream_t live_stream = nullptr;
+    cudaEvent_t live_done[kLiveRing] = {}, live_copied[kLiveRing] = {};
+    DevBuf d_live_mom;  // [n_snap][n_sets][8] moments at the snapshot steps
 
     Batch batch() const {
         Batch b;
@@ -162,17 +175,44 @@ struct abp_ctx {
     }
     void release_batch() {
         // Buffers are kept (and reused by the next batch when large enough);
-        // see release_all() for freeing them.
+        // see release_all() for freeing them.  Live results stop: their
+        // buffers were sized by the batch.
+        if (live_stream) cudaStreamSynchronize(live_stream);
         drop_graphs();
         have_batch = false;
+        live = false;
+        live_mom = nullptr;
+        live_hx = live_hv = nullptr;
+        live_sent = live_ready = 0;
+    }
+    void release_streams() {
+        if (live_stream) cudaStreamSynchronize(live_stream);
+        for (cudaEvent_t *arr : {adj_ev + 0, live_done + 0, live_copied + 0}) {
+            const int n = arr == adj_ev ? 5 : kLiveRing;
+            for (int i = 0; i < n; ++i)
+                if (arr[i]) {
+                    cudaEventDestroy(arr[i]);
+                    arr[i] = nullptr;
+                }
+        }
+        if (live_stream) {
+            cudaStreamDestroy(live_stream);
+            live_stream = nullptr;
+        }
+        if (aux) {
+            cudaStreamDestroy(aux);
+            aux = nullptr;
+        }
     }
     void release_all() {
+        if (live_stream) cudaStreamSynchronize(live_stream);
         drop_graphs();
         for (DevBuf *b : {&d_queue, &d_round, &d_perm, &d_set_first, &d_set_order, &d_params, &d_steps, &d_set_tile_begin, &d_tile_first, &d_tile_count, &d_tile_set, &d_y,
                           &d_yacc, &d_ylo, &d_v, &d_e, &d_y0, &d_cell, &d_hx, &d_hv, &d_ckpt, &d_partials,
-                          &d_moments, &d_adj})
+                          &d_moments, &d_adj, &d_live_mom})
             b->release();
         have_batch = false;
+        live = false;
     }
 };
 
