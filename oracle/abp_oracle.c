@@ -242,6 +242,44 @@ static void tangent_step(const or_params *p, double dt, double z, const double s
     t[2] = de + dt * de_rate;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Marsaglia's xorshift generator with four 32-bit words of state (G. Marsaglia,
+ * "Xorshift RNGs", J. Stat. Softw. 8(14), 2003; the variant with shifts
+ * 11, 8, 19), the RNG of the paper's Fig. 1, kept as an option beside the
+ * counter-based Philox stream.  One call advances the state (x, y, z, w) to
+ * (y, z, w, w ^ (w >> 19) ^ t ^ (t >> 8)) with t = x ^ (x << 11) and returns
+ * the new w.  Each trajectory seeds its own state from the Philox block of
+ * counter 2^63 + 1 (the initial condition uses 2^63); an all-zero state (never
+ * met in practice) becomes (0, 0, 0, 1).  Each step draws two words (u1, u2) and
+ * uses the cosine branch of Box-Muller, one "xorshift, Box-Muller" per iteration
+ * as in Fig. 1. */
+uint32_t or_xorshift128_step(uint32_t s[4])
+{
+    const uint32_t t = s[0] ^ (s[0] << 11);
+    s[0] = s[1];
+    s[1] = s[2];
+    s[2] = s[3];
+    s[3] = s[3] ^ (s[3] >> 19) ^ t ^ (t >> 8);
+    return s[3];
+}
+
+void or_xorshift_seed(uint64_t seed, uint64_t traj, uint32_t s[4])
+{
+    or_noise_words(seed, traj, ((uint64_t)1 << 63) + 1, s);
+    if ((s[0] | s[1] | s[2] | s[3]) == 0)
+        s[3] = 1;
+}
+
+/* The normal of the next step of an xorshift stream. */
+double or_xorshift_normal(uint32_t s[4])
+{
+    double z[2];
+    const uint32_t wa = or_xorshift128_step(s);
+    const uint32_t wb = or_xorshift128_step(s);
+    or_box_muller(wa, wb, z);
+    return z[0];
+}
+
 /* Initial condition of global trajectory `traj` (counter m = 2^63). */
 void or_initial_state(const or_params *p, uint64_t seed, int32_t v0_mode, uint64_t traj,
                       double s[3])
@@ -274,8 +312,10 @@ typedef struct {
     int32_t hist_x_bins;    /* 0: no position histogram */
     int32_t hist_v_bins;    /* 0: no velocity histogram */
     double v_lo, v_hi;
-    int32_t want_grad;      /* Euler-Maruyama only */
+    int32_t want_grad;      /* Euler-Maruyama with Philox noise only */
     int32_t scheme;         /* 0: Euler-Maruyama (the paper's), 1: stochastic Heun */
+    int32_t noise;          /* 0: Philox4x32-10 by (seed, trajectory, step); 1: xorshift per trajectory */
+    int32_t reserved;
 } or_run_args;
 
 typedef struct {
@@ -354,10 +394,13 @@ static void *run_range(void *arg)
         }
         double vsum = 0.0;
         int64_t snap = 0;
+        uint32_t xs[4];
+        if (a->noise == 1)
+            or_xorshift_seed(a->seed, traj, xs);
         if (a->n_steps == 0 && a->snapshot_every <= 0)
             snapshot(a, snap++, s, wk->hx, wk->hv);
         for (int64_t n = 0; n < a->n_steps; ++n) {
-            const double z = or_normal(a->seed, traj, (uint64_t)n);
+            const double z = a->noise == 1 ? or_xorshift_normal(xs) : or_normal(a->seed, traj, (uint64_t)n);
             if (a->scheme == 1) {
                 /* x advances by (v + v~) dt / 2: that is the step's velocity */
                 const double v_n = s[1];
@@ -402,7 +445,7 @@ int or_run_set(const or_run_args *a, or_run_out *o)
     if (!a || !o || a->n_traj < 0 || a->n_steps < 0 || !(a->dt > 0.0) || !(a->p.L > 0.0)
         || a->p.D < 0.0 || a->hist_x_bins < 0 || a->hist_v_bins < 0
         || (a->hist_v_bins > 0 && !(a->v_hi > a->v_lo)) || a->scheme < 0 || a->scheme > 1
-        || (a->scheme == 1 && a->want_grad))
+        || (a->scheme == 1 && a->want_grad) || a->noise < 0 || a->noise > 1 || (a->noise == 1 && a->want_grad))
         return -1;
     const int64_t M = a->n_traj;
     const int64_t n_snap = or_n_snapshots(a->n_steps, a->snapshot_every);

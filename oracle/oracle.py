@@ -50,6 +50,8 @@ class RunArgs(C.Structure):
         ("v_hi", C.c_double),
         ("want_grad", C.c_int32),
         ("scheme", C.c_int32),
+        ("noise", C.c_int32),
+        ("reserved", C.c_int32),
     ]
 
 
@@ -95,6 +97,11 @@ def lib():
         L.or_potential_dx.restype = C.c_double
         L.or_em_step.argtypes = [C.POINTER(Params), C.c_double, C.c_double, _PD]
         L.or_heun_step.argtypes = [C.POINTER(Params), C.c_double, C.c_double, _PD, _PD]
+        L.or_xorshift128_step.argtypes = [C.POINTER(C.c_uint32)]
+        L.or_xorshift128_step.restype = C.c_uint32
+        L.or_xorshift_seed.argtypes = [C.c_uint64, C.c_uint64, C.POINTER(C.c_uint32)]
+        L.or_xorshift_normal.argtypes = [C.POINTER(C.c_uint32)]
+        L.or_xorshift_normal.restype = C.c_double
         L.or_initial_state.argtypes = [C.POINTER(Params), C.c_uint64, C.c_int32, C.c_uint64, _PD]
         L.or_n_snapshots.argtypes = [C.c_int64, C.c_int64]
         L.or_n_snapshots.restype = C.c_int64
@@ -160,6 +167,25 @@ def heun_step(params: dict, dt: float, z: float, state):
     return (s[0], s[1], s[2]), vp.value
 
 
+def xorshift_step(state):
+    """One xorshift call: returns (output word, new state)."""
+    s = (C.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in state])
+    out = lib().or_xorshift128_step(s)
+    return int(out), tuple(int(v) for v in s)
+
+
+def xorshift_seed(seed: int, traj: int):
+    s = (C.c_uint32 * 4)()
+    lib().or_xorshift_seed(seed, traj, s)
+    return tuple(int(v) for v in s)
+
+
+def xorshift_words(seed: int, traj: int, count: int):
+    """The first `count` words of trajectory traj's xorshift stream."""
+    s = (C.c_uint32 * 4)(*xorshift_seed(seed, traj))
+    return [int(lib().or_xorshift128_step(s)) for _ in range(count)]
+
+
 def initial_state(params: dict, seed: int, v0_mode: int, traj: int):
     s = (C.c_double * 3)()
     lib().or_initial_state(C.byref(make_params(**params)), seed, v0_mode, traj, s)
@@ -175,11 +201,13 @@ def n_snapshots(n_steps: int, snapshot_every: int) -> int:
 def run_set(params: dict, *, seed: int, dt: float, n_traj: int, n_steps: int, traj_base: int = 0,
             v0_mode: int = 0, snapshot_every: int = 0, hist_x_bins: int = 0, hist_v_bins: int = 0,
             v_lo: float = -5.0, v_hi: float = 5.0, want_states: bool = False, want_grad: bool = False,
-            want_traj_grad: bool = False, n_threads: int | None = None, scheme: int = 0) -> dict:
+            want_traj_grad: bool = False, n_threads: int | None = None, scheme: int = 0, noise: int = 0) -> dict:
     """Integrate one parameter set's ensemble in FP64 and reduce it.
 
     ``scheme`` 0 is the paper's explicit Euler-Maruyama step, 1 the stochastic Heun
-    predictor-corrector on the same noise (no gradient for it).
+    predictor-corrector on the same noise (no gradient for it).  ``noise`` 0 is the
+    counter-based Philox stream, 1 Marsaglia's xorshift per trajectory (two words and one
+    Box-Muller cosine per step; no gradient for it).
 
     Returns a dict with ``sums`` = (sum vbar, sum vbar^2, sum dx, sum dx^2), the derived
     ``mean_v``, ``se_v``, ``msd``, ``d_eff``, per-trajectory ``vbar`` and (optionally) the
@@ -195,6 +223,7 @@ def run_set(params: dict, *, seed: int, dt: float, n_traj: int, n_steps: int, tr
     a.hist_x_bins, a.hist_v_bins, a.v_lo, a.v_hi = hist_x_bins, hist_v_bins, v_lo, v_hi
     a.want_grad = 1 if (want_grad or want_traj_grad) else 0
     a.scheme = int(scheme)
+    a.noise = int(noise)
     o = RunOut()
     out: dict = {}
     keep = []
