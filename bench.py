@@ -61,7 +61,7 @@ def parse():
                     help="N_TRAJ,N_STEPS: time only the forward and backward of the differentiation workload at "
                          "this size (profiling; prints one JSON line without the bench keys)")
     ap.add_argument("--configs", default="",
-                    help="also time other workloads, comma-separated: single, uneven, force, heun, snapshots, "
+                    help="also time other workloads, comma-separated: single, uneven, force, heun, xorshift, snapshots, "
                          "precision, items (or 'all'); reported under 'configs'")
     return ap.parse_args()
 
@@ -498,7 +498,7 @@ def configs_leg(A, stream, names):
     from paper_1104_2499_gb300 import workloads as W
 
     if names == ["all"]:
-        names = ["single", "uneven", "force", "heun", "precision", "items", "snapshots"]
+        names = ["single", "uneven", "force", "heun", "xorshift", "precision", "items", "snapshots"]
     out = {}
     for name in names:
         if name == "single":
@@ -512,6 +512,10 @@ def configs_leg(A, stream, names):
         elif name == "heun":
             w = W.sweep_grid()
             w.scheme, w.name = 1, w.name + "_heun"
+            out[name] = time_workload(A, stream, w, 1)[0]
+        elif name == "xorshift":
+            w = W.sweep_grid()
+            w.noise, w.name = 1, w.name + "_xorshift"
             out[name] = time_workload(A, stream, w, 1)[0]
         elif name == "precision":
             out[name] = precision_leg(A, stream)

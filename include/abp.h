@@ -117,7 +117,12 @@ typedef struct {
                                     with the same noise increment w of the step (weak order 2 for
                                     this additive noise; a variant the paper does not use).
                                     Heun needs state_fp64 = 0 and checkpoint_every = 0 (no adjoint) */
-    int32_t reserved;            /* must be 0 */
+    int32_t noise;               /* 0: counter-based Philox4x32-10 keyed by (seed, trajectory, step);
+                                    1: Marsaglia's xorshift (shifts 11, 8, 19), the RNG of Fig. 1:
+                                    one 128-bit state per trajectory, seeded from the Philox block
+                                    of counter 2^63 + 1, two words and one Box-Muller cosine per
+                                    step.  Xorshift keeps 16 more bytes of state per trajectory and
+                                    needs scheme 0, state_fp64 = 0 and checkpoint_every = 0 */
 } abp_config;
 
 /* Create a context on the current CUDA device.  cuda_stream is a cudaStream_t
@@ -274,6 +279,11 @@ ABP_API abp_status abp_philox(uint64_t seed, const uint64_t *traj, const uint64_
  * of trajectory traj (device output of count floats). */
 ABP_API abp_status abp_normals(uint64_t seed, uint64_t traj, uint64_t n0, int64_t count, float *out,
                        void *cuda_stream);
+
+/* The first `count` words of the xorshift stream of global trajectory `traj`
+ * under `seed` (noise = 1), written to device memory out[count] on
+ * cuda_stream: the verification entry of the xorshift option. */
+ABP_API abp_status abp_xorshift(uint64_t seed, uint64_t traj, int64_t count, uint32_t *out, void *cuda_stream);
 
 /* --- allocation-free entry point ------------------------------------------ */
 

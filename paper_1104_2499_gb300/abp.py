@@ -55,7 +55,7 @@ class abp_config(C.Structure):
         ("steps_per_launch", C.c_int64),
         ("traj_base", C.c_uint64),
         ("scheme", C.c_int32),
-        ("reserved", C.c_int32),
+        ("noise", C.c_int32),
     ]
 
 
@@ -92,6 +92,8 @@ def lib():
                                  C.POINTER(C.c_int32)]
         L.abp_tuning.restype = st
         L.abp_tiles.argtypes = [_VP, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+        L.abp_xorshift.argtypes = [C.c_uint64, C.c_uint64, C.c_int64, _VP, _VP]
+        L.abp_xorshift.restype = st
         L.abp_live.argtypes = [_VP, _VP, _VP, _VP]
         L.abp_live.restype = st
         L.abp_live_ready.argtypes = [_VP, C.POINTER(C.c_int64)]
@@ -203,6 +205,11 @@ def abp_tiles(ctx):
     return {"tiles": t.value, "packed": p.value, "narrow": n.value}
 
 
+def abp_xorshift(seed: int, traj: int, out, stream=None):
+    """The first out.numel() words of trajectory traj's xorshift stream (device int32 tensor)."""
+    _check(lib().abp_xorshift(seed, traj, out.numel(), _ptr(out), _stream_ptr(stream)), what="abp_xorshift")
+
+
 def abp_live(ctx, moments=None, hist_x=None, hist_v=None):
     """Stream every snapshot (moments [n_snap, n_sets, 8] float64, histograms int32) into
     page-locked host tensors while the integration runs; all None switches it off."""
@@ -289,7 +296,7 @@ def abp_version() -> str:
 
 def make_config(w: "W.Workload", *, state_fp64: bool = False, particles_per_thread: int = 0,
                 steps_per_launch: int = 0, traj_base: int = 0, schedule: int = 0,
-                scheme: int | None = None) -> abp_config:
+                scheme: int | None = None, noise: int | None = None) -> abp_config:
     c = abp_config()
     c.seed = int(w.seed)
     c.dt = float(w.dt)
@@ -306,6 +313,7 @@ def make_config(w: "W.Workload", *, state_fp64: bool = False, particles_per_thre
     c.steps_per_launch = int(steps_per_launch)
     c.traj_base = int(traj_base)
     c.scheme = int(w.scheme if scheme is None else scheme)
+    c.noise = int(w.noise if noise is None else noise)
     return c
 
 

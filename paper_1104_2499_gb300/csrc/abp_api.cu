@@ -115,11 +115,13 @@ struct TuneTable {
     bool done = false;
     float ms[3][3] = {};  // [schedule 1 = lockstep, 2 = work queue][ppt 1, 2, 4]
 };
-TuneTable g_tune[64][3];
+TuneTable g_tune[64][4];
 
 // Kind of integrator a timing table belongs to: 0 FP32 Euler-Maruyama, 1 FP64
-// state, 2 FP32 stochastic Heun.
-int tune_kind(const abp_ctx *ctx) { return ctx->cfg.state_fp64 ? 1 : (ctx->cfg.scheme == 1 ? 2 : 0); }
+// state, 2 FP32 stochastic Heun, 3 FP32 Euler-Maruyama with xorshift noise.
+int tune_kind(const abp_ctx *ctx) {
+    return ctx->cfg.state_fp64 ? 1 : ctx->cfg.scheme == 1 ? 2 : ctx->cfg.noise == 1 ? 3 : 0;
+}
 
 void measure_candidates(abp_ctx *ctx, TuneTable &tt) {
     const int fp = ctx->cfg.state_fp64 ? 1 : 0;
@@ -129,7 +131,9 @@ void measure_candidates(abp_ctx *ctx, TuneTable &tt) {
     const size_t rsz = fp ? sizeof(double) : sizeof(float);
     const int cands[3] = {1, 2, 4};
     const int max_tiles = (int)((T + kThreads - 1) / kThreads);
-    const size_t bytes = 256 * 16 + (sizeof(int64_t) + 5 * sizeof(int32_t)) * max_tiles + (6 * rsz + 4) * T + 8192;
+    const bool xorshift = ctx->cfg.noise == 1;
+    const size_t bytes =
+        256 * 16 + (sizeof(int64_t) + 5 * sizeof(int32_t)) * max_tiles + (6 * rsz + 4 + (xorshift ? 16 : 0)) * T + 8192;
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) tt.ms[i][j] = 1e30f;
     void *mem = nullptr;
@@ -160,6 +164,7 @@ void measure_candidates(abp_ctx *ctx, TuneTable &tt) {
     st.e = take(rsz * T);
     st.y0 = take(rsz * T);
     st.cell = (int32_t *)take(sizeof(int32_t) * T);
+    st.xs = xorshift ? (uint4 *)take(sizeof(uint4) * T) : nullptr;
     int32_t *d_queue = (int32_t *)take(sizeof(int32_t) * ((size_t)max_tiles + 1));
     int32_t *d_perm = (int32_t *)take(sizeof(int32_t) * max_tiles);
     int32_t *d_rs = (int32_t *)take(sizeof(int32_t) * 2);
@@ -169,6 +174,7 @@ void measure_candidates(abp_ctx *ctx, TuneTable &tt) {
     Noise nz{};
     nz.dt = 1e-3;
     nz.scheme = heun ? 1 : 0;
+    nz.noise = xorshift ? 1 : 0;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -212,7 +218,7 @@ void measure_candidates(abp_ctx *ctx, TuneTable &tt) {
         b.tile_count = d_count;
         b.tile_set = d_tset;
         int bps = 0;
-        persistent_occupancy(fp != 0, c, 0, &bps, heun);
+        persistent_occupancy(fp != 0, c, 0, &bps, heun ? 1 : xorshift ? 2 : 0);
         Queue q;
         q.head = d_queue;
         q.done = d_queue + 1;
@@ -421,7 +427,8 @@ abp_status abp_create(abp_ctx **out, const abp_config *cfg, void *cuda_stream) {
     if (cfg->checkpoint_every > 0 && cfg->state_fp64) return ABP_EINVAL;  // adjoint runs on the FP32 path
     if (cfg->scheme != 0 && cfg->scheme != 1) return ABP_EINVAL;
     if (cfg->scheme == 1 && (cfg->state_fp64 || cfg->checkpoint_every > 0)) return ABP_EINVAL;  // FP32, no adjoint
-    if (cfg->reserved != 0) return ABP_EINVAL;
+    if (cfg->noise != 0 && cfg->noise != 1) return ABP_EINVAL;
+    if (cfg->noise == 1 && (cfg->scheme != 0 || cfg->state_fp64 || cfg->checkpoint_every > 0)) return ABP_EINVAL;
     abp_ctx *ctx = new (std::nothrow) abp_ctx();
     if (!ctx) return ABP_ENOMEM;
     ctx->cfg = *cfg;
@@ -586,7 +593,8 @@ abp_status abp_set_params(abp_ctx *ctx, int32_t n_sets, const abp_params *sets, 
         int bps = 0;
         const size_t smem = sizeof(uint32_t) * (size_t)(std::max(c.hist_x_bins, 0) +
                                                         (c.hist_v_bins > 0 ? c.hist_v_bins + 2 : 0));
-        cudaError_t oe = persistent_occupancy(c.state_fp64 != 0, ctx->ppt, smem, &bps, c.scheme == 1);
+        cudaError_t oe =
+            persistent_occupancy(c.state_fp64 != 0, ctx->ppt, smem, &bps, c.scheme == 1 ? 1 : c.noise == 1 ? 2 : 0);
         if (oe != cudaSuccess) return cuda_fail(ctx, oe, "occupancy query");
         ctx->grid = std::max(bps, 1) * std::max(ctx->sm_count, 1);
     }
@@ -613,6 +621,7 @@ abp_status abp_set_params(abp_ctx *ctx, int32_t n_sets, const abp_params *sets, 
     ALLOC(d_e, rsz * T, "state e");
     ALLOC(d_y0, rsz * T, "state y0");
     ALLOC(d_cell, sizeof(int32_t) * T, "state cell");
+    if (c.noise == 1) ALLOC(d_xs, sizeof(uint4) * T, "xorshift states");
     ALLOC(d_hx, sizeof(uint32_t) * (size_t)ctx->n_snap * n_sets * (size_t)std::max(c.hist_x_bins, 0), "x histograms");
     ALLOC(d_hv, sizeof(uint32_t) * (size_t)ctx->n_snap * n_sets * (size_t)(c.hist_v_bins > 0 ? c.hist_v_bins + 2 : 0),
           "v histograms");
@@ -1009,6 +1018,7 @@ struct SaveHeader {
     uint64_t seed, traj_base;
     uint64_t hx_bytes, hv_bytes;
     uint64_t signature;  // FNV-1a of the sets' parameters, sizes and step counts
+    int32_t noise, reserved;  // noise: 0 Philox, 1 xorshift (its states follow the cell indices)
 };
 
 uint64_t batch_signature(const abp_ctx *ctx) {
@@ -1031,7 +1041,8 @@ std::vector<std::pair<DevBuf *, size_t>> image_parts(abp_ctx *ctx) {
     const size_t T = (size_t)ctx->total_traj, rsz = ctx->cfg.state_fp64 ? sizeof(double) : sizeof(float);
     return {{&ctx->d_y, rsz * T},    {&ctx->d_yacc, rsz * T}, {&ctx->d_ylo, rsz * T},
             {&ctx->d_v, rsz * T},    {&ctx->d_e, rsz * T},    {&ctx->d_y0, rsz * T},
-            {&ctx->d_cell, 4 * T},   {&ctx->d_hx, ctx->d_hx.bytes}, {&ctx->d_hv, ctx->d_hv.bytes}};
+            {&ctx->d_cell, 4 * T},   {&ctx->d_xs, ctx->cfg.noise == 1 ? 16 * T : 0},
+            {&ctx->d_hx, ctx->d_hx.bytes}, {&ctx->d_hv, ctx->d_hv.bytes}};
 }
 
 }  // namespace
@@ -1050,7 +1061,8 @@ abp_status abp_save(abp_ctx *ctx, void *buf, size_t *bytes) {
     if (*bytes < need) return fail(ctx, ABP_EINVAL, "abp_save: buffer of %zu bytes, %zu needed", *bytes, need);
     SaveHeader hd{};
     memcpy(hd.magic, "ABPSAVE1", 8);
-    hd.version = 1;
+    hd.version = 2;
+    hd.noise = ctx->cfg.noise;
     hd.fp64 = ctx->cfg.state_fp64 ? 1 : 0;
     hd.g = ctx->g;
     hd.total_traj = ctx->total_traj;
@@ -1089,9 +1101,10 @@ abp_status abp_load(abp_ctx *ctx, const void *buf, size_t bytes) {
     if (e != cudaSuccess) return cuda_fail(ctx, e, "abp_load header");
     size_t need = sizeof(hd);
     for (auto &pt : image_parts(ctx)) need += pt.second;
-    if (memcmp(hd.magic, "ABPSAVE1", 8) != 0 || hd.version != 1)
+    if (memcmp(hd.magic, "ABPSAVE1", 8) != 0 || hd.version != 2)
         return fail(ctx, ABP_EINVAL, "abp_load: not an image written by abp_save");
-    if (hd.fp64 != (ctx->cfg.state_fp64 ? 1u : 0u) || hd.scheme != ctx->cfg.scheme || hd.total_traj != ctx->total_traj ||
+    if (hd.fp64 != (ctx->cfg.state_fp64 ? 1u : 0u) || hd.scheme != ctx->cfg.scheme || hd.noise != ctx->cfg.noise ||
+        hd.total_traj != ctx->total_traj ||
         hd.n_sets != ctx->n_sets ||
         hd.signature != batch_signature(ctx) || hd.hx_bytes != ctx->d_hx.bytes || hd.hv_bytes != ctx->d_hv.bytes ||
         bytes < need || hd.g < 0 || hd.g > ctx->max_steps)
@@ -1179,6 +1192,14 @@ abp_status abp_normals(uint64_t seed, uint64_t traj, uint64_t n0, int64_t count,
     if (!out || !is_device_ptr(out)) return ABP_EINVAL;
     cudaError_t e = launch_normals((uint32_t)seed, (uint32_t)(seed >> 32), traj, n0, count, out,
                                    (cudaStream_t)cuda_stream);
+    return e == cudaSuccess ? ABP_OK : ABP_ECUDA;
+}
+
+abp_status abp_xorshift(uint64_t seed, uint64_t traj, int64_t count, uint32_t *out, void *cuda_stream) {
+    if (count < 0) return ABP_EINVAL;
+    if (count == 0) return ABP_OK;
+    if (!out || !is_device_ptr(out)) return ABP_EINVAL;
+    cudaError_t e = launch_xorshift((uint32_t)seed, (uint32_t)(seed >> 32), traj, count, out, (cudaStream_t)cuda_stream);
     return e == cudaSuccess ? ABP_OK : ABP_ECUDA;
 }
 

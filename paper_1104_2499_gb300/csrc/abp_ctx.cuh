@@ -86,7 +86,7 @@ struct abp_ctx {
 
     // device
     DevBuf d_params, d_steps, d_set_tile_begin, d_tile_first, d_tile_count, d_tile_set, d_set_first, d_set_order;
-    DevBuf d_y, d_yacc, d_ylo, d_v, d_e, d_y0, d_cell;
+    DevBuf d_y, d_yacc, d_ylo, d_v, d_e, d_y0, d_cell, d_xs;
     DevBuf d_hx, d_hv, d_ckpt, d_partials, d_moments, d_status;
     DevBuf d_queue, d_round, d_perm;  // work queue: head + done[n_tiles]; round starts; tile order
     DevBuf d_adj;  // adjoint scratch
@@ -134,6 +134,7 @@ struct abp_ctx {
         s.e = d_e.p;
         s.y0 = d_y0.p;
         s.cell = (int32_t *)d_cell.p;
+        s.xs = cfg.noise == 1 ? (uint4 *)d_xs.p : nullptr;
         return s;
     }
     Hist hist() const {
@@ -163,6 +164,7 @@ struct abp_ctx {
         n.v0_mode = cfg.v0_mode;
         n.traj_base = cfg.traj_base;
         n.scheme = cfg.scheme;
+        n.noise = cfg.noise;
         return n;
     }
     void drop_graphs() {
@@ -208,7 +210,7 @@ struct abp_ctx {
         if (live_stream) cudaStreamSynchronize(live_stream);
         drop_graphs();
         for (DevBuf *b : {&d_queue, &d_round, &d_perm, &d_set_first, &d_set_order, &d_params, &d_steps, &d_set_tile_begin, &d_tile_first, &d_tile_count, &d_tile_set, &d_y,
-                          &d_yacc, &d_ylo, &d_v, &d_e, &d_y0, &d_cell, &d_hx, &d_hv, &d_ckpt, &d_partials,
+                          &d_yacc, &d_ylo, &d_v, &d_e, &d_y0, &d_cell, &d_xs, &d_hx, &d_hv, &d_ckpt, &d_partials,
                           &d_moments, &d_adj, &d_live_mom})
             b->release();
         have_batch = false;

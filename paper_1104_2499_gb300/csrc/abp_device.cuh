@@ -100,6 +100,28 @@ __device__ __forceinline__ uint4 step_block(uint32_t m, const StepStream &s, con
 
 // Counter of the initial-condition draw (m = 2^63; step counters stay below 2^32).
 constexpr uint64_t kInitCounter = 0x8000000000000000ull;
+// Counter of the Philox block that seeds a trajectory's xorshift state.
+constexpr uint64_t kXorshiftSeedCounter = kInitCounter + 1;
+
+// Marsaglia's xorshift with four 32-bit words of state and shifts (11, 8, 19)
+// (Xorshift RNGs, 2003), the generator of Fig. 1: (x, y, z, w) -> (y, z, w,
+// w ^ (w >> 19) ^ t ^ (t >> 8)), t = x ^ (x << 11); returns the new w.
+__device__ __forceinline__ uint32_t xorshift128(uint32_t (&s)[4]) {
+    const uint32_t t = s[0] ^ (s[0] << 11);
+    s[0] = s[1];
+    s[1] = s[2];
+    s[2] = s[3];
+    s[3] = s[3] ^ (s[3] >> 19) ^ t ^ (t >> 8);
+    return s[3];
+}
+
+// The xorshift state of global trajectory t: the Philox block of counter
+// 2^63 + 1; an all-zero block (never met in practice) becomes (0, 0, 0, 1).
+__device__ __forceinline__ uint4 xorshift_seed(uint64_t t, uint32_t k0, uint32_t k1) {
+    uint4 w = noise_block(kXorshiftSeedCounter, t, k0, k1);
+    if ((w.x | w.y | w.z | w.w) == 0u) w.w = 1u;
+    return w;
+}
 
 // --------------------------------------------------------------------------
 // Hardware approximations used by the FP32 path.  The approximate square

@@ -55,6 +55,7 @@ struct State {
     void *e;       // depot energy
     void *y0;      // initial fraction (x0 = L y0)
     int32_t *cell; // period index
+    uint4 *xs;     // xorshift state (x, y, z, w) of each trajectory (noise 1), else NULL
 };
 
 struct Hist {
@@ -82,6 +83,7 @@ struct Noise {
     uint64_t traj_base;  // added to every state index to give the global trajectory id
     uint32_t rk[20];     // round keys: rk[2r], rk[2r+1] = (k0 + r W0, k1 + r W1)
     int32_t scheme;      // 0 Euler-Maruyama, 1 stochastic Heun (FP32 state)
+    int32_t noise;       // 0 Philox by (seed, trajectory, step), 1 xorshift per trajectory
 };
 
 // Work queue of the persistent integrator (device buffers owned by the context).
@@ -108,6 +110,7 @@ cudaError_t launch_get_state(const Batch &b, const State &s, double dt, int64_t 
                              double *e, double *vbar, cudaStream_t st);
 cudaError_t launch_philox(uint32_t k0, uint32_t k1, const uint64_t *traj, const uint64_t *m, int64_t n,
                           uint32_t *out, cudaStream_t st);
+cudaError_t launch_xorshift(uint32_t k0, uint32_t k1, uint64_t traj, int64_t count, uint32_t *out, cudaStream_t st);
 cudaError_t launch_normals(uint32_t k0, uint32_t k1, uint64_t traj, uint64_t n0, int64_t count, float *out,
                            cudaStream_t st);
 
@@ -115,6 +118,7 @@ cudaError_t launch_persistent(const Batch &b, const State &s, const Hist &h, con
                               const Queue &q, int ppt, int grid, int64_t g0, int64_t g1, int64_t seg,
                               cudaStream_t st);
 // Resident blocks per SM of the persistent integrator (sets its shared-memory limit too).
-cudaError_t persistent_occupancy(bool fp64, int ppt, size_t smem, int *blocks_per_sm, bool heun = false);
+// mode: 0 Euler-Maruyama, 1 stochastic Heun, 2 Euler-Maruyama with xorshift noise
+cudaError_t persistent_occupancy(bool fp64, int ppt, size_t smem, int *blocks_per_sm, int mode = 0);
 
 }  // namespace abp

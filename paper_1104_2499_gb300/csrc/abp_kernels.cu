@@ -142,6 +142,7 @@ __global__ void __launch_bounds__(kThreads) init_kernel(Batch b, State st, Hist 
                 v0 = sqrt(p.D) * ze;
             }
         }
+        if (nz.noise == 1 && st.xs) st.xs[t] = xorshift_seed((uint64_t)t + nz.traj_base, nz.k0, nz.k1);
         s.y[t] = y0;
         s.y0[t] = y0;
         s.yacc[t] = 0;
@@ -175,7 +176,13 @@ struct Slots {
     float pb[PPT];  // phase_base(y) of the FP32 path
     int32_t cell[PPT];
     StepStream ss[PPT];
+    uint32_t xs[PPT][4];  // xorshift states (mode 2)
 };
+
+// Integrator modes (template parameter MODE): 0 Euler-Maruyama with Philox
+// noise, 1 stochastic Heun with Philox noise, 2 Euler-Maruyama with xorshift
+// noise (two words and one Box-Muller cosine per step).
+constexpr int kModeEM = 0, kModeHeun = 1, kModeXorshift = 2;
 
 // Round keys of the launch's seed as a kernel parameter (constant bank).
 struct KeyParam {
@@ -195,8 +202,19 @@ __device__ __forceinline__ void step_f32(const Coef<float> &k, float nrs, float 
 // One Euler-Maruyama step of every slot at an arbitrary step index n (the
 // unaligned head / tail of a range): the counter block of n is generated for
 // this step alone.
-template <typename R, int PPT, bool HEUN = false>
+template <typename R, int PPT, int MODE = kModeEM>
 __device__ __forceinline__ void single_step(const Coef<R> &k, const RoundKeys &K, Slots<R, PPT> &S, int64_t n) {
+    if constexpr (MODE == kModeXorshift) {
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) {
+            float nrs, cs, sn;
+            const uint32_t wa = xorshift128(S.xs[q]);
+            const uint32_t wb = xorshift128(S.xs[q]);
+            box_muller_f32(wa, wb, k.bm, nrs, cs, sn);
+            em_step_f32(k, nrs, cs, S.pb[q], S.yacc[q], S.v[q], S.e[q]);
+        }
+        return;
+    }
     const uint32_t j = (uint32_t)(n & 3);
     const uint32_t m = (uint32_t)(n >> 2);
 #pragma unroll
@@ -208,7 +226,7 @@ __device__ __forceinline__ void single_step(const Coef<R> &k, const RoundKeys &K
                 box_muller_f32(w.x, w.y, k.bm, nrs, cs, sn);
             else
                 box_muller_f32(w.z, w.w, k.bm, nrs, cs, sn);
-            step_f32<HEUN>(k, nrs, (j & 1) ? sn : cs, S.pb[q], S.yacc[q], S.v[q], S.e[q]);
+            step_f32<MODE == kModeHeun>(k, nrs, (j & 1) ? sn : cs, S.pb[q], S.yacc[q], S.v[q], S.e[q]);
         } else {
             const double z = normal_from_block_f64(w, j);
             em_step<double>(k, k.sigma * z, S.y[q], S.yacc[q], S.v[q], S.e[q]);
@@ -217,8 +235,14 @@ __device__ __forceinline__ void single_step(const Coef<R> &k, const RoundKeys &K
 }
 
 // Four steps 4m .. 4m+3 of every slot from one counter block each.
-template <typename R, int PPT, bool HEUN = false>
+template <typename R, int PPT, int MODE = kModeEM>
 __device__ __forceinline__ void group_step(const Coef<R> &k, const RoundKeys &K, Slots<R, PPT> &S, uint32_t m) {
+    if constexpr (MODE == kModeXorshift) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) single_step<R, PPT, MODE>(k, K, S, 0);
+        return;
+    }
+    constexpr bool HEUN = MODE == kModeHeun;
     uint4 w[PPT];
 #pragma unroll
     for (int q = 0; q < PPT; ++q) w[q] = step_block(m, S.ss[q], K);
@@ -252,24 +276,24 @@ __device__ __forceinline__ void group_step(const Coef<R> &k, const RoundKeys &K,
 
 // Steps [n, n_end) of every slot.  Folds happen after absolute multiples of
 // kBlockSteps steps; counter blocks are absolute multiples of 4.
-template <typename R, int PPT, bool HEUN = false>
+template <typename R, int PPT, int MODE = kModeEM>
 __device__ __forceinline__ void advance(const Coef<R> &k, const RoundKeys &K, Slots<R, PPT> &S, int64_t n,
                                         int64_t n_end) {
     while (n < n_end) {
         const int64_t blk_end = min(n_end, (n | (int64_t)(kBlockSteps - 1)) + 1);
         while (n < blk_end && (n & 3)) {
-            single_step<R, PPT, HEUN>(k, K, S, n);
+            single_step<R, PPT, MODE>(k, K, S, n);
             ++n;
         }
         if (n < blk_end) {
             const uint32_t m_end = (uint32_t)(blk_end >> 2);
             uint32_t m = (uint32_t)(n >> 2);
 #pragma unroll kGroupUnroll
-            for (; m < m_end; ++m) group_step<R, PPT, HEUN>(k, K, S, m);
+            for (; m < m_end; ++m) group_step<R, PPT, MODE>(k, K, S, m);
             n = (int64_t)m << 2;
         }
         while (n < blk_end) {
-            single_step<R, PPT, HEUN>(k, K, S, n);
+            single_step<R, PPT, MODE>(k, K, S, n);
             ++n;
         }
         if ((blk_end & (kBlockSteps - 1)) == 0) {
@@ -290,7 +314,7 @@ __device__ __forceinline__ void advance(const Coef<R> &k, const RoundKeys &K, Sl
 // PACKED: a packed tile (several sets of equal step count, PPT 1): each thread
 // takes the coefficients of its own trajectory's set, and histograms go to
 // global memory directly.
-template <typename R, int PPT, bool PACKED = false, bool HEUN = false>
+template <typename R, int PPT, bool PACKED = false, int MODE = kModeEM>
 __device__ __forceinline__ void run_tile(const Batch &b, const State &st, const Hist &h, const Ckpt &ck,
                                          const Noise &nz, const RoundKeys &K, uint32_t *sh, int tile, int64_t w0,
                                          int64_t w1, int lane_base = 0) {
@@ -324,6 +348,13 @@ __device__ __forceinline__ void run_tile(const Batch &b, const State &st, const 
         S.cell[q] = __ldcg(&s.cell[idx[q]]);
         if constexpr (sizeof(R) == 4) S.pb[q] = phase_base(S.y[q]);
         S.ss[q] = step_stream((uint64_t)idx[q] + nz.traj_base, K);
+        if constexpr (MODE == kModeXorshift) {
+            const uint4 w = __ldcg(&st.xs[idx[q]]);
+            S.xs[q][0] = w.x;
+            S.xs[q][1] = w.y;
+            S.xs[q][2] = w.z;
+            S.xs[q][3] = w.w;
+        }
     }
 
     const bool hist = h.bx > 0 || h.bv > 0;
@@ -341,7 +372,7 @@ __device__ __forceinline__ void run_tile(const Batch &b, const State &st, const 
         int64_t seg_end = n_end;
         if (hist && h.snap_every > 0) seg_end = min(seg_end, (n / h.snap_every + 1) * h.snap_every);
         if (ck.every > 0) seg_end = min(seg_end, (n / ck.every + 1) * ck.every);
-        if (warp_live) advance<R, PPT, HEUN>(k, K, S, n, seg_end);
+        if (warp_live) advance<R, PPT, MODE>(k, K, S, n, seg_end);
         n = seg_end;
         if (hist && (h.snap_every > 0 ? (n % h.snap_every == 0) : (n == N))) {
             const int64_t snap = h.snap_every > 0 ? n / h.snap_every - 1 : 0;
@@ -381,6 +412,7 @@ __device__ __forceinline__ void run_tile(const Batch &b, const State &st, const 
         s.v[idx[q]] = S.v[q];
         s.e[idx[q]] = S.e[q];
         s.cell[idx[q]] = S.cell[q];
+        if constexpr (MODE == kModeXorshift) st.xs[idx[q]] = make_uint4(S.xs[q][0], S.xs[q][1], S.xs[q][2], S.xs[q][3]);
     }
 }
 
@@ -395,7 +427,7 @@ __device__ __forceinline__ void zero_hist(uint32_t *sh, const Hist &h) {
 // Lockstep schedule: one block per tile (narrow launch: `sub` blocks per tile,
 // each taking blockDim.x consecutive trajectories of it), every tile over the
 // window [g0, g1).
-template <typename R, int PPT, bool PACKED, bool HEUN>
+template <typename R, int PPT, bool PACKED, int MODE>
 __global__ void ABP_INTEGRATE_BOUNDS integrate_kernel(Batch b, State st, Hist h, Ckpt ck, Noise nz,
                                                      KeyParam kp, int64_t g0, int64_t g1) {
     extern __shared__ uint32_t sh[];
@@ -403,7 +435,7 @@ __global__ void ABP_INTEGRATE_BOUNDS integrate_kernel(Batch b, State st, Hist h,
     const int sub = b.narrow ? (PACKED ? b.sub_packed : b.sub_single) : 1;
     const int tile = (PACKED ? b.n_single : 0) + (int)blockIdx.x / sub;
     const int lane_base = ((int)blockIdx.x % sub) * (int)blockDim.x;
-    run_tile<R, PPT, PACKED, HEUN>(b, st, h, ck, nz, kp.K, sh, tile, g0, g1, lane_base);
+    run_tile<R, PPT, PACKED, MODE>(b, st, h, ck, nz, kp.K, sh, tile, g0, g1, lane_base);
 }
 
 __device__ __forceinline__ uint64_t global_ns() {
@@ -430,7 +462,7 @@ __device__ __forceinline__ void store_release(int32_t *p, int v) {
 // before it, so the earliest unfinished item is always runnable.  The wait is
 // bounded: past q.wait_limit_ns the block records status 1 and every block
 // leaves at its next check, without touching the item.
-template <typename R, int PPT, bool HEUN>
+template <typename R, int PPT, int MODE>
 __global__ void ABP_INTEGRATE_BOUNDS persistent_kernel(Batch b, State st, Hist h, Ckpt ck, Noise nz, KeyParam kp,
                                                       Queue q, int64_t g0, int64_t g1, int64_t seg) {
     extern __shared__ uint32_t sh[];
@@ -474,7 +506,7 @@ __global__ void ABP_INTEGRATE_BOUNDS persistent_kernel(Batch b, State st, Hist h
         if (s_tile < 0) break;
         {
             const int64_t w0 = g0 + (int64_t)s_round * seg;
-            run_tile<R, PPT, false, HEUN>(b, st, h, ck, nz, kp.K, sh, s_tile, w0, min(w0 + seg, g1));
+            run_tile<R, PPT, false, MODE>(b, st, h, ck, nz, kp.K, sh, s_tile, w0, min(w0 + seg, g1));
         }
         __syncthreads();  // every thread's state stores precede the publication
         if (threadIdx.x == 0 && s_tile != q.hold_tile) {
@@ -704,11 +736,11 @@ KeyParam key_param(uint32_t k0, uint32_t k1) {
     return kp;
 }
 
-template <typename R, int PPT, bool HEUN = false>
+template <typename R, int PPT, int MODE = kModeEM>
 cudaError_t launch_persistent_t(const Batch &b, const State &s, const Hist &h, const Ckpt &c, const Noise &nz,
                                 const Queue &q, int grid, int64_t g0, int64_t g1, int64_t seg, cudaStream_t st) {
     const size_t smem = hist_smem(h);
-    auto kern = persistent_kernel<R, PPT, HEUN>;
+    auto kern = persistent_kernel<R, PPT, MODE>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -717,11 +749,11 @@ cudaError_t launch_persistent_t(const Batch &b, const State &s, const Hist &h, c
     return cudaGetLastError();
 }
 
-template <typename R, int PPT, bool HEUN = false>
+template <typename R, int PPT, int MODE = kModeEM>
 cudaError_t launch_integrate_t(const Batch &b, const State &s, const Hist &h, const Ckpt &c, const Noise &nz,
                                int64_t g0, int64_t g1, cudaStream_t st) {
     const size_t smem = hist_smem(h);
-    auto kern = integrate_kernel<R, PPT, false, HEUN>;
+    auto kern = integrate_kernel<R, PPT, false, MODE>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -731,7 +763,7 @@ cudaError_t launch_integrate_t(const Batch &b, const State &s, const Hist &h, co
     if (b.n_single > 0)
         kern<<<(unsigned)(b.n_single * sub_s), threads, smem, st>>>(b, s, h, c, nz, key_param(nz.k0, nz.k1), g0, g1);
     if (b.n_tiles > b.n_single)  // packed tiles: one trajectory per thread, histograms in global memory
-        integrate_kernel<R, 1, true, HEUN><<<(unsigned)((b.n_tiles - b.n_single) * sub_p), threads, 0, st>>>(
+        integrate_kernel<R, 1, true, MODE><<<(unsigned)((b.n_tiles - b.n_single) * sub_p), threads, 0, st>>>(
             b, s, h, c, nz, key_param(nz.k0, nz.k1), g0, g1);
     return cudaGetLastError();
 }
@@ -768,9 +800,15 @@ cudaError_t launch_integrate(const Batch &b, const State &s, const Hist &h, cons
         }
     } else if (nz.scheme == 1) {
         switch (ppt) {
-            case 1: return launch_integrate_t<float, 1, true>(b, s, h, c, nz, g0, g1, st);
-            case 2: return launch_integrate_t<float, 2, true>(b, s, h, c, nz, g0, g1, st);
-            case 4: return launch_integrate_t<float, 4, true>(b, s, h, c, nz, g0, g1, st);
+            case 1: return launch_integrate_t<float, 1, kModeHeun>(b, s, h, c, nz, g0, g1, st);
+            case 2: return launch_integrate_t<float, 2, kModeHeun>(b, s, h, c, nz, g0, g1, st);
+            case 4: return launch_integrate_t<float, 4, kModeHeun>(b, s, h, c, nz, g0, g1, st);
+        }
+    } else if (nz.noise == 1) {
+        switch (ppt) {
+            case 1: return launch_integrate_t<float, 1, kModeXorshift>(b, s, h, c, nz, g0, g1, st);
+            case 2: return launch_integrate_t<float, 2, kModeXorshift>(b, s, h, c, nz, g0, g1, st);
+            case 4: return launch_integrate_t<float, 4, kModeXorshift>(b, s, h, c, nz, g0, g1, st);
         }
     } else {
         switch (ppt) {
@@ -794,9 +832,15 @@ cudaError_t launch_persistent(const Batch &b, const State &s, const Hist &h, con
         }
     } else if (nz.scheme == 1) {
         switch (ppt) {
-            case 1: return launch_persistent_t<float, 1, true>(b, s, h, c, nz, q, grid, g0, g1, seg, st);
-            case 2: return launch_persistent_t<float, 2, true>(b, s, h, c, nz, q, grid, g0, g1, seg, st);
-            case 4: return launch_persistent_t<float, 4, true>(b, s, h, c, nz, q, grid, g0, g1, seg, st);
+            case 1: return launch_persistent_t<float, 1, kModeHeun>(b, s, h, c, nz, q, grid, g0, g1, seg, st);
+            case 2: return launch_persistent_t<float, 2, kModeHeun>(b, s, h, c, nz, q, grid, g0, g1, seg, st);
+            case 4: return launch_persistent_t<float, 4, kModeHeun>(b, s, h, c, nz, q, grid, g0, g1, seg, st);
+        }
+    } else if (nz.noise == 1) {
+        switch (ppt) {
+            case 1: return launch_persistent_t<float, 1, kModeXorshift>(b, s, h, c, nz, q, grid, g0, g1, seg, st);
+            case 2: return launch_persistent_t<float, 2, kModeXorshift>(b, s, h, c, nz, q, grid, g0, g1, seg, st);
+            case 4: return launch_persistent_t<float, 4, kModeXorshift>(b, s, h, c, nz, q, grid, g0, g1, seg, st);
         }
     } else {
         switch (ppt) {
@@ -808,18 +852,17 @@ cudaError_t launch_persistent(const Batch &b, const State &s, const Hist &h, con
     return cudaErrorInvalidValue;
 }
 
-cudaError_t persistent_occupancy(bool fp64, int ppt, size_t smem, int *blocks_per_sm, bool heun) {
-    const void *f = nullptr;
-    if (fp64) {
-        f = ppt == 1 ? (const void *)persistent_kernel<double, 1, false>
-            : ppt == 2 ? (const void *)persistent_kernel<double, 2, false> : (const void *)persistent_kernel<double, 4, false>;
-    } else if (heun) {
-        f = ppt == 1 ? (const void *)persistent_kernel<float, 1, true>
-            : ppt == 2 ? (const void *)persistent_kernel<float, 2, true> : (const void *)persistent_kernel<float, 4, true>;
-    } else {
-        f = ppt == 1 ? (const void *)persistent_kernel<float, 1, false>
-            : ppt == 2 ? (const void *)persistent_kernel<float, 2, false> : (const void *)persistent_kernel<float, 4, false>;
-    }
+template <typename R, int MODE>
+const void *persistent_fn(int ppt) {
+    return ppt == 1 ? (const void *)persistent_kernel<R, 1, MODE>
+           : ppt == 2 ? (const void *)persistent_kernel<R, 2, MODE> : (const void *)persistent_kernel<R, 4, MODE>;
+}
+
+cudaError_t persistent_occupancy(bool fp64, int ppt, size_t smem, int *blocks_per_sm, int mode) {
+    const void *f = fp64 ? persistent_fn<double, kModeEM>(ppt)
+                    : mode == kModeHeun ? persistent_fn<float, kModeHeun>(ppt)
+                    : mode == kModeXorshift ? persistent_fn<float, kModeXorshift>(ppt)
+                    : persistent_fn<float, kModeEM>(ppt);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -877,6 +920,23 @@ cudaError_t launch_normals(uint32_t k0, uint32_t k1, uint64_t traj, uint64_t n0,
     if (n0 + (uint64_t)count > ((uint64_t)1 << 34)) return cudaErrorInvalidValue;  // step counters below 2^34
     const int blocks = (int)std::min<int64_t>((count + 255) / 256, 4096);
     normals_kernel<<<blocks, 256, 0, st>>>(key_param(k0, k1), traj, n0, count, out);
+    return cudaGetLastError();
+}
+
+namespace {
+// The first `count` words of one trajectory's xorshift stream (one thread: the
+// stream is sequential by construction).
+__global__ void xorshift_kernel(uint32_t k0, uint32_t k1, uint64_t traj, int64_t count, uint32_t *out) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    const uint4 w = xorshift_seed(traj, k0, k1);
+    uint32_t s[4] = {w.x, w.y, w.z, w.w};
+    for (int64_t i = 0; i < count; ++i) out[i] = xorshift128(s);
+}
+}  // namespace
+
+cudaError_t launch_xorshift(uint32_t k0, uint32_t k1, uint64_t traj, int64_t count, uint32_t *out, cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    xorshift_kernel<<<1, 32, 0, st>>>(k0, k1, traj, count, out);
     return cudaGetLastError();
 }
 

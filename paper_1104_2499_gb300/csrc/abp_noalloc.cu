@@ -137,7 +137,8 @@ extern "C" abp_status abp_run_set_noalloc(const abp_params *params, const abp_co
     if (cfg->hist_v_bins > 0 && !(cfg->v_hi > cfg->v_lo))
         return say(err, err_len, ABP_EINVAL, "v_hi must exceed v_lo");
     if (cfg->scheme != 0 && cfg->scheme != 1) return say(err, err_len, ABP_EINVAL, "scheme must be 0 or 1");
-    if (cfg->reserved != 0) return say(err, err_len, ABP_EINVAL, "reserved must be 0");
+    if (cfg->noise != 0)
+        return say(err, err_len, ABP_EINVAL, "the allocation-free entry point uses the counter-based noise only");
     if (cfg->snapshot_every < 0 || cfg->steps_per_launch < 0 || (cfg->schedule < 0 || cfg->schedule > 2))
         return say(err, err_len, ABP_EINVAL, "invalid snapshot_every / steps_per_launch / schedule");
     const int ppt = cfg->particles_per_thread ? cfg->particles_per_thread : 1;
@@ -201,6 +202,7 @@ extern "C" abp_status abp_run_set_noalloc(const abp_params *params, const abp_co
     s.e = base + kOffE;
     s.y0 = base + kOffY0;
     s.cell = (int32_t *)(base + kOffCell);
+    s.xs = nullptr;
     Hist h;
     h.x = hist_x;
     h.v = hist_v;
@@ -222,6 +224,7 @@ extern "C" abp_status abp_run_set_noalloc(const abp_params *params, const abp_co
     nz.v0_mode = cfg->v0_mode;
     nz.traj_base = cfg->traj_base;
     nz.scheme = cfg->scheme;
+    nz.noise = 0;
 
     e = cudaGetLastError();
     if (e == cudaSuccess) e = launch_init(b, s, h, c, nz, st);

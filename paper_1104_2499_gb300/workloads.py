@@ -43,6 +43,7 @@ class Workload:
     snapshot_every: int = 0     # 0: one snapshot after the last step
     checkpoint_every: int = 0
     scheme: int = 0             # 0: Euler-Maruyama (the paper's step), 1: stochastic Heun
+    noise: int = 0              # 0: counter-based Philox, 1: xorshift per trajectory (Fig. 1)
     notes: str = ""
     extra: dict = field(default_factory=dict)
 
