@@ -8,6 +8,7 @@
 #include <unistd.h>
 
 #include <algorithm>
+#include <map>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -108,9 +109,9 @@ abp_status deliver(abp_ctx *ctx, void *dst, const void *src, size_t n, bool *syn
 
 // Schedule and particles per thread.  Every (schedule, PPT) candidate is timed
 // once per device and state type on a synthetic single-set batch several
-// waves deep (4,096 trajectories per SM, 2,048 steps after a 256-step warm-up,
-// CUDA events on the context's stream); the fastest candidate allowed by the
-// configuration wins.
+// waves deep (4,096 trajectories per SM, 8,192 steps after a 256-step warm-up,
+// CUDA events on the context's stream); autotune() weighs the table with the
+// batch at hand.
 struct TuneTable {
     bool done = false;
     float ms[3][3] = {};  // [schedule 1 = lockstep, 2 = work queue][ppt 1, 2, 4]
@@ -127,7 +128,9 @@ void measure_candidates(abp_ctx *ctx, TuneTable &tt) {
     const int fp = ctx->cfg.state_fp64 ? 1 : 0;
     const bool heun = ctx->cfg.scheme == 1;
     const int64_t T = (int64_t)std::max(ctx->sm_count, 1) * 4096;
-    const int64_t warm = 256, steps = 2048;
+    // the timed window runs as kTrialRounds work-queue rounds, as real batches do
+    constexpr int kTrialRounds = 4;
+    const int64_t warm = 256, steps = 8192;
     const size_t rsz = fp ? sizeof(double) : sizeof(float);
     const int cands[3] = {1, 2, 4};
     const int max_tiles = (int)((T + kThreads - 1) / kThreads);
@@ -167,7 +170,7 @@ void measure_candidates(abp_ctx *ctx, TuneTable &tt) {
     st.xs = xorshift ? (uint4 *)take(sizeof(uint4) * T) : nullptr;
     int32_t *d_queue = (int32_t *)take(sizeof(int32_t) * ((size_t)max_tiles + 1));
     int32_t *d_perm = (int32_t *)take(sizeof(int32_t) * max_tiles);
-    int32_t *d_rs = (int32_t *)take(sizeof(int32_t) * 2);
+    int32_t *d_rs = (int32_t *)take(sizeof(int32_t) * (kTrialRounds + 1));
     int32_t *d_status = (int32_t *)take(sizeof(int32_t));
     Hist h{};
     Ckpt ck{};
@@ -191,7 +194,8 @@ void measure_candidates(abp_ctx *ctx, TuneTable &tt) {
             perm[t] = t;
         }
         const int32_t stb[2] = {0, nt};
-        const int32_t rs[2] = {0, nt};
+        int32_t rs[kTrialRounds + 1];
+        for (int r = 0; r <= kTrialRounds; ++r) rs[r] = r * nt;
         cudaMemcpyAsync(d_prm, &prm, sizeof(prm), cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(d_steps, &nsteps, sizeof(nsteps), cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(d_stb, stb, sizeof(stb), cudaMemcpyHostToDevice, s);
@@ -236,7 +240,12 @@ void measure_candidates(abp_ctx *ctx, TuneTable &tt) {
                     launch_integrate(b, st, h, ck, nz, c, g0, g1, s);
                 } else {
                     cudaMemsetAsync(d_queue, 0, sizeof(int32_t) * ((size_t)nt + 1), s);
-                    launch_persistent(b, st, h, ck, nz, q, c, grid, g0, g1, g1 - g0, s);
+                    // the warm-up as one round, the timed window as kTrialRounds rounds
+                    Queue qw = q;
+                    const int rounds = g0 == 0 ? 1 : kTrialRounds;
+                    qw.n_rounds = rounds;
+                    qw.n_items = rounds * nt;
+                    launch_persistent(b, st, h, ck, nz, qw, c, grid, g0, g1, (g1 - g0) / rounds, s);
                 }
             };
             launch_init(b, st, h, ck, nz, s);
@@ -329,7 +338,66 @@ void save_tune(const abp_ctx *ctx, const TuneTable &tt) {
     if (rename(tmp.c_str(), path.c_str()) != 0) remove(tmp.c_str());
 }
 
-// Sets ctx->sched and ctx->ppt from the configuration and the timing table.
+// Fraction of a candidate's launch capacity that the batch keeps busy, in
+// particle-steps: lockstep runs the tiles that still have steps in each window
+// of the default length, in waves of `cap` resident blocks (small sets of
+// equal step count share packed tiles); the work queue balances all
+// tile-steps over `cap` blocks, plus half a work item of tail, bounded below by
+// the longest tile's chain.
+// A tile of kThreads * ppt slots costs the same however full it is.
+double batch_efficiency(const abp_ctx *ctx, int sched, int ppt, int64_t cap) {
+    const int32_t n = ctx->n_sets;
+    const int64_t slots = (int64_t)kThreads * ppt;
+    std::vector<std::pair<int64_t, int64_t>> tiles;  // (tile count, steps)
+    std::map<int64_t, int64_t> small;               // steps -> trajectories of small sets (lockstep packs them)
+    double useful = 0.0;
+    int64_t max_n = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        const int64_t M = ctx->n_traj[i], N = ctx->n_steps[i];
+        if (M <= 0 || N <= 0) continue;
+        useful += (double)M * (double)N;
+        max_n = std::max(max_n, N);
+        if (sched == 1 && ctx->cfg.checkpoint_every == 0 && M < kThreads)
+            small[N] += M;
+        else
+            tiles.emplace_back((M + slots - 1) / slots, N);
+    }
+    for (const auto &kv : small) tiles.emplace_back((kv.second + kThreads - 1) / kThreads, kv.first);
+    if (useful <= 0.0 || cap <= 0) return 1.0;
+    double cost = 0.0;  // particle-step capacity spent
+    if (sched == 2) {
+        // list scheduling of the work items: makespan about W / cap plus half an item
+        double tile_steps = 0.0;
+        for (const auto &t : tiles) tile_steps += (double)t.first * (double)t.second;
+        int64_t item = 1000;
+        for (int64_t S : {100000, 10000, 1000}) {
+            int64_t items = 0;
+            for (const auto &t : tiles) items += t.first * ((t.second + S - 1) / S);
+            if (items >= 32 * cap) {
+                item = S;
+                break;
+            }
+        }
+        const double span = std::max(tile_steps / (double)cap + 0.5 * (double)std::min(item, max_n), (double)max_n);
+        cost = (double)cap * span * (double)slots;
+    } else {
+        const int64_t spl = ctx->cfg.steps_per_launch > 0 ? ctx->cfg.steps_per_launch : default_steps_per_launch(ctx);
+        for (int64_t g = 0; g < max_n; g += spl) {
+            int64_t active = 0, len = 0;
+            for (const auto &t : tiles)
+                if (t.second > g) {
+                    active += t.first;
+                    len = std::max(len, std::min(t.second, g + spl) - g);
+                }
+            cost += (double)((active + cap - 1) / cap) * (double)cap * (double)len * (double)slots;
+        }
+    }
+    return cost > 0.0 ? std::min(1.0, useful / cost) : 1.0;
+}
+
+// Sets ctx->sched and ctx->ppt from the configuration, the timing table and
+// the batch: each allowed candidate's trial time divided by the fraction of
+// its capacity this batch keeps busy; the smallest prediction wins.
 void autotune(abp_ctx *ctx) {
     const int want_sched = ctx->cfg.schedule;          // 0 auto, 1 lockstep, 2 work queue
     const int want_ppt = ctx->cfg.particles_per_thread;  // 0 auto
@@ -346,14 +414,24 @@ void autotune(abp_ctx *ctx) {
         if (tt.done) save_tune(ctx, tt);
     }
     const int cands[3] = {1, 2, 4};
-    float best = 1e30f;
+    const abp_config &c = ctx->cfg;
+    const size_t smem = sizeof(uint32_t) * (size_t)(c.hist_x_bins + (c.hist_v_bins > 0 ? c.hist_v_bins + 2 : 0));
+    const int mode = c.scheme == 1 ? 1 : c.noise == 1 ? 2 : 0;
+    double best = 1e300;
     int bs = want_sched ? want_sched : 1, bp = want_ppt ? want_ppt : 1;
     for (int sch = 1; sch <= 2; ++sch) {
         if (want_sched && sch != want_sched) continue;
         for (int ci = 0; ci < 3; ++ci) {
             if (want_ppt && cands[ci] != want_ppt) continue;
-            if (tt.ms[sch][ci] < best) {
-                best = tt.ms[sch][ci];
+            if (!(tt.ms[sch][ci] < 1e29f)) continue;
+            int bps = 0;
+            const cudaError_t oe = sch == 1 ? integrate_occupancy(c.state_fp64 != 0, cands[ci], smem, &bps, mode)
+                                            : persistent_occupancy(c.state_fp64 != 0, cands[ci], smem, &bps, mode);
+            if (oe != cudaSuccess) cudaGetLastError();
+            const int64_t cap = (int64_t)std::max(bps, 1) * std::max(ctx->sm_count, 1);
+            const double pred = (double)tt.ms[sch][ci] / batch_efficiency(ctx, sch, cands[ci], cap);
+            if (pred < best) {
+                best = pred;
                 bs = sch;
                 bp = cands[ci];
             }

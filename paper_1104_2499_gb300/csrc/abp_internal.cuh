@@ -120,5 +120,6 @@ cudaError_t launch_persistent(const Batch &b, const State &s, const Hist &h, con
 // Resident blocks per SM of the persistent integrator (sets its shared-memory limit too).
 // mode: 0 Euler-Maruyama, 1 stochastic Heun, 2 Euler-Maruyama with xorshift noise
 cudaError_t persistent_occupancy(bool fp64, int ppt, size_t smem, int *blocks_per_sm, int mode = 0);
+cudaError_t integrate_occupancy(bool fp64, int ppt, size_t smem, int *blocks_per_sm, int mode = 0);
 
 }  // namespace abp

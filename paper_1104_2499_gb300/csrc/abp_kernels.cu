@@ -870,6 +870,24 @@ cudaError_t persistent_occupancy(bool fp64, int ppt, size_t smem, int *blocks_pe
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, kThreads, smem);
 }
 
+template <typename R, int MODE>
+const void *integrate_fn(int ppt) {
+    return ppt == 1 ? (const void *)integrate_kernel<R, 1, false, MODE>
+           : ppt == 2 ? (const void *)integrate_kernel<R, 2, false, MODE> : (const void *)integrate_kernel<R, 4, false, MODE>;
+}
+
+cudaError_t integrate_occupancy(bool fp64, int ppt, size_t smem, int *blocks_per_sm, int mode) {
+    const void *f = fp64 ? integrate_fn<double, kModeEM>(ppt)
+                    : mode == kModeHeun ? integrate_fn<float, kModeHeun>(ppt)
+                    : mode == kModeXorshift ? integrate_fn<float, kModeXorshift>(ppt)
+                    : integrate_fn<float, kModeEM>(ppt);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, kThreads, smem);
+}
+
 cudaError_t launch_reduce(const Batch &b, const State &s, const Noise &nz, int64_t g, double *partials,
                           double *moments, cudaStream_t st) {
     if (b.n_sets == 0) return cudaSuccess;
