@@ -99,13 +99,15 @@ typedef struct {
                                     0: one snapshot after each set's last step */
     int64_t checkpoint_every;    /* K > 0: keep the state every K steps for abp_backward;
                                     0: no checkpoints (abp_backward returns ABP_ESTATE) */
-    int32_t particles_per_thread;/* 1, 2 or 4 trajectories per CUDA thread; 0 = autotuned (timed on
-                                    this device once per process) */
-    int32_t schedule;            /* 0: chosen by the autotuner (timed on this device once per
-                                    process); 1: lockstep -- one launch per window of
-                                    steps_per_launch steps over all tiles; 2: work queue -- one
+    int32_t particles_per_thread;/* 1, 2 or 4 trajectories per CUDA thread; 0 = autotuned */
+    int32_t schedule;            /* 0: chosen by the autotuner; 1: lockstep -- one launch per window
+                                    of steps_per_launch steps over all tiles; 2: work queue -- one
                                     persistent launch whose blocks pop (tile, round) items, so
-                                    uneven sets balance across SMs */
+                                    uneven sets balance across SMs.  The autotuner times every
+                                    (schedule, particles_per_thread) pair once per device and
+                                    library build (table kept beside the library) and predicts
+                                    each pair's time on the batch of abp_set_params from the busy
+                                    fraction of its resident blocks */
     int64_t steps_per_launch;    /* lockstep: steps per launch; work queue: steps per work item
                                     (round); 0 = chosen automatically */
     uint64_t traj_base;          /* added to every global trajectory id: a process that runs
