@@ -105,13 +105,18 @@ def test_autotuner_choices(abp):
 
 
 def test_autotuner_weighs_the_batch(abp):
-    # the uneven batch (step counts over two decades) leaves lockstep windows with few tiles
-    # at the end; the work queue keeps every block busy, so it is predicted (and measured,
-    # 9.41e11 against 9.08e11 particle-steps/s) faster there
-    w = W.uneven_batch()
+    # the load sweep (64 sets x 4,096 trajectories) fills 1.1 waves of lockstep blocks, so
+    # half the second wave idles in every window; the work queue keeps every block busy and
+    # is predicted (and measured, 8.56e11 against 8.04e11 particle-steps/s) faster.  A batch
+    # nine waves deep stays with lockstep's better per-step code.
+    w = W.force_sweep()
     with abp.Ensemble(w) as ens:
         ens.set_params()
         assert ens.tuning()["schedule"] == 2
+    big = W.sweep_grid(n_steps=20_000)  # 2,048 x 1,024 trajectories: nine lockstep waves
+    with abp.Ensemble(big) as ens:
+        ens.set_params()
+        assert ens.tuning()["schedule"] == 1
 
 
 def test_bounded_wait_reports_timeout_and_context_recovers(abp):
