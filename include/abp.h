@@ -256,6 +256,27 @@ ABP_API abp_status abp_tuning(const abp_ctx *ctx, int32_t *schedule, int32_t *pa
  * tiling never changes a result: state, moments and histograms are the same bits. */
 ABP_API abp_status abp_tiles(const abp_ctx *ctx, int32_t *n_tiles, int32_t *n_packed, int32_t *narrow);
 
+/* Host-only planning, the logic abp_set_params applies (no device work, usable
+ * without a GPU).  abp_plan: the tiling of a batch of n_sets sets (n_traj,
+ * n_steps host arrays) for `schedule` (1 lockstep, 2 work queue),
+ * particles_per_thread (1, 2, 4), adjoint checkpoints on (checkpoints != 0) or
+ * off, on a device of sm_count SMs.  Outputs (host, any may be NULL): tiles in
+ * all, packed tiles among them, narrow block width (0 if not narrow); and, when
+ * max_tiles >= the tile count, every tile's first trajectory, trajectory count
+ * and set (a packed tile: its first non-empty set).  A negative count or a
+ * schedule / particles_per_thread out of range gives ABP_EINVAL.
+ * abp_plan_efficiency: the fraction of the launch capacity (resident_blocks
+ * blocks of 256 * particles_per_thread trajectories) the batch keeps busy, in
+ * particle-steps, which the autotuner divides each candidate's trial time by;
+ * steps_per_launch 0 = the default lockstep window. */
+ABP_API abp_status abp_plan(int32_t n_sets, const int64_t *n_traj, const int64_t *n_steps, int32_t schedule,
+                            int32_t particles_per_thread, int32_t checkpoints, int32_t sm_count, int32_t *n_tiles,
+                            int32_t *n_packed, int32_t *narrow, int64_t *tile_first, int32_t *tile_count,
+                            int32_t *tile_set, int32_t max_tiles);
+ABP_API abp_status abp_plan_efficiency(int32_t n_sets, const int64_t *n_traj, const int64_t *n_steps,
+                                       int32_t schedule, int32_t particles_per_thread, int32_t checkpoints,
+                                       int64_t steps_per_launch, int64_t resident_blocks, double *efficiency);
+
 /* Number of kernels this context has enqueued since it was created (host output). */
 ABP_API abp_status abp_kernel_launches(const abp_ctx *ctx, int64_t *launches);
 

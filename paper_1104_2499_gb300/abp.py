@@ -92,6 +92,13 @@ def lib():
                                  C.POINTER(C.c_int32)]
         L.abp_tuning.restype = st
         L.abp_tiles.argtypes = [_VP, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+        P64, P32 = C.POINTER(C.c_int64), C.POINTER(C.c_int32)
+        L.abp_plan.argtypes = [C.c_int32, P64, P64, C.c_int32, C.c_int32, C.c_int32, C.c_int32, P32, P32, P32,
+                               P64, P32, P32, C.c_int32]
+        L.abp_plan.restype = st
+        L.abp_plan_efficiency.argtypes = [C.c_int32, P64, P64, C.c_int32, C.c_int32, C.c_int32, C.c_int64,
+                                          C.c_int64, C.POINTER(C.c_double)]
+        L.abp_plan_efficiency.restype = st
         L.abp_xorshift.argtypes = [C.c_uint64, C.c_uint64, C.c_int64, _VP, _VP]
         L.abp_xorshift.restype = st
         L.abp_live.argtypes = [_VP, _VP, _VP, _VP]
@@ -203,6 +210,35 @@ def abp_tiles(ctx):
     t, p, n = C.c_int32(), C.c_int32(), C.c_int32()
     _check(lib().abp_tiles(ctx, C.byref(t), C.byref(p), C.byref(n)), ctx)
     return {"tiles": t.value, "packed": p.value, "narrow": n.value}
+
+
+def abp_plan(n_traj, n_steps, schedule: int, particles_per_thread: int, checkpoints: bool = False,
+             sm_count: int = 152) -> dict:
+    """The tiling abp_set_params makes for this batch (host only, no GPU needed)."""
+    n = len(n_traj)
+    M = (C.c_int64 * max(n, 1))(*[int(v) for v in n_traj])
+    N = (C.c_int64 * max(n, 1))(*[int(v) for v in n_steps])
+    nt, npk, nar = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(lib().abp_plan(n, M, N, schedule, particles_per_thread, 1 if checkpoints else 0, sm_count, C.byref(nt),
+                          C.byref(npk), C.byref(nar), None, None, None, 0), what="abp_plan")
+    k = nt.value
+    first, count, sset = (C.c_int64 * max(k, 1))(), (C.c_int32 * max(k, 1))(), (C.c_int32 * max(k, 1))()
+    _check(lib().abp_plan(n, M, N, schedule, particles_per_thread, 1 if checkpoints else 0, sm_count, None, None,
+                          None, first, count, sset, k), what="abp_plan")
+    return {"tiles": k, "packed": npk.value, "narrow": nar.value, "tile_first": list(first[:k]),
+            "tile_count": list(count[:k]), "tile_set": list(sset[:k])}
+
+
+def abp_plan_efficiency(n_traj, n_steps, schedule: int, particles_per_thread: int, resident_blocks: int,
+                        checkpoints: bool = False, steps_per_launch: int = 0) -> float:
+    """Busy fraction of a candidate's launch capacity for this batch (the autotuner's model)."""
+    n = len(n_traj)
+    M = (C.c_int64 * max(n, 1))(*[int(v) for v in n_traj])
+    N = (C.c_int64 * max(n, 1))(*[int(v) for v in n_steps])
+    e = C.c_double()
+    _check(lib().abp_plan_efficiency(n, M, N, schedule, particles_per_thread, 1 if checkpoints else 0,
+                                     steps_per_launch, resident_blocks, C.byref(e)), what="abp_plan_efficiency")
+    return e.value
 
 
 def abp_xorshift(seed: int, traj: int, out, stream=None):

@@ -82,16 +82,18 @@ bool finite_params(const abp_params &p) {
     return true;
 }
 
-int64_t default_steps_per_launch(const abp_ctx *ctx) {
-    // Equal windows of about 2e10 particle-steps each (tens of ms on a GB300),
-    // a multiple of 64 steps.
-    if (ctx->total_traj == 0 || ctx->max_steps == 0) return std::max<int64_t>(ctx->max_steps, 1);
-    const double work = (double)ctx->total_traj * (double)ctx->max_steps;
+// Equal windows of about 2e10 particle-steps each (tens of ms on a GB300),
+// a multiple of 64 steps.
+int64_t default_window(int64_t total_traj, int64_t max_steps) {
+    if (total_traj == 0 || max_steps == 0) return std::max<int64_t>(max_steps, 1);
+    const double work = (double)total_traj * (double)max_steps;
     const int64_t n_launch = std::max<int64_t>(1, (int64_t)std::ceil(work / 2.0e10));
-    int64_t s = (ctx->max_steps + n_launch - 1) / n_launch;
+    int64_t s = (max_steps + n_launch - 1) / n_launch;
     s = ((s + 63) / 64) * 64;
-    return std::max<int64_t>(1, std::min<int64_t>(s, ctx->max_steps));
+    return std::max<int64_t>(1, std::min<int64_t>(s, max_steps));
 }
+
+int64_t default_steps_per_launch(const abp_ctx *ctx) { return default_window(ctx->total_traj, ctx->max_steps); }
 
 // Copy n bytes of a device buffer to a caller pointer that may be host or device.
 abp_status deliver(abp_ctx *ctx, void *dst, const void *src, size_t n, bool *synced) {
@@ -345,19 +347,19 @@ void save_tune(const abp_ctx *ctx, const TuneTable &tt) {
 // tile-steps over `cap` blocks, plus half a work item of tail, bounded below by
 // the longest tile's chain.
 // A tile of kThreads * ppt slots costs the same however full it is.
-double batch_efficiency(const abp_ctx *ctx, int sched, int ppt, int64_t cap) {
-    const int32_t n = ctx->n_sets;
+double batch_efficiency(int32_t n, const int64_t *n_traj, const int64_t *n_steps, int sched, int ppt,
+                        bool checkpoints, int64_t spl, int64_t cap) {
     const int64_t slots = (int64_t)kThreads * ppt;
     std::vector<std::pair<int64_t, int64_t>> tiles;  // (tile count, steps)
     std::map<int64_t, int64_t> small;               // steps -> trajectories of small sets (lockstep packs them)
     double useful = 0.0;
     int64_t max_n = 0;
     for (int32_t i = 0; i < n; ++i) {
-        const int64_t M = ctx->n_traj[i], N = ctx->n_steps[i];
+        const int64_t M = n_traj[i], N = n_steps[i];
         if (M <= 0 || N <= 0) continue;
         useful += (double)M * (double)N;
         max_n = std::max(max_n, N);
-        if (sched == 1 && ctx->cfg.checkpoint_every == 0 && M < kThreads)
+        if (sched == 1 && !checkpoints && M < kThreads)
             small[N] += M;
         else
             tiles.emplace_back((M + slots - 1) / slots, N);
@@ -381,7 +383,7 @@ double batch_efficiency(const abp_ctx *ctx, int sched, int ppt, int64_t cap) {
         const double span = std::max(tile_steps / (double)cap + 0.5 * (double)std::min(item, max_n), (double)max_n);
         cost = (double)cap * span * (double)slots;
     } else {
-        const int64_t spl = ctx->cfg.steps_per_launch > 0 ? ctx->cfg.steps_per_launch : default_steps_per_launch(ctx);
+        spl = std::max<int64_t>(spl, 1);
         for (int64_t g = 0; g < max_n; g += spl) {
             int64_t active = 0, len = 0;
             for (const auto &t : tiles)
@@ -393,6 +395,98 @@ double batch_efficiency(const abp_ctx *ctx, int sched, int ppt, int64_t cap) {
         }
     }
     return cost > 0.0 ? std::min(1.0, useful / cost) : 1.0;
+}
+
+// The tiling of a batch (host only).  Tiles are contiguous runs of at most
+// kThreads * ppt trajectories of one set, followed -- lockstep schedule, no
+// adjoint checkpoints -- by packed tiles: runs of consecutive small sets (fewer
+// than kThreads trajectories each, equal step counts, at least two non-empty)
+// sharing one block, one trajectory per thread.  A lockstep batch with fewer
+// tiles than SMs is launched narrow: blocks of the widest w in {256, 128, 64}
+// that still gives every SM a block (else 32), one trajectory per thread.
+struct TilePlan {
+    std::vector<int64_t> set_first, tile_first;
+    std::vector<int32_t> set_packed, set_tile_begin, tile_count, tile_set, set_order;
+    int32_t n_single = 0, n_unpacked = 0, narrow = 0, sub_single = 1, sub_packed = 1;
+};
+
+bool plan_tiles(int32_t n_sets, const int64_t *n_traj, const int64_t *n_steps, int sched, int ppt, bool checkpoints,
+                int sm_count, TilePlan &p) {
+    const int64_t tile = (int64_t)kThreads * ppt;
+    const bool can_pack = sched == 1 && !checkpoints;
+    p.set_first.assign((size_t)n_sets + 1, 0);
+    for (int32_t i = 0; i < n_sets; ++i) p.set_first[i + 1] = p.set_first[i] + n_traj[i];
+    p.set_packed.assign((size_t)n_sets, 0);
+    std::vector<std::pair<int32_t, int32_t>> groups;  // [first set, end set) of each packed tile
+    if (can_pack) {
+        int32_t i = 0;
+        while (i < n_sets) {
+            if (n_traj[i] <= 0 || n_traj[i] >= kThreads) {
+                ++i;
+                continue;
+            }
+            int32_t j = i, nonempty = 0;
+            int64_t cnt = 0;
+            while (j < n_sets && (n_traj[j] == 0 || (n_traj[j] < kThreads && n_steps[j] == n_steps[i])) &&
+                   cnt + n_traj[j] <= kThreads) {
+                cnt += n_traj[j];
+                nonempty += n_traj[j] > 0 ? 1 : 0;
+                ++j;
+            }
+            if (nonempty >= 2) {
+                groups.emplace_back(i, j);
+                for (int32_t k = i; k < j; ++k) p.set_packed[k] = n_traj[k] > 0 ? 1 : 0;
+            }
+            i = j > i ? j : i + 1;
+        }
+    }
+    p.set_tile_begin.assign(1, 0);
+    p.tile_first.clear();
+    p.tile_count.clear();
+    p.tile_set.clear();
+    for (int32_t i = 0; i < n_sets; ++i) {
+        if (!p.set_packed[i])
+            for (int64_t off = 0; off < n_traj[i]; off += tile) {
+                p.tile_first.push_back(p.set_first[i] + off);
+                p.tile_count.push_back((int32_t)std::min(tile, n_traj[i] - off));
+                p.tile_set.push_back(i);
+            }
+        if (p.tile_first.size() > (size_t)INT32_MAX / 2) return false;
+        p.set_tile_begin.push_back((int32_t)p.tile_first.size());
+    }
+    p.n_single = (int32_t)p.tile_first.size();
+    for (const auto &gr : groups) {
+        int32_t lead = gr.first;
+        while (n_traj[lead] == 0) ++lead;  // the first non-empty set carries the group's step count
+        p.tile_first.push_back(p.set_first[gr.first]);
+        p.tile_count.push_back((int32_t)(p.set_first[gr.second] - p.set_first[gr.first]));
+        p.tile_set.push_back(lead);
+    }
+    const int32_t n_tiles = (int32_t)p.tile_first.size();
+    p.set_order.clear();
+    for (int32_t i = 0; i < n_sets; ++i)
+        if (!p.set_packed[i]) p.set_order.push_back(i);
+    p.n_unpacked = (int32_t)p.set_order.size();
+    for (int32_t i = 0; i < n_sets; ++i)
+        if (p.set_packed[i]) p.set_order.push_back(i);
+    p.narrow = 0;
+    p.sub_single = p.sub_packed = 1;
+    if (sched == 1 && n_tiles > 0 && n_tiles < sm_count) {
+        int w = 32;
+        for (int cand : {256, 128, 64}) {
+            if (cand >= tile) continue;
+            int64_t blocks = 0;
+            for (int32_t t = 0; t < n_tiles; ++t) blocks += (p.tile_count[t] + cand - 1) / cand;
+            if (blocks >= sm_count) {
+                w = cand;
+                break;
+            }
+        }
+        p.narrow = w;
+        p.sub_single = (int32_t)((tile + w - 1) / w);
+        p.sub_packed = kThreads / w;
+    }
+    return true;
 }
 
 // Sets ctx->sched and ctx->ppt from the configuration, the timing table and
@@ -429,7 +523,10 @@ void autotune(abp_ctx *ctx) {
                                             : persistent_occupancy(c.state_fp64 != 0, cands[ci], smem, &bps, mode);
             if (oe != cudaSuccess) cudaGetLastError();
             const int64_t cap = (int64_t)std::max(bps, 1) * std::max(ctx->sm_count, 1);
-            const double pred = (double)tt.ms[sch][ci] / batch_efficiency(ctx, sch, cands[ci], cap);
+            const int64_t spl = c.steps_per_launch > 0 ? c.steps_per_launch : default_steps_per_launch(ctx);
+            const double pred = (double)tt.ms[sch][ci] / batch_efficiency(ctx->n_sets, ctx->n_traj.data(),
+                                                                          ctx->n_steps.data(), sch, cands[ci],
+                                                                          c.checkpoint_every > 0, spl, cap);
             if (pred < best) {
                 best = pred;
                 bs = sch;
@@ -571,87 +668,25 @@ abp_status abp_set_params(abp_ctx *ctx, int32_t n_sets, const abp_params *sets, 
     ctx->g = 0;
     ctx->ckpt_complete = true;
 
-    // Tiles: contiguous runs of at most kThreads * ppt trajectories of one set,
-    // then -- lockstep schedule, no adjoint checkpoints -- packed tiles: groups of
-    // consecutive small sets (fewer than kThreads trajectories each, equal step
-    // counts) sharing one block, one trajectory per thread.
     autotune(ctx);
-    const int64_t tile = (int64_t)kThreads * ctx->ppt;
-    const bool can_pack = ctx->sched == 1 && ctx->cfg.checkpoint_every == 0;
-    ctx->set_first.assign((size_t)n_sets + 1, 0);
-    for (int32_t i = 0; i < n_sets; ++i) ctx->set_first[i + 1] = ctx->set_first[i] + n_traj[i];
-    ctx->set_packed.assign((size_t)n_sets, 0);
-    std::vector<std::pair<int32_t, int32_t>> groups;  // [first set, end set) of each packed tile
-    if (can_pack) {
-        int32_t i = 0;
-        while (i < n_sets) {
-            if (n_traj[i] <= 0 || n_traj[i] >= kThreads) {
-                ++i;
-                continue;
-            }
-            int32_t j = i, nonempty = 0;
-            int64_t cnt = 0;
-            while (j < n_sets && (n_traj[j] == 0 || (n_traj[j] < kThreads && n_steps[j] == n_steps[i])) &&
-                   cnt + n_traj[j] <= kThreads) {
-                cnt += n_traj[j];
-                nonempty += n_traj[j] > 0 ? 1 : 0;
-                ++j;
-            }
-            if (nonempty >= 2) {
-                groups.emplace_back(i, j);
-                for (int32_t k = i; k < j; ++k) ctx->set_packed[k] = n_traj[k] > 0 ? 1 : 0;
-            }
-            i = j > i ? j : i + 1;
-        }
-    }
-    ctx->set_tile_begin.assign(1, 0);
-    ctx->tile_first.clear();
-    ctx->tile_count.clear();
-    ctx->tile_set.clear();
-    for (int32_t i = 0; i < n_sets; ++i) {
-        if (!ctx->set_packed[i])
-            for (int64_t off = 0; off < n_traj[i]; off += tile) {
-                ctx->tile_first.push_back(ctx->set_first[i] + off);
-                ctx->tile_count.push_back((int32_t)std::min(tile, n_traj[i] - off));
-                ctx->tile_set.push_back(i);
-            }
-        if (ctx->tile_first.size() > (size_t)INT32_MAX / 2) return fail(ctx, ABP_EINVAL, "too many tiles");
-        ctx->set_tile_begin.push_back((int32_t)ctx->tile_first.size());
-    }
-    ctx->n_single = (int32_t)ctx->tile_first.size();
-    for (const auto &gr : groups) {
-        int32_t lead = gr.first;
-        while (n_traj[lead] == 0) ++lead;  // the first non-empty set carries the group's step count
-        ctx->tile_first.push_back(ctx->set_first[gr.first]);
-        ctx->tile_count.push_back((int32_t)(ctx->set_first[gr.second] - ctx->set_first[gr.first]));
-        ctx->tile_set.push_back(lead);
-    }
-    ctx->n_tiles = (int32_t)ctx->tile_first.size();
-    ctx->set_order.clear();
-    for (int32_t i = 0; i < n_sets; ++i)
-        if (!ctx->set_packed[i]) ctx->set_order.push_back(i);
-    ctx->n_unpacked = (int32_t)ctx->set_order.size();
-    for (int32_t i = 0; i < n_sets; ++i)
-        if (ctx->set_packed[i]) ctx->set_order.push_back(i);
-    // A lockstep batch with fewer tiles than SMs is launched narrow: blocks of
-    // the widest w in {256, 128, 64} that still gives every SM a block (else 32),
-    // one trajectory per thread, so its warps spread over the SMs.
-    ctx->narrow = 0;
-    ctx->sub_single = ctx->sub_packed = 1;
-    if (ctx->sched == 1 && ctx->n_tiles > 0 && ctx->n_tiles < ctx->sm_count) {
-        int w = 32;
-        for (int cand : {256, 128, 64}) {
-            if (cand >= tile) continue;
-            int64_t blocks = 0;
-            for (int32_t t = 0; t < ctx->n_tiles; ++t) blocks += (ctx->tile_count[t] + cand - 1) / cand;
-            if (blocks >= ctx->sm_count) {
-                w = cand;
-                break;
-            }
-        }
-        ctx->narrow = w;
-        ctx->sub_single = (int32_t)((tile + w - 1) / w);
-        ctx->sub_packed = kThreads / w;
+    {
+        TilePlan plan;
+        if (!plan_tiles(n_sets, n_traj, n_steps, ctx->sched, ctx->ppt, ctx->cfg.checkpoint_every > 0, ctx->sm_count,
+                        plan))
+            return fail(ctx, ABP_EINVAL, "too many tiles");
+        ctx->set_first.swap(plan.set_first);
+        ctx->set_packed.swap(plan.set_packed);
+        ctx->set_tile_begin.swap(plan.set_tile_begin);
+        ctx->tile_first.swap(plan.tile_first);
+        ctx->tile_count.swap(plan.tile_count);
+        ctx->tile_set.swap(plan.tile_set);
+        ctx->set_order.swap(plan.set_order);
+        ctx->n_single = plan.n_single;
+        ctx->n_tiles = (int32_t)ctx->tile_first.size();
+        ctx->n_unpacked = plan.n_unpacked;
+        ctx->narrow = plan.narrow;
+        ctx->sub_single = plan.sub_single;
+        ctx->sub_packed = plan.sub_packed;
     }
     const abp_config &c = ctx->cfg;
     const bool any_hist = c.hist_x_bins > 0 || c.hist_v_bins > 0;
@@ -1016,6 +1051,55 @@ abp_status abp_live_ready(abp_ctx *ctx, int64_t *n_ready) {
         ++ctx->live_ready;
     }
     *n_ready = ctx->live_ready;
+    return ABP_OK;
+}
+
+namespace {
+bool plan_args_ok(int32_t n_sets, const int64_t *n_traj, const int64_t *n_steps, int32_t schedule, int32_t ppt) {
+    if (n_sets < 0 || (n_sets > 0 && (!n_traj || !n_steps))) return false;
+    if (schedule != 1 && schedule != 2) return false;
+    if (ppt != 1 && ppt != 2 && ppt != 4) return false;
+    for (int32_t i = 0; i < n_sets; ++i)
+        if (n_traj[i] < 0 || n_steps[i] < 0) return false;
+    return true;
+}
+}  // namespace
+
+abp_status abp_plan(int32_t n_sets, const int64_t *n_traj, const int64_t *n_steps, int32_t schedule,
+                    int32_t particles_per_thread, int32_t checkpoints, int32_t sm_count, int32_t *n_tiles,
+                    int32_t *n_packed, int32_t *narrow, int64_t *tile_first, int32_t *tile_count, int32_t *tile_set,
+                    int32_t max_tiles) {
+    if (!plan_args_ok(n_sets, n_traj, n_steps, schedule, particles_per_thread) || sm_count < 1) return ABP_EINVAL;
+    TilePlan p;
+    if (!plan_tiles(n_sets, n_traj, n_steps, schedule, particles_per_thread, checkpoints != 0, sm_count, p))
+        return ABP_EINVAL;
+    const int32_t nt = (int32_t)p.tile_first.size();
+    if (n_tiles) *n_tiles = nt;
+    if (n_packed) *n_packed = nt - p.n_single;
+    if (narrow) *narrow = p.narrow;
+    if (max_tiles >= nt)
+        for (int32_t t = 0; t < nt; ++t) {
+            if (tile_first) tile_first[t] = p.tile_first[t];
+            if (tile_count) tile_count[t] = p.tile_count[t];
+            if (tile_set) tile_set[t] = p.tile_set[t];
+        }
+    return ABP_OK;
+}
+
+abp_status abp_plan_efficiency(int32_t n_sets, const int64_t *n_traj, const int64_t *n_steps, int32_t schedule,
+                               int32_t particles_per_thread, int32_t checkpoints, int64_t steps_per_launch,
+                               int64_t resident_blocks, double *efficiency) {
+    if (!efficiency || !plan_args_ok(n_sets, n_traj, n_steps, schedule, particles_per_thread) || resident_blocks < 1 ||
+        steps_per_launch < 0)
+        return ABP_EINVAL;
+    int64_t total = 0, max_n = 0;
+    for (int32_t i = 0; i < n_sets; ++i) {
+        total += n_traj[i];
+        max_n = std::max(max_n, n_steps[i]);
+    }
+    const int64_t spl = steps_per_launch > 0 ? steps_per_launch : default_window(total, max_n);
+    *efficiency = batch_efficiency(n_sets, n_traj, n_steps, schedule, particles_per_thread, checkpoints != 0, spl,
+                                   resident_blocks);
     return ABP_OK;
 }
 
