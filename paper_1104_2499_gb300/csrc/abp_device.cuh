@@ -208,6 +208,7 @@ struct Coef {
     R K;     // dt h 0.453 2 pi / L
     R A4;    // 4 a K
     R dtL;   // dt / L
+    R hdtL;  // dt / (2 L)
 };
 
 // Phase of the potential: phi = 2 pi (y + 0.1903) = 2 pi (y - 0.8097) + 2 pi.
@@ -232,6 +233,7 @@ __device__ __forceinline__ Coef<R> make_coef(double q, double c, double d, doubl
     k.K = (R)K;
     k.A4 = (R)(4.0 * a * K);
     k.dtL = (R)(dt / L);
+    k.hdtL = (R)(0.5 * dt / L);
     return k;
 }
 
@@ -299,9 +301,9 @@ __device__ __forceinline__ void heun_step_f32(const Coef<float> &k, float nrs, f
     const float c1 = __cosf(phase_arg(pb, fmaf(v, k.dtL, yacc)));
     const float dv1 = fmaf(fmaf(k.A4, c1, k.K), c1, fmaf(fmaf(k.Bd, ep, k.Gd), vp, k.F));
     const float de1 = fmaf(ep, fmaf(-k.Bd, vp * vp, k.Cm), k.Cq);
-    yacc = fmaf(0.5f * (v + vp), k.dtL, yacc);
+    yacc = fmaf(v + vp, k.hdtL, yacc);  // (v + v~) dt / (2 L); halving is exact
     v = v + fmaf(0.5f, dv0 + dv1, sz);
-    e = e + 0.5f * (de0 + de1);
+    e = fmaf(0.5f, de0 + de1, e);
 }
 
 template <typename R>
