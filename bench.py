@@ -595,7 +595,7 @@ def main():
         A.abp_reduce(ens.ctx, mom, hx, None)
         if dist is not None:
             with torch.cuda.stream(stream):
-                dist.all_reduce(mom[:, 4:8])
+                shard.all_reduce_sums_(mom, dist.all_reduce)
 
     for _ in range(args.warmup):
         with torch.cuda.stream(stream):

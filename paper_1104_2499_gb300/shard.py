@@ -47,3 +47,12 @@ def combine(local_moments, n_traj_per_rank, n_steps, dt: float, world: int, all_
     sums = all_reduce(sums)
     M = np.asarray(n_traj_per_rank, dtype=np.float64) * world
     return moments_from_sums(sums, M, n_steps, dt)
+
+
+def all_reduce_sums_(moments, all_reduce) -> None:
+    """In place: add the per-set sums (columns 4..7) of a torch moments tensor [n_sets, 8]
+    across ranks.  The columns are a strided view, which collectives do not take, so they
+    are reduced through a contiguous copy and written back."""
+    sums = moments[:, 4:8].contiguous()
+    all_reduce(sums)
+    moments[:, 4:8].copy_(sums)

@@ -72,6 +72,11 @@ def _worker(rank, world, port, out_dir, fail_rank):
     try:
         res = shard.combine(local, w.n_traj, w.n_steps, w.dt, world, all_reduce)
         np.save(os.path.join(out_dir, "rank%d.npy" % rank), res)
+        # the benchmark's in-place form on a torch moments tensor (a strided column view)
+        mom = torch.from_numpy(local.copy())
+        shard.all_reduce_sums_(mom, dist.all_reduce)
+        np.testing.assert_array_equal(mom[:, 4:8].numpy(), res[:, 4:8])
+        np.testing.assert_array_equal(mom[:, :4].numpy(), local[:, :4])
     except Exception as e:  # the collective ended with an error instead of hanging
         status = "error: " + type(e).__name__
     with open(os.path.join(out_dir, "status%d.txt" % rank), "w") as f:
@@ -99,6 +104,8 @@ def _run(world, fail_rank, tmp_path):
 def test_replicas_combine_to_the_concatenated_ensemble(tmp_path):
     procs = _run(2, -1, tmp_path)
     assert all(p.exitcode == 0 for p in procs)
+    for r in range(2):
+        assert (tmp_path / ("status%d.txt" % r)).read_text() == "ok"
     w = _batch()
     r0 = np.load(tmp_path / "rank0.npy")
     r1 = np.load(tmp_path / "rank1.npy")
