@@ -316,6 +316,9 @@ typedef struct {
     int32_t scheme;         /* 0: Euler-Maruyama (the paper's), 1: stochastic Heun */
     int32_t noise;          /* 0: Philox4x32-10 by (seed, trajectory, step); 1: xorshift per trajectory */
     int32_t reserved;
+    int64_t grad_window;    /* W > 0: windowed gradient -- the tangents restart from zero at steps
+                               W, 2W, ... (each window's time average differentiated with the state
+                               at the window's start held fixed); 0: the full pathwise gradient */
 } or_run_args;
 
 typedef struct {
@@ -410,6 +413,9 @@ static void *run_range(void *arg)
             } else {
                 vsum += s[1];
                 if (a->want_grad) {
+                    if (a->grad_window > 0 && n > 0 && n % a->grad_window == 0)
+                        for (int j = 0; j < 6; ++j)
+                            t[j][0] = t[j][1] = t[j][2] = 0.0;
                     for (int j = 0; j < 6; ++j) {
                         tsum[j] += t[j][1];
                         tangent_step(p, a->dt, z, s, unit[j], t[j]);
@@ -445,7 +451,8 @@ int or_run_set(const or_run_args *a, or_run_out *o)
     if (!a || !o || a->n_traj < 0 || a->n_steps < 0 || !(a->dt > 0.0) || !(a->p.L > 0.0)
         || a->p.D < 0.0 || a->hist_x_bins < 0 || a->hist_v_bins < 0
         || (a->hist_v_bins > 0 && !(a->v_hi > a->v_lo)) || a->scheme < 0 || a->scheme > 1
-        || (a->scheme == 1 && a->want_grad) || a->noise < 0 || a->noise > 1 || (a->noise == 1 && a->want_grad))
+        || (a->scheme == 1 && a->want_grad) || a->noise < 0 || a->noise > 1 || (a->noise == 1 && a->want_grad)
+        || a->grad_window < 0)
         return -1;
     const int64_t M = a->n_traj;
     const int64_t n_snap = or_n_snapshots(a->n_steps, a->snapshot_every);

@@ -52,6 +52,7 @@ class RunArgs(C.Structure):
         ("scheme", C.c_int32),
         ("noise", C.c_int32),
         ("reserved", C.c_int32),
+        ("grad_window", C.c_int64),
     ]
 
 
@@ -201,13 +202,16 @@ def n_snapshots(n_steps: int, snapshot_every: int) -> int:
 def run_set(params: dict, *, seed: int, dt: float, n_traj: int, n_steps: int, traj_base: int = 0,
             v0_mode: int = 0, snapshot_every: int = 0, hist_x_bins: int = 0, hist_v_bins: int = 0,
             v_lo: float = -5.0, v_hi: float = 5.0, want_states: bool = False, want_grad: bool = False,
-            want_traj_grad: bool = False, n_threads: int | None = None, scheme: int = 0, noise: int = 0) -> dict:
+            want_traj_grad: bool = False, n_threads: int | None = None, scheme: int = 0, noise: int = 0,
+            grad_window: int = 0) -> dict:
     """Integrate one parameter set's ensemble in FP64 and reduce it.
 
     ``scheme`` 0 is the paper's explicit Euler-Maruyama step, 1 the stochastic Heun
     predictor-corrector on the same noise (no gradient for it).  ``noise`` 0 is the
     counter-based Philox stream, 1 Marsaglia's xorshift per trajectory (two words and one
-    Box-Muller cosine per step; no gradient for it).
+    Box-Muller cosine per step; no gradient for it).  ``grad_window`` W > 0 restarts the
+    tangents at steps W, 2W, ...: the windowed gradient (each window's contribution to the
+    time average differentiated with the window's initial state held fixed).
 
     Returns a dict with ``sums`` = (sum vbar, sum vbar^2, sum dx, sum dx^2), the derived
     ``mean_v``, ``se_v``, ``msd``, ``d_eff``, per-trajectory ``vbar`` and (optionally) the
@@ -224,6 +228,7 @@ def run_set(params: dict, *, seed: int, dt: float, n_traj: int, n_steps: int, tr
     a.want_grad = 1 if (want_grad or want_traj_grad) else 0
     a.scheme = int(scheme)
     a.noise = int(noise)
+    a.grad_window = int(grad_window)
     o = RunOut()
     out: dict = {}
     keep = []

@@ -349,3 +349,41 @@ def test_edge_cases():
     assert r["hist_x"].sum() == 5 and np.all(r["vbar"] == 0) and np.all(r["x"] == r["x0"])
     with pytest.raises(ValueError):
         O.run_set(p, seed=1, dt=-1e-3, n_traj=5, n_steps=10)
+
+
+# --------------------------------------------------------------------------- windowed gradient
+
+def _gamma_tangent_closed_form(F0, g, dt, N, W):
+    # D = 0, d = 0, h = 0, v0 = 0: v_i = vinf (1 - rho^i), rho = 1 - g dt, and the tangent along
+    # gamma0 obeys t_{i+1} = rho t_i - dt v_i from t = 0 at each window start s:
+    #   t_{s+j} = -dt vinf [ (1 - rho^j) / (1 - rho) - j rho^(s+j-1) ]
+    rho, vinf = 1 - g * dt, F0 / g
+    n = np.arange(N)
+    s = (n // W) * W if W > 0 else np.zeros_like(n)
+    j = n - s
+    t = -dt * vinf * ((1 - rho**j) / (1 - rho) - j * rho ** np.maximum(s + j - 1, 0))
+    t[j == 0] = 0.0
+    return t.mean()
+
+
+@pytest.mark.parametrize("W", [0, 1, 37, 500, 5000])
+def test_windowed_tangent_closed_form(W):
+    p = P(d=0.0, h=0.0, D=0.0, F0=0.4, gamma0=1.5)
+    dt, N = 1e-2, 1200
+    r = O.run_set(p, seed=2, dt=dt, n_traj=3, n_steps=N, want_grad=True, grad_window=W)
+    expect = _gamma_tangent_closed_form(p["F0"], p["gamma0"], dt, N, W if W < N else 0)
+    gi = O.GRAD_PARAMS.index("gamma0")
+    assert r["grad"][gi] == pytest.approx(expect, rel=1e-10)
+
+
+def test_windowed_gradient_limits():
+    p = P(D=0.2)
+    kw = dict(seed=4, dt=1e-3, n_traj=16, n_steps=700, v0_mode=1, want_grad=True)
+    full = O.run_set(p, **kw)["grad"]
+    np.testing.assert_array_equal(O.run_set(p, grad_window=700, **kw)["grad"], full)
+    np.testing.assert_array_equal(O.run_set(p, grad_window=10_000, **kw)["grad"], full)
+    # one-step windows: only the initial velocity's dependence on D survives, in step 0
+    r = O.run_set(p, grad_window=1, **kw)
+    assert np.all(r["grad"][1:] == 0.0)
+    v0 = np.array([O.initial_state(p, 4, 1, t)[1] for t in range(16)])
+    assert r["grad"][0] == pytest.approx(v0.mean() / (2 * p["D"]) / 700, rel=1e-12)
