@@ -280,6 +280,23 @@ def adjoint_leg(A, stream, small=False, size=None, accuracy=True):
         stream.synchronize()
         fwd_ms, bwd_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
         g_full = g.cpu().numpy()[0]
+        # windowed adjoint (windows of 2,000 steps, t = 2): bounded where the full one is not
+        win = 2000 if w.n_steps[0] >= 2000 else w.n_steps[0]
+        g_win = ens.backward(window=win).cpu().numpy()[0] if win % w.checkpoint_every == 0 else None
+    windowed = None
+    if g_win is not None and accuracy:
+        # the oracle's windowed tangent on 1,024 trajectories of the same set: its mean and
+        # standard error (paths decorrelate over the horizon, so this is a statistical check)
+        sub = 1024
+        r = O.run_set(w.sets[0], seed=w.seed, dt=w.dt, n_traj=sub, n_steps=w.n_steps[0], v0_mode=w.v0_mode,
+                      want_traj_grad=True, grad_window=win)
+        se = r["dvbar"].std(axis=0, ddof=1) / math.sqrt(sub)
+        z = np.abs(g_win - r["grad"]) / np.maximum(se, 1e-300)
+        windowed = {"window_steps": win, "grad_gpu": dict(zip(A.GRAD_PARAMS, map(float, g_win))),
+                    "oracle_subset_mean": dict(zip(A.GRAD_PARAMS, map(float, r["grad"]))),
+                    "oracle_subset_se": dict(zip(A.GRAD_PARAMS, map(float, se))),
+                    "max_abs_diff_over_se": float(z.max()), "oracle_subset_trajectories": sub}
+
     def check(n_steps, rel_h, K):
         wa = W.differentiation(n_traj=4096, n_steps=n_steps, checkpoint_every=K)
         with A.Ensemble(wa, stream=stream) as ens, torch.cuda.stream(stream):
@@ -307,7 +324,7 @@ def adjoint_leg(A, stream, small=False, size=None, accuracy=True):
     return {"workload": w.name, "particle_steps": w.particle_steps, "checkpoint_every": w.checkpoint_every,
             "forward_ms": fwd_ms, "backward_ms": bwd_ms, "backward_over_forward": bwd_ms / fwd_ms,
             "max_abs_pathwise_grad_full_horizon": float(np.max(np.abs(g_full))),
-            "accuracy": acc}
+            "windowed": windowed, "accuracy": acc}
 
 
 # ----------------------------------------------------------------------------- visualisation leg

@@ -231,6 +231,17 @@ ABP_API abp_status abp_load(abp_ctx *ctx, const void *buf, size_t bytes);
  * reverse, accumulating in FP64. */
 ABP_API abp_status abp_backward(abp_ctx *ctx, const double *dJ_dmean_v, double *grad);
 
+/* Windowed pathwise adjoint: as abp_backward, with the adjoint state restarted
+ * from zero at steps window, 2 window, ... -- each window's contribution to
+ * the time-averaged velocity differentiated with the state at the window's
+ * start held fixed.  Over long horizons the frozen-noise dynamics of Sec. 2 is
+ * chaotic and the full pathwise derivative grows exponentially with time; the
+ * windowed derivative stays bounded (a truncated sensitivity: it leaves out
+ * the effect of a parameter change that outlasts a window).  window must be a
+ * positive multiple of checkpoint_every (else ABP_EINVAL); window >= the run
+ * length gives abp_backward's result. */
+ABP_API abp_status abp_backward_windowed(abp_ctx *ctx, const double *dJ_dmean_v, double *grad, int64_t window);
+
 /* Upper bound, in nanoseconds, of every device-side wait of the work-queue
  * schedule (schedule 2) (a work item waiting for the previous round of its tile); 0 restores
  * the default of 60 s.  An expired wait ends the launch with ABP_ETIMEOUT

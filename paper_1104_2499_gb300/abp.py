@@ -122,6 +122,8 @@ def lib():
         L.abp_load.restype = st
         L.abp_backward.argtypes = [_VP, _VP, _VP]
         L.abp_backward.restype = st
+        L.abp_backward_windowed.argtypes = [_VP, _VP, _VP, C.c_int64]
+        L.abp_backward_windowed.restype = st
         L.abp_synchronize.argtypes = [_VP]
         L.abp_synchronize.restype = st
         L.abp_destroy.argtypes = [_VP]
@@ -299,8 +301,11 @@ def abp_load(ctx, buf):
     _check(lib().abp_load(ctx, _ptr(buf), nbytes), ctx)
 
 
-def abp_backward(ctx, dJ_dmean_v=None, grad=None):
-    _check(lib().abp_backward(ctx, _ptr(dJ_dmean_v), _ptr(grad)), ctx)
+def abp_backward(ctx, dJ_dmean_v=None, grad=None, window: int = 0):
+    if window:
+        _check(lib().abp_backward_windowed(ctx, _ptr(dJ_dmean_v), _ptr(grad), int(window)), ctx)
+    else:
+        _check(lib().abp_backward(ctx, _ptr(dJ_dmean_v), _ptr(grad)), ctx)
 
 
 def abp_synchronize(ctx):
@@ -444,11 +449,11 @@ class Ensemble:
         abp_get_state(self.ctx, out["x"], out["x0"], out["v"], out["e"], out["vbar"])
         return out
 
-    def backward(self, dJ=None, host: bool = False):
+    def backward(self, dJ=None, host: bool = False, window: int = 0):
         torch = self.torch
         dev = "cpu" if host else self.device
         g = torch.empty((self.w.n_sets, 6), dtype=torch.float64, device=dev)
-        abp_backward(self.ctx, dJ, g)
+        abp_backward(self.ctx, dJ, g, window)
         return g
 
     def synchronize(self):

@@ -289,7 +289,8 @@ __global__ void __launch_bounds__(kL1Threads) adjoint_level1_kernel(AdjArgs a, i
 }
 
 __global__ void __launch_bounds__(kRevThreads, ABP_ADJ_MIN_BLOCKS) adjoint_reverse_kernel(AdjArgs a, SegView sv,
-                                                                                          int64_t seg, int sub) {
+                                                                                          int64_t seg, int sub,
+                                                                                          int64_t window) {
     const Batch &b = a.b;
     const int tile = (int)blockIdx.x / sub;
     const int li = ((int)blockIdx.x % sub) * (int)blockDim.x + (int)threadIdx.x;
@@ -305,7 +306,9 @@ __global__ void __launch_bounds__(kRevThreads, ABP_ADJ_MIN_BLOCKS) adjoint_rever
     if (li >= b.tile_count[tile]) return;
     const int64_t idx = b.tile_first[tile] + li;
     const StepStream ss = step_stream((uint64_t)idx + a.nz.traj_base, a.K);
-    const float4 l0 = sv.lam[idx];
+    float4 l0 = sv.lam[idx];
+    // windowed adjoint: the window ending at step (seg + 1) K starts from zero
+    if (window > 0 && ((seg + 1) * K) % window == 0) l0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     float lx = l0.x, lv = l0.y, le = l0.z;
     float acc[6] = {0, 0, 0, 0, 0, 0};
     reverse_chunks(a, k, ss, kx, dtf, idx, s0, s1, lx, lv, le, acc);
@@ -392,7 +395,13 @@ abp_status set_err(abp_ctx *ctx, abp_status st, const char *msg, cudaError_t e =
 using namespace abp;
 
 extern "C" abp_status abp_backward(abp_ctx *ctx, const double *dJ_dmean_v, double *grad) {
+    return abp_backward_windowed(ctx, dJ_dmean_v, grad, 0);
+}
+
+extern "C" abp_status abp_backward_windowed(abp_ctx *ctx, const double *dJ_dmean_v, double *grad, int64_t window) {
     if (!ctx) return ABP_EINVAL;
+    if (window < 0 || (window > 0 && (ctx->cfg.checkpoint_every <= 0 || window % ctx->cfg.checkpoint_every != 0)))
+        return set_err(ctx, ABP_EINVAL, "abp_backward_windowed: window must be a multiple of checkpoint_every");
     if (!grad) return set_err(ctx, ABP_EINVAL, "abp_backward: grad is NULL");
     if (!ctx->have_batch) return set_err(ctx, ABP_ESTATE, "abp_backward before abp_set_params");
     if (ctx->cfg.checkpoint_every <= 0)
@@ -496,7 +505,8 @@ extern "C" abp_status abp_backward(abp_ctx *ctx, const double *dJ_dmean_v, doubl
             if (e == cudaSuccess) e = cudaStreamWaitEvent(s, l1_done[seg & 1], 0);
             AdjArgs as = a;
             as.sub = sub[seg & 1];
-            adjoint_reverse_kernel<<<(unsigned)((int64_t)ctx->n_tiles * sub2), kRevThreads, 0, s>>>(as, sv, seg, sub2);
+            adjoint_reverse_kernel<<<(unsigned)((int64_t)ctx->n_tiles * sub2), kRevThreads, 0, s>>>(as, sv, seg, sub2,
+                                                                                                   window);
             if (e == cudaSuccess) e = cudaEventRecord(rev_done[seg & 1], s);
             ctx->launches += 2;
         }

@@ -87,3 +87,48 @@ def test_autograd_function(abp):
     mv.sum().backward()
     ref = oracle_grads(w)
     np.testing.assert_allclose(theta.grad.numpy(), ref, rtol=1e-3, atol=1e-3 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("window", [500, 1000])
+def test_windowed_adjoint_matches_oracle(abp, window):
+    # 2,000 steps: the FP32 and FP64 paths stay together, so the windowed derivatives must
+    # agree as the full ones do (1e-3 of the largest component)
+    sets = [W._with(D=0.05), W._with(D=0.2, q=2.0, asym=0.1)]
+    w = W.Workload(name="adj_win", sets=sets, n_traj=[512, 300], n_steps=[2000, 1800], dt=1e-3, seed=33, v0_mode=1,
+                   checkpoint_every=500)
+    with abp.Ensemble(w) as ens:
+        ens.run()
+        g = ens.backward(host=True, window=window).numpy()
+        full = ens.backward(host=True).numpy()
+        same = ens.backward(host=True, window=2000).numpy()
+    base = w.traj_base()
+    for i, p in enumerate(w.sets):
+        r = O.run_set(p, seed=w.seed, dt=w.dt, n_traj=w.n_traj[i], n_steps=w.n_steps[i], traj_base=base[i],
+                      v0_mode=w.v0_mode, want_grad=True, grad_window=window)
+        scale = np.max(np.abs(r["grad"]))
+        assert np.max(np.abs(g[i] - r["grad"])) <= 1e-3 * scale, (i, g[i], r["grad"])
+    np.testing.assert_array_equal(same, full)  # a window past the run is the full adjoint
+    for bad in (-1, 250, 777):
+        with pytest.raises(abp.AbpError):
+            with abp.Ensemble(w) as e2:
+                e2.run()
+                e2.backward(window=bad)
+
+
+def test_windowed_adjoint_long_horizon(abp):
+    # 8,000 steps (t = 8): chaos has separated some FP32 paths from their FP64 twins, so the
+    # two windowed estimates are compared within their statistical error (per-trajectory
+    # spread of the oracle's windowed tangents), and both stay bounded while the full pathwise
+    # derivative has grown by ~e^{0.46 t}
+    p = W._with(D=0.05)
+    w = W.Workload(name="adj_long", sets=[p], n_traj=[2048], n_steps=[8000], dt=1e-3, seed=34, v0_mode=1,
+                   checkpoint_every=500)
+    with abp.Ensemble(w) as ens:
+        ens.run()
+        g = ens.backward(host=True, window=1500).numpy()[0]
+        full = ens.backward(host=True).numpy()[0]
+    r = O.run_set(p, seed=w.seed, dt=w.dt, n_traj=2048, n_steps=8000, v0_mode=1, want_traj_grad=True,
+                  grad_window=1500)
+    se = r["dvbar"].std(axis=0, ddof=1) / np.sqrt(2048)
+    assert np.all(np.abs(g - r["grad"]) <= 3 * np.sqrt(2) * se + 1e-3 * np.max(np.abs(r["grad"]))), (g, r["grad"], se)
+    assert np.max(np.abs(g)) < 0.1 * np.max(np.abs(full))
