@@ -292,7 +292,7 @@ __device__ __forceinline__ void em_step_f32(const Coef<float> &k, float nrs, flo
 // the state once, as in em_step_f32.
 __device__ __forceinline__ void heun_step_f32(const Coef<float> &k, float nrs, float trig, float pb, float &yacc,
                                               float &v, float &e) {
-    const float sz = nrs * trig;
+    const float sz = __fmul_rn(nrs, trig);  // kept a product: the compiler may not fuse it into the sums below
     const float c0 = __cosf(phase_arg(pb, yacc));
     const float dv0 = fmaf(fmaf(k.A4, c0, k.K), c0, fmaf(fmaf(k.Bd, e, k.Gd), v, k.F));
     const float de0 = fmaf(e, fmaf(-k.Bd, v * v, k.Cm), k.Cq);
@@ -304,6 +304,92 @@ __device__ __forceinline__ void heun_step_f32(const Coef<float> &k, float nrs, f
     yacc = fmaf(v + vp, k.hdtL, yacc);  // (v + v~) dt / (2 L); halving is exact
     v = v + fmaf(0.5f, dv0 + dv1, sz);
     e = fmaf(0.5f, de0 + de1, e);
+}
+
+// --------------------------------------------------------------------------
+// Paired FP32 arithmetic.  sm_100-family GPUs have two-lane FP32 instructions
+// (__ffma2_rn, __fadd2_rn, __fmul2_rn): one instruction applies the same
+// operation to the two halves of a register pair, each half rounded exactly as
+// the scalar fmaf / + / * would round it.  A thread that holds two
+// trajectories steps them with these, so the FP32 part of a step takes half
+// the issue slots; the results are bitwise those of the scalar functions
+// above (tested: paired and unpaired launches give the same state).
+#ifndef ABP_F32X2
+#define ABP_F32X2 1
+#endif
+
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+
+// The coefficients of Coef<float> that the paired step reads, duplicated into
+// both halves of a pair.
+struct Coef2 {
+    float2 A, nBd, Bd, Cq, Gd, F, K, A4, dtL, bm, Cm, hdtL;
+};
+
+__device__ __forceinline__ Coef2 make_coef2(const Coef<float> &k) {
+    Coef2 c;
+    c.A = dup2(k.A);
+    c.nBd = dup2(-k.Bd);
+    c.Bd = dup2(k.Bd);
+    c.Cq = dup2(k.Cq);
+    c.Gd = dup2(k.Gd);
+    c.F = dup2(k.F);
+    c.K = dup2(k.K);
+    c.A4 = dup2(k.A4);
+    c.dtL = dup2(k.dtL);
+    c.bm = dup2(k.bm);
+    c.Cm = dup2(k.Cm);
+    c.hdtL = dup2(k.hdtL);
+    return c;
+}
+
+// box_muller_f32 of two word pairs (wa.x, wb.x) and (wa.y, wb.y), same
+// operations in the same order.
+__device__ __forceinline__ void box_muller_f32x2(uint2 wa, uint2 wb, float2 c2, float2 &nrs, float2 &cs,
+                                                 float2 &sn) {
+    const float2 u1 =
+        __ffma2_rn(make_float2(__uint2float_rn(wa.x), __uint2float_rn(wa.y)), dup2(0x1p-32f), dup2(0x1p-33f));
+    const float2 p = __fmul2_rn(make_float2(__log2f(u1.x), __log2f(u1.y)), c2);
+    nrs = make_float2(-sqrt_approx(fabsf(p.x)), -sqrt_approx(fabsf(p.y)));
+    const float2 f = make_float2(__uint_as_float(0x3f800000u | (wb.x >> 9)), __uint_as_float(0x3f800000u | (wb.y >> 9)));
+    const float2 ang = __ffma2_rn(f, dup2(kTwoPiF), dup2(-1.5f * kTwoPiF));
+    __sincosf(ang.x, &sn.x, &cs.x);
+    __sincosf(ang.y, &sn.y, &cs.y);
+}
+
+// em_step_f32 of two trajectories, same operations in the same order.
+__device__ __forceinline__ void em_step_f32x2(const Coef2 &k, float2 nrs, float2 trig, float2 pb, float2 &yacc,
+                                              float2 &v, float2 &e) {
+    const float2 ph = __ffma2_rn(yacc, dup2(kTwoPiF), pb);
+    const float2 cphi = make_float2(__cosf(ph.x), __cosf(ph.y));
+    const float2 t1 = __ffma2_rn(k.nBd, __fmul2_rn(v, v), k.A);
+    const float2 hv = __ffma2_rn(k.Bd, e, k.Gd);
+    const float2 a1 = __ffma2_rn(nrs, trig, k.F);
+    const float2 a2 = __ffma2_rn(hv, v, a1);
+    const float2 P = __ffma2_rn(k.A4, cphi, k.K);
+    const float2 dv = __ffma2_rn(P, cphi, a2);
+    yacc = __ffma2_rn(v, k.dtL, yacc);
+    e = __ffma2_rn(e, t1, k.Cq);
+    v = __fadd2_rn(v, dv);
+}
+
+// heun_step_f32 of two trajectories, same operations in the same order.
+__device__ __forceinline__ void heun_step_f32x2(const Coef2 &k, float2 nrs, float2 trig, float2 pb, float2 &yacc,
+                                                float2 &v, float2 &e) {
+    const float2 sz = __fmul2_rn(nrs, trig);
+    const float2 ph0 = __ffma2_rn(yacc, dup2(kTwoPiF), pb);
+    const float2 c0 = make_float2(__cosf(ph0.x), __cosf(ph0.y));
+    const float2 dv0 = __ffma2_rn(__ffma2_rn(k.A4, c0, k.K), c0, __ffma2_rn(__ffma2_rn(k.Bd, e, k.Gd), v, k.F));
+    const float2 de0 = __ffma2_rn(e, __ffma2_rn(k.nBd, __fmul2_rn(v, v), k.Cm), k.Cq);
+    const float2 vp = __fadd2_rn(v, __fadd2_rn(dv0, sz));
+    const float2 ep = __fadd2_rn(e, de0);
+    const float2 ph1 = __ffma2_rn(__ffma2_rn(v, k.dtL, yacc), dup2(kTwoPiF), pb);
+    const float2 c1 = make_float2(__cosf(ph1.x), __cosf(ph1.y));
+    const float2 dv1 = __ffma2_rn(__ffma2_rn(k.A4, c1, k.K), c1, __ffma2_rn(__ffma2_rn(k.Bd, ep, k.Gd), vp, k.F));
+    const float2 de1 = __ffma2_rn(ep, __ffma2_rn(k.nBd, __fmul2_rn(vp, vp), k.Cm), k.Cq);
+    yacc = __ffma2_rn(__fadd2_rn(v, vp), k.hdtL, yacc);
+    v = __fadd2_rn(v, __ffma2_rn(dup2(0.5f), __fadd2_rn(dv0, dv1), sz));
+    e = __ffma2_rn(dup2(0.5f), __fadd2_rn(de0, de1), e);
 }
 
 template <typename R>

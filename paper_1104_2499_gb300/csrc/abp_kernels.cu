@@ -199,12 +199,59 @@ __device__ __forceinline__ void step_f32(const Coef<float> &k, float nrs, float 
         em_step_f32(k, nrs, trig, pb, yacc, v, e);
 }
 
+// The paired FP32 step of the configured scheme (two trajectories).
+template <bool HEUN>
+__device__ __forceinline__ void step_f32x2(const Coef2 &k, float2 nrs, float2 trig, float2 pb, float2 &yacc,
+                                           float2 &v, float2 &e) {
+    if constexpr (HEUN)
+        heun_step_f32x2(k, nrs, trig, pb, yacc, v, e);
+    else
+        em_step_f32x2(k, nrs, trig, pb, yacc, v, e);
+}
+
+// Slots 2p and 2p + 1 as FP32 pairs, and back.
+template <int PPT>
+struct Pair {
+    float2 yacc, v, e, pb;
+    __device__ __forceinline__ Pair(const Slots<float, PPT> &S, int p)
+        : yacc(make_float2(S.yacc[p], S.yacc[p + 1])), v(make_float2(S.v[p], S.v[p + 1])),
+          e(make_float2(S.e[p], S.e[p + 1])), pb(make_float2(S.pb[p], S.pb[p + 1])) {}
+    __device__ __forceinline__ void store(Slots<float, PPT> &S, int p) const {
+        S.yacc[p] = yacc.x;
+        S.yacc[p + 1] = yacc.y;
+        S.v[p] = v.x;
+        S.v[p + 1] = v.y;
+        S.e[p] = e.x;
+        S.e[p + 1] = e.y;
+    }
+};
+
+// Whether the FP32 slots of a thread are stepped in pairs.
+template <typename R, int PPT>
+constexpr bool kPaired = sizeof(R) == 4 && PPT % 2 == 0 && ABP_F32X2 && ABP_ANGLE_FFMA;
+
 // One Euler-Maruyama step of every slot at an arbitrary step index n (the
 // unaligned head / tail of a range): the counter block of n is generated for
 // this step alone.
 template <typename R, int PPT, int MODE = kModeEM>
 __device__ __forceinline__ void single_step(const Coef<R> &k, const RoundKeys &K, Slots<R, PPT> &S, int64_t n) {
-    if constexpr (MODE == kModeXorshift) {
+    if constexpr (MODE == kModeXorshift && kPaired<R, PPT>) {
+        const Coef2 k2 = make_coef2(k);
+#pragma unroll
+        for (int p = 0; p < PPT; p += 2) {
+            Pair<PPT> P(S, p);
+            uint2 wa, wb;
+            wa.x = xorshift128(S.xs[p]);
+            wb.x = xorshift128(S.xs[p]);
+            wa.y = xorshift128(S.xs[p + 1]);
+            wb.y = xorshift128(S.xs[p + 1]);
+            float2 nrs, cs, sn;
+            box_muller_f32x2(wa, wb, k2.bm, nrs, cs, sn);
+            em_step_f32x2(k2, nrs, cs, P.pb, P.yacc, P.v, P.e);
+            P.store(S, p);
+        }
+        return;
+    } else if constexpr (MODE == kModeXorshift) {
 #pragma unroll
         for (int q = 0; q < PPT; ++q) {
             float nrs, cs, sn;
@@ -246,7 +293,22 @@ __device__ __forceinline__ void group_step(const Coef<R> &k, const RoundKeys &K,
     uint4 w[PPT];
 #pragma unroll
     for (int q = 0; q < PPT; ++q) w[q] = step_block(m, S.ss[q], K);
-    if constexpr (sizeof(R) == 4) {
+    if constexpr (kPaired<R, PPT>) {
+        // trajectories 2p and 2p + 1 in the two halves of FP32 register pairs
+        const Coef2 k2 = make_coef2(k);
+#pragma unroll
+        for (int p = 0; p < PPT; p += 2) {
+            Pair<PPT> P(S, p);
+            float2 nr, cs, sn;
+            box_muller_f32x2(make_uint2(w[p].x, w[p + 1].x), make_uint2(w[p].y, w[p + 1].y), k2.bm, nr, cs, sn);
+            step_f32x2<HEUN>(k2, nr, cs, P.pb, P.yacc, P.v, P.e);
+            step_f32x2<HEUN>(k2, nr, sn, P.pb, P.yacc, P.v, P.e);
+            box_muller_f32x2(make_uint2(w[p].z, w[p + 1].z), make_uint2(w[p].w, w[p + 1].w), k2.bm, nr, cs, sn);
+            step_f32x2<HEUN>(k2, nr, cs, P.pb, P.yacc, P.v, P.e);
+            step_f32x2<HEUN>(k2, nr, sn, P.pb, P.yacc, P.v, P.e);
+            P.store(S, p);
+        }
+    } else if constexpr (sizeof(R) == 4) {
         float nr[PPT], cs[PPT], sn[PPT];
 #pragma unroll
         for (int q = 0; q < PPT; ++q) box_muller_f32(w[q].x, w[q].y, k.bm, nr[q], cs[q], sn[q]);
