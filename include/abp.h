@@ -107,7 +107,8 @@ typedef struct {
                                     (schedule, particles_per_thread) pair once per device and
                                     library build (table kept beside the library) and predicts
                                     each pair's time on the batch of abp_set_params from the busy
-                                    fraction of its resident blocks */
+                                    fraction of its resident blocks; the work queue must beat
+                                    lockstep by more than 2% to be chosen */
     int64_t steps_per_launch;    /* lockstep: steps per launch; work queue: steps per work item
                                     (round); 0 = chosen automatically */
     uint64_t traj_base;          /* added to every global trajectory id: a process that runs
@@ -256,7 +257,8 @@ ABP_API abp_status abp_test_hold_tile(abp_ctx *ctx, int32_t tile);
 
 /* The autotuner's choices for the current batch (host outputs, any may be NULL):
  * schedule (1 lockstep, 2 work queue), particles per thread, steps per launch
- * (lockstep) or per work item (work queue), resident blocks of the work queue. */
+ * (lockstep) or per work item (work queue), and the blocks of the chosen schedule's
+ * integrator kernel resident on the GPU at once (the work queue's grid). */
 ABP_API abp_status abp_tuning(const abp_ctx *ctx, int32_t *schedule, int32_t *particles_per_thread,
                               int64_t *steps_per_item, int32_t *blocks);
 

@@ -492,6 +492,12 @@ bool plan_tiles(int32_t n_sets, const int64_t *n_traj, const int64_t *n_steps, i
 // Sets ctx->sched and ctx->ppt from the configuration, the timing table and
 // the batch: each allowed candidate's trial time divided by the fraction of
 // its capacity this batch keeps busy; the smallest prediction wins.
+// The work queue is chosen only when predicted faster than lockstep by more
+// than this fraction (about the run-to-run spread of the trial): between
+// near-equal candidates the lockstep schedule, which has no device-side waits,
+// is kept, and the choice stays the same from one machine to the next.
+constexpr double kQueueMargin = 0.02;
+
 void autotune(abp_ctx *ctx) {
     const int want_sched = ctx->cfg.schedule;          // 0 auto, 1 lockstep, 2 work queue
     const int want_ppt = ctx->cfg.particles_per_thread;  // 0 auto
@@ -526,7 +532,8 @@ void autotune(abp_ctx *ctx) {
             const int64_t spl = c.steps_per_launch > 0 ? c.steps_per_launch : default_steps_per_launch(ctx);
             const double pred = (double)tt.ms[sch][ci] / batch_efficiency(ctx->n_sets, ctx->n_traj.data(),
                                                                           ctx->n_steps.data(), sch, cands[ci],
-                                                                          c.checkpoint_every > 0, spl, cap);
+                                                                          c.checkpoint_every > 0, spl, cap) *
+                                (sch == 2 ? 1.0 + kQueueMargin : 1.0);
             if (pred < best) {
                 best = pred;
                 bs = sch;
@@ -1130,7 +1137,20 @@ abp_status abp_tuning(const abp_ctx *ctx, int32_t *schedule, int32_t *particles_
     if (schedule) *schedule = ctx->sched;
     if (particles_per_thread) *particles_per_thread = ctx->ppt;
     if (steps_per_item) *steps_per_item = ctx->steps_per_launch;
-    if (blocks) *blocks = ctx->grid;
+    if (blocks) {
+        *blocks = ctx->grid;
+        if (ctx->sched == 1) {  // lockstep: the blocks of the integrator resident at once
+            const abp_config &c = ctx->cfg;
+            const size_t smem =
+                sizeof(uint32_t) * (size_t)(std::max(c.hist_x_bins, 0) + (c.hist_v_bins > 0 ? c.hist_v_bins + 2 : 0));
+            int bps = 0;
+            if (integrate_occupancy(c.state_fp64 != 0, ctx->ppt, smem, &bps, c.scheme == 1 ? 1 : c.noise == 1 ? 2 : 0) ==
+                cudaSuccess)
+                *blocks = bps * std::max(ctx->sm_count, 1);
+            else
+                cudaGetLastError();
+        }
+    }
     return ABP_OK;
 }
 

@@ -336,9 +336,35 @@ __device__ __forceinline__ void group_step(const Coef<R> &k, const RoundKeys &K,
     }
 }
 
+// Counter blocks per iteration of the inner loop, per kernel (measured on the
+// D x q sweep): the FP32 Euler-Maruyama kernels with two trajectories per
+// thread run fastest with 8 blocks (32 steps) per iteration, lockstep 1.038e12
+// against 1.011e12 particle-steps/s with 2 and 0.98e12 with 12 (a body that no
+// longer fits the instruction cache), the work queue 1.023e12 against
+// 1.002e12; the other kernels keep the default, where longer bodies cost
+// registers and blocks per SM without a measured gain.
+#ifndef ABP_UNROLL_EM2
+#define ABP_UNROLL_EM2 8
+#endif
+#ifndef ABP_UNROLL_EM2_QUEUE
+#define ABP_UNROLL_EM2_QUEUE 8
+#endif
+#ifndef ABP_UNROLL_HEUN2
+#define ABP_UNROLL_HEUN2 kGroupUnroll
+#endif
+template <typename R, int PPT, int MODE, bool QUEUE>
+constexpr int group_unroll() {
+    if constexpr (sizeof(R) == 4 && PPT == 2 && MODE == kModeEM)
+        return QUEUE ? ABP_UNROLL_EM2_QUEUE : ABP_UNROLL_EM2;
+    else if constexpr (sizeof(R) == 4 && PPT == 2 && MODE == kModeHeun)
+        return ABP_UNROLL_HEUN2;
+    else
+        return kGroupUnroll;
+}
+
 // Steps [n, n_end) of every slot.  Folds happen after absolute multiples of
 // kBlockSteps steps; counter blocks are absolute multiples of 4.
-template <typename R, int PPT, int MODE = kModeEM>
+template <typename R, int PPT, int MODE = kModeEM, int UNROLL = kGroupUnroll>
 __device__ __forceinline__ void advance(const Coef<R> &k, const RoundKeys &K, Slots<R, PPT> &S, int64_t n,
                                         int64_t n_end) {
     while (n < n_end) {
@@ -350,7 +376,7 @@ __device__ __forceinline__ void advance(const Coef<R> &k, const RoundKeys &K, Sl
         if (n < blk_end) {
             const uint32_t m_end = (uint32_t)(blk_end >> 2);
             uint32_t m = (uint32_t)(n >> 2);
-#pragma unroll kGroupUnroll
+#pragma unroll UNROLL
             for (; m < m_end; ++m) group_step<R, PPT, MODE>(k, K, S, m);
             n = (int64_t)m << 2;
         }
@@ -376,7 +402,7 @@ __device__ __forceinline__ void advance(const Coef<R> &k, const RoundKeys &K, Sl
 // PACKED: a packed tile (several sets of equal step count, PPT 1): each thread
 // takes the coefficients of its own trajectory's set, and histograms go to
 // global memory directly.
-template <typename R, int PPT, bool PACKED = false, int MODE = kModeEM>
+template <typename R, int PPT, bool PACKED = false, int MODE = kModeEM, int UNROLL = kGroupUnroll>
 __device__ __forceinline__ void run_tile(const Batch &b, const State &st, const Hist &h, const Ckpt &ck,
                                          const Noise &nz, const RoundKeys &K, uint32_t *sh, int tile, int64_t w0,
                                          int64_t w1, int lane_base = 0) {
@@ -434,7 +460,7 @@ __device__ __forceinline__ void run_tile(const Batch &b, const State &st, const 
         int64_t seg_end = n_end;
         if (hist && h.snap_every > 0) seg_end = min(seg_end, (n / h.snap_every + 1) * h.snap_every);
         if (ck.every > 0) seg_end = min(seg_end, (n / ck.every + 1) * ck.every);
-        if (warp_live) advance<R, PPT, MODE>(k, K, S, n, seg_end);
+        if (warp_live) advance<R, PPT, MODE, UNROLL>(k, K, S, n, seg_end);
         n = seg_end;
         if (hist && (h.snap_every > 0 ? (n % h.snap_every == 0) : (n == N))) {
             const int64_t snap = h.snap_every > 0 ? n / h.snap_every - 1 : 0;
@@ -497,7 +523,8 @@ __global__ void ABP_INTEGRATE_BOUNDS integrate_kernel(Batch b, State st, Hist h,
     const int sub = b.narrow ? (PACKED ? b.sub_packed : b.sub_single) : 1;
     const int tile = (PACKED ? b.n_single : 0) + (int)blockIdx.x / sub;
     const int lane_base = ((int)blockIdx.x % sub) * (int)blockDim.x;
-    run_tile<R, PPT, PACKED, MODE>(b, st, h, ck, nz, kp.K, sh, tile, g0, g1, lane_base);
+    run_tile<R, PPT, PACKED, MODE, group_unroll<R, PPT, MODE, false>()>(b, st, h, ck, nz, kp.K, sh, tile, g0, g1,
+                                                                       lane_base);
 }
 
 __device__ __forceinline__ uint64_t global_ns() {
@@ -568,7 +595,8 @@ __global__ void ABP_INTEGRATE_BOUNDS persistent_kernel(Batch b, State st, Hist h
         if (s_tile < 0) break;
         {
             const int64_t w0 = g0 + (int64_t)s_round * seg;
-            run_tile<R, PPT, false, MODE>(b, st, h, ck, nz, kp.K, sh, s_tile, w0, min(w0 + seg, g1));
+            run_tile<R, PPT, false, MODE, group_unroll<R, PPT, MODE, true>()>(b, st, h, ck, nz, kp.K, sh, s_tile, w0,
+                                                                              min(w0 + seg, g1));
         }
         __syncthreads();  // every thread's state stores precede the publication
         if (threadIdx.x == 0 && s_tile != q.hold_tile) {
