@@ -243,15 +243,19 @@ ABP_API abp_status abp_backward(abp_ctx *ctx, const double *dJ_dmean_v, double *
  * length gives abp_backward's result. */
 ABP_API abp_status abp_backward_windowed(abp_ctx *ctx, const double *dJ_dmean_v, double *grad, int64_t window);
 
-/* Upper bound, in nanoseconds, of every device-side wait of the work-queue
- * schedule (schedule 2) (a work item waiting for the previous round of its tile); 0 restores
- * the default of 60 s.  An expired wait ends the launch with ABP_ETIMEOUT
+/* Upper bound, in nanoseconds, of every device-side wait: in the work-queue
+ * schedule (schedule 2) a work item waiting for the previous round of its tile,
+ * in a warp-specialised narrow lockstep launch (a batch with fewer tiles than
+ * SMs) a warp waiting for its partner's noise or slot; 0 restores the default
+ * of 60 s.  An expired wait ends the launch with ABP_ETIMEOUT
  * (reported by abp_synchronize); the context stays usable after abp_reset. */
 ABP_API abp_status abp_set_wait_limit(abp_ctx *ctx, int64_t wait_limit_ns);
 
 /* Test hook for failure detection: tile `tile` (index in the tile table, -1 to
  * clear) never publishes the completion of its rounds in later work-queue
- * launches, so the items that depend on it wait until the wait limit expires.
+ * launches, so the items that depend on it wait until the wait limit expires;
+ * in warp-specialised narrow lockstep launches its producer warps never hand
+ * their noise over, so its stepping warps wait until the limit expires.
  * Nothing faults or hangs: the launch ends and reports ABP_ETIMEOUT. */
 ABP_API abp_status abp_test_hold_tile(abp_ctx *ctx, int32_t tile);
 

@@ -842,7 +842,9 @@ cudaError_t enqueue_window(abp_ctx *ctx, int64_t g0, int64_t g1, const int32_t *
     *kernels = 0;
     if (ctx->sched == 1) {
         for (int64_t g = g0; g < g1; g += ctx->steps_per_launch) {
-            cudaError_t e = launch_integrate(b, st, h, c, nz, ctx->ppt, g, std::min(g1, g + ctx->steps_per_launch), s);
+            const WaitCtl wc{(int32_t *)ctx->d_status.p, ctx->wait_limit_ns, ctx->hold_tile};
+            cudaError_t e =
+                launch_integrate(b, st, h, c, nz, ctx->ppt, g, std::min(g1, g + ctx->steps_per_launch), s, &wc);
             if (e != cudaSuccess) return e;
             *kernels += (b.n_single > 0 ? 1 : 0) + (b.n_tiles > b.n_single ? 1 : 0);
         }

@@ -101,8 +101,16 @@ struct Queue {
 
 cudaError_t launch_init(const Batch &b, const State &s, const Hist &h, const Ckpt &c, const Noise &nz,
                         cudaStream_t st);
+// Device-side waits of a lockstep launch (the warp-specialised narrow form):
+// the context's status word, the wait limit and the test hook's held tile.
+struct WaitCtl {
+    int32_t *status;
+    int64_t limit_ns;
+    int32_t hold_tile;  // test hook: this tile's producer warps never hand over noise (-1: none)
+};
+
 cudaError_t launch_integrate(const Batch &b, const State &s, const Hist &h, const Ckpt &c, const Noise &nz,
-                             int ppt, int64_t g0, int64_t g1, cudaStream_t st);
+                             int ppt, int64_t g0, int64_t g1, cudaStream_t st, const WaitCtl *wait = nullptr);
 // partials: [n_tiles][4] scratch; moments: [n_sets][8].
 cudaError_t launch_reduce(const Batch &b, const State &s, const Noise &nz, int64_t g, double *partials,
                           double *moments, cudaStream_t st);

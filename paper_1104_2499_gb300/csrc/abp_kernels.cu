@@ -24,6 +24,11 @@
 #ifndef ABP_GROUP_UNROLL
 #define ABP_GROUP_UNROLL 2
 #endif
+// Warp-specialised narrow launches (noise drawn by producer warps); 0 keeps
+// every narrow launch on the plain integrator.
+#ifndef ABP_WS
+#define ABP_WS 1
+#endif
 #ifndef ABP_MIN_BLOCKS
 #define ABP_MIN_BLOCKS 0
 #endif
@@ -89,12 +94,26 @@ __device__ __forceinline__ int bin_v(R v, R v_lo, R v_hi, R scale, int bv) {
     return b < bv ? b : bv - 1;
 }
 
+// Barrier over the threads that step trajectories: the whole block, or in a
+// warp-specialised block (WS) its first `n` threads, on hardware barrier 1.
+template <bool WS>
+__device__ __forceinline__ void stepper_barrier(int n) {
+    if constexpr (WS)
+        asm volatile("bar.sync 1, %0;" ::"r"(n) : "memory");
+    else
+        __syncthreads();
+}
+
 // Add the block's counts to the global histogram of (snap, set) and clear
-// the shared copy.  Must be reached by every thread of the block.
-__device__ __forceinline__ void flush_hist(uint32_t *sh, const Hist &h, int64_t snap, int32_t set, int32_t n_sets) {
-    __syncthreads();
+// the shared copy.  Must be reached by every stepping thread of the block
+// (`n` of them: blockDim.x, or the consumer threads of a WS block).
+template <bool WS = false>
+__device__ __forceinline__ void flush_hist(uint32_t *sh, const Hist &h, int64_t snap, int32_t set, int32_t n_sets,
+                                           int n = 0) {
+    if constexpr (!WS) n = blockDim.x;
+    stepper_barrier<WS>(n);
     const int nb = h.bx + (h.bv > 0 ? h.bv + 2 : 0);
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    for (int i = threadIdx.x; i < nb; i += n) {
         const uint32_t c = sh[i];
         if (c) {
             if (i < h.bx)
@@ -104,7 +123,7 @@ __device__ __forceinline__ void flush_hist(uint32_t *sh, const Hist &h, int64_t 
         }
         sh[i] = 0;
     }
-    __syncthreads();
+    stepper_barrier<WS>(n);
 }
 
 // ---------------------------------------------------------------- init
@@ -169,6 +188,13 @@ __global__ void __launch_bounds__(kThreads) init_kernel(Batch b, State st, Hist 
 }
 
 // ---------------------------------------------------------------- integrator
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 
 template <typename R, int PPT>
 struct Slots {
@@ -394,6 +420,123 @@ __device__ __forceinline__ void advance(const Coef<R> &k, const RoundKeys &K, Sl
     }
 }
 
+// ------------------------------------------- warp-specialised narrow launch
+// A narrow launch has at most one warp per scheduler, so a warp steps alone and
+// its time per step is the latency of its own instruction chain: the counter
+// block and Box-Muller of four steps, then four dependent state updates.  In
+// the warp-specialised form every consumer warp (its trajectories stepped as
+// in run_tile) has a producer warp that draws the same (nrs, trig) pairs for
+// the same steps ahead into a shared-memory ring; the consumer's chain is the
+// state update alone.  The ring holds kWsSlots slots of kWsSlotSteps steps per
+// warp pair; slot j of a launch holds absolute steps [j S, (j + 1) S), so a
+// slot never straddles a position fold.  Producer and consumer hand slots over
+// through mbarriers (32 arrivals: the lanes of the warp).  Every wait is
+// bounded: past the wait limit the thread records status 1 and stops waiting,
+// so the launch runs to its end and the host reports the timeout.
+constexpr int kWsSlotSteps = 16;
+constexpr int kWsSlots = 4;
+// Stepping threads per block at most: only a narrow launch of 32-thread blocks
+// (fewer than two stepping warps per SM) is latency-bound enough to gain.
+// Measured on the work-items sweep (10^4 steps per cycle): 0.30 against 0.42 ms
+// per cycle up to 2^13 items (32 threads), but 0.433 against 0.425 at 2^14 (64)
+// and 0.593 against 0.549 at 2^15 (128), where several stepping warps share a
+// scheduler and the producers' instructions cost more than the chain saves.
+constexpr int kWsMaxWidth = 32;
+constexpr int kWsMaxPairs = kWsMaxWidth / 32;
+static_assert(kBlockSteps % kWsSlotSteps == 0 && kWsSlotSteps % 4 == 0, "slots hold whole counter blocks");
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+struct WsRing {
+    float2 *buf;       // [pairs][kWsSlots][kWsSlotSteps][32] (nrs, trig) per lane and step
+    uint64_t *full;    // [pairs][kWsSlots]: slot written by the producer warp
+    uint64_t *empty;   // [pairs][kWsSlots]: slot read by the consumer warp
+    int32_t *status;   // 1 once a wait gave up
+    int64_t limit_ns;
+    int32_t hold_tile; // test hook: the producers of this tile never hand a slot over
+};
+
+// Wait for the completion of phase `parity` of `bar`, at most limit_ns; after
+// a failure (here or in another thread) the thread no longer waits.
+__device__ __forceinline__ void ws_wait(uint64_t *bar, uint32_t parity, const WsRing &r, bool &failed) {
+    if (failed || mbar_try_wait(bar, parity)) return;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return;
+        if (*(volatile int32_t *)r.status != 0 || global_ns() - t0 > (uint64_t)r.limit_ns) {
+            atomicCAS(r.status, 0, 1);
+            failed = true;
+            return;
+        }
+    }
+}
+
+// Consumer side of one warp pair: the slot held (absolute slot index) and the
+// first slot of the launch.
+struct WsCons {
+    WsRing r;
+    int pair;
+    int64_t a0, held;
+    bool failed;
+};
+
+// advance() with the noise taken from the ring (FP32, one trajectory per
+// thread, counter-based noise).
+template <bool HEUN>
+__device__ __forceinline__ void advance_ws(const Coef<float> &k, Slots<float, 1> &S, int64_t n, int64_t n_end,
+                                           WsCons &c) {
+    constexpr int SS = kWsSlotSteps;
+    const int lane = threadIdx.x & 31;
+    while (n < n_end) {
+        const int64_t a = n / SS;
+        const int64_t kf = a - c.a0;
+        const int slot = (int)(kf % kWsSlots);
+        if (a != c.held) {
+            if (c.held >= 0) mbar_arrive(&c.r.empty[c.pair * kWsSlots + (int)((c.held - c.a0) % kWsSlots)]);
+            ws_wait(&c.r.full[c.pair * kWsSlots + slot], (uint32_t)((kf / kWsSlots) & 1), c.r, c.failed);
+            c.held = a;
+        }
+        const float2 *ring = c.r.buf + ((size_t)(c.pair * kWsSlots + slot) * SS) * 32 + lane;
+        const int64_t a_end = min(n_end, (a + 1) * SS);
+        if (n == a * SS && a_end == (a + 1) * SS) {
+#pragma unroll
+            for (int i = 0; i < SS; ++i) {
+                const float2 t = ring[i * 32];
+                step_f32<HEUN>(k, t.x, t.y, S.pb[0], S.yacc[0], S.v[0], S.e[0]);
+            }
+        } else {
+            // a fold can fall only on a slot's end (slots tile the 64-step blocks)
+            for (; n < a_end; ++n) {
+                const float2 t = ring[(int)(n - a * SS) * 32];
+                step_f32<HEUN>(k, t.x, t.y, S.pb[0], S.yacc[0], S.v[0], S.e[0]);
+            }
+        }
+        n = a_end;
+        if ((n & (kBlockSteps - 1)) == 0) {
+            fold_position<float>(S.y[0], S.yacc[0], S.ylo[0], S.cell[0]);
+            S.pb[0] = phase_base(S.y[0]);
+        }
+    }
+}
+
 // Steps [max(w0, 0), w1) ∩ [0, N) of every trajectory of one tile: load the
 // state (through L2, so a tile continued by another block sees its latest
 // state), step it in registers, fill snapshot histograms and checkpoints, and
@@ -402,11 +545,14 @@ __device__ __forceinline__ void advance(const Coef<R> &k, const RoundKeys &K, Sl
 // PACKED: a packed tile (several sets of equal step count, PPT 1): each thread
 // takes the coefficients of its own trajectory's set, and histograms go to
 // global memory directly.
-template <typename R, int PPT, bool PACKED = false, int MODE = kModeEM, int UNROLL = kGroupUnroll>
+// WS: the consumer threads of a warp-specialised block (noise from the ring
+// of `wc`, histogram flushes on the consumers' own barrier).
+template <typename R, int PPT, bool PACKED = false, int MODE = kModeEM, int UNROLL = kGroupUnroll, bool WS = false>
 __device__ __forceinline__ void run_tile(const Batch &b, const State &st, const Hist &h, const Ckpt &ck,
                                          const Noise &nz, const RoundKeys &K, uint32_t *sh, int tile, int64_t w0,
-                                         int64_t w1, int lane_base = 0) {
+                                         int64_t w1, int lane_base = 0, WsCons *wc = nullptr) {
     static_assert(!PACKED || PPT == 1, "packed tiles hold one trajectory per thread");
+    static_assert(!WS || (sizeof(R) == 4 && PPT == 1 && MODE != kModeXorshift), "WS: FP32, PPT 1, counter noise");
     const int64_t first = b.tile_first[tile];
     const int count = b.tile_count[tile];
     const int set_t = b.tile_set[tile];
@@ -455,12 +601,20 @@ __device__ __forceinline__ void run_tile(const Batch &b, const State &st, const 
     for (int q = 0; q < PPT; ++q) any_act |= act[q];
     const bool warp_live = __any_sync(0xffffffffu, any_act);
 
+    if constexpr (WS) {
+        wc->a0 = n_begin / kWsSlotSteps;
+        wc->held = -1;
+    }
     int64_t n = n_begin;
     while (n < n_end) {
         int64_t seg_end = n_end;
         if (hist && h.snap_every > 0) seg_end = min(seg_end, (n / h.snap_every + 1) * h.snap_every);
         if (ck.every > 0) seg_end = min(seg_end, (n / ck.every + 1) * ck.every);
-        if (warp_live) advance<R, PPT, MODE, UNROLL>(k, K, S, n, seg_end);
+        if constexpr (WS) {
+            if (warp_live) advance_ws<MODE == kModeHeun>(k, S, n, seg_end, *wc);
+        } else {
+            if (warp_live) advance<R, PPT, MODE, UNROLL>(k, K, S, n, seg_end);
+        }
         n = seg_end;
         if (hist && (h.snap_every > 0 ? (n % h.snap_every == 0) : (n == N))) {
             const int64_t snap = h.snap_every > 0 ? n / h.snap_every - 1 : 0;
@@ -478,7 +632,7 @@ __device__ __forceinline__ void run_tile(const Batch &b, const State &st, const 
                     if (h.bx > 0) atomicAdd(&sh[bin_x<R>(S.y[q] + S.yacc[q], h.bx)], 1u);
                     if (h.bv > 0) atomicAdd(&sh[h.bx + bin_v<R>(S.v[q], v_lo, v_hi, v_scale, h.bv)], 1u);
                 }
-                flush_hist(sh, h, snap, set, b.n_sets);
+                flush_hist<WS>(sh, h, snap, set, b.n_sets, (int)blockDim.x / 2);
             }
         }
         if (ck.every > 0 && n % ck.every == 0 && sizeof(R) == 4) {
@@ -527,10 +681,88 @@ __global__ void ABP_INTEGRATE_BOUNDS integrate_kernel(Batch b, State st, Hist h,
                                                                        lane_base);
 }
 
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
+// Producer side of one warp pair: the (nrs, trig) pairs of every step of the
+// launch's slots for the trajectories of consumer threads ci (lane by lane), in
+// slot order, each slot reused only after its consumer released it.  The
+// values are those single_step / group_step compute: same counter blocks, same
+// Box-Muller, same coefficient.
+template <bool PACKED>
+__device__ __forceinline__ void ws_produce(const Batch &b, const Noise &nz, const RoundKeys &K, const WsRing &r,
+                                           int tile, int64_t w0, int64_t w1, int lane_base, int pair, int ci) {
+    constexpr int SS = kWsSlotSteps;
+    const int64_t first = b.tile_first[tile];
+    const int count = b.tile_count[tile];
+    const int set_t = b.tile_set[tile];
+    const int64_t N = b.set_steps[set_t];
+    const int64_t n_begin = min(w0, N), n_end = min(w1, N);
+    if (n_begin >= n_end) return;  // uniform over the block, as for the consumers
+    const int li = lane_base + ci;
+    const bool act = li < count;
+    const int64_t idx = first + (act ? li : count - 1);
+    if (!__any_sync(0xffffffffu, act)) return;  // the consumer warp does not step either
+    if (tile == r.hold_tile) return;            // test hook: the consumers' waits run out
+    const int set = PACKED ? find_set(b, first + min(li, count - 1)) : set_t;
+    const abp_params p = b.params[set];
+    const Coef<float> k = make_coef<float>(p.q, p.c, p.d, p.gamma0, p.F0, p.D, p.h, p.L, p.asym, nz.dt);
+    const StepStream ss = step_stream((uint64_t)idx + nz.traj_base, K);
+    const int lane = threadIdx.x & 31;
+    const int64_t a0 = n_begin / SS, a1 = (n_end - 1) / SS;
+    bool failed = false;
+    for (int64_t a = a0; a <= a1; ++a) {
+        const int64_t kf = a - a0;
+        const int slot = (int)(kf % kWsSlots);
+        if (kf >= kWsSlots) ws_wait(&r.empty[pair * kWsSlots + slot], (uint32_t)((kf / kWsSlots - 1) & 1), r, failed);
+        float2 *out = r.buf + ((size_t)(pair * kWsSlots + slot) * SS) * 32 + lane;
+#pragma unroll
+        for (int j = 0; j < SS / 4; ++j) {
+            const uint4 wv = step_block((uint32_t)(a * (SS / 4) + j), ss, K);
+            float nr, cs, sn;
+            box_muller_f32(wv.x, wv.y, k.bm, nr, cs, sn);
+            out[(4 * j) * 32] = make_float2(nr, cs);
+            out[(4 * j + 1) * 32] = make_float2(nr, sn);
+            box_muller_f32(wv.z, wv.w, k.bm, nr, cs, sn);
+            out[(4 * j + 2) * 32] = make_float2(nr, cs);
+            out[(4 * j + 3) * 32] = make_float2(nr, sn);
+        }
+        mbar_arrive(&r.full[pair * kWsSlots + slot]);
+    }
+}
+
+// Warp-specialised narrow lockstep launch (FP32, counter-based noise): blocks
+// of 2 w threads over the w trajectories a narrow block of w threads takes
+// (sub blocks per tile); threads [0, w) step them (run_tile), threads [w, 2 w)
+// produce their noise.  Dynamic shared memory: the histogram bins (one-set
+// tiles), then the ring at the next 16-byte boundary.
+template <bool PACKED, int MODE>
+__global__ void __launch_bounds__(2 * kWsMaxWidth) ws_kernel(Batch b, State st, Hist h, Ckpt ck, Noise nz,
+                                                            KeyParam kp, int64_t g0, int64_t g1, WaitCtl wait) {
+    extern __shared__ uint32_t sh[];
+    __shared__ uint64_t full[kWsMaxPairs * kWsSlots], empty[kWsMaxPairs * kWsSlots];
+    const int w = (int)blockDim.x / 2;
+    const int pairs = w / 32;
+    if ((int)threadIdx.x < pairs * kWsSlots) {
+        mbar_init(&full[threadIdx.x], 32);
+        mbar_init(&empty[threadIdx.x], 32);
+    }
+    if constexpr (!PACKED) zero_hist(sh, h);
+    __syncthreads();
+    const int nb = PACKED ? 0 : h.bx + (h.bv > 0 ? h.bv + 2 : 0);
+    float2 *ring = (float2 *)(sh + ((nb + 3) & ~3));
+    if (smem_addr(ring) & 15) {  // uniform; never expected (dynamic shared memory is 16-byte aligned)
+        if (threadIdx.x == 0) atomicCAS(wait.status, 0, 2);
+        return;
+    }
+    const WsRing r{ring, full, empty, wait.status, wait.limit_ns, wait.hold_tile};
+    const int sub = PACKED ? b.sub_packed : b.sub_single;
+    const int tile = (PACKED ? b.n_single : 0) + (int)blockIdx.x / sub;
+    const int lane_base = ((int)blockIdx.x % sub) * w;
+    if ((int)threadIdx.x < w) {
+        WsCons c{r, (int)threadIdx.x >> 5, 0, -1, false};
+        run_tile<float, 1, PACKED, MODE, kGroupUnroll, true>(b, st, h, ck, nz, kp.K, sh, tile, g0, g1, lane_base, &c);
+    } else {
+        const int ci = (int)threadIdx.x - w;
+        ws_produce<PACKED>(b, nz, kp.K, r, tile, g0, g1, lane_base, ci >> 5, ci);
+    }
 }
 
 __device__ __forceinline__ int load_acquire(const int32_t *p) {
@@ -839,14 +1071,47 @@ cudaError_t launch_persistent_t(const Batch &b, const State &s, const Hist &h, c
     return cudaGetLastError();
 }
 
+// Warp-specialised form of a narrow launch (see ws_kernel).
+template <int MODE>
+cudaError_t launch_ws(const Batch &b, const State &s, const Hist &h, const Ckpt &c, const Noise &nz, int64_t g0,
+                      int64_t g1, const WaitCtl &wait, cudaStream_t st) {
+    const int w = b.narrow;
+    const size_t ring = sizeof(float2) * (size_t)(w / 32) * kWsSlots * kWsSlotSteps * 32;
+    const size_t hist = (hist_smem(h) + 15) & ~(size_t)15;
+    const KeyParam kp = key_param(nz.k0, nz.k1);
+    if (b.n_single > 0) {
+        auto kern = ws_kernel<false, MODE>;
+        const size_t smem = hist + ring;
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        kern<<<(unsigned)(b.n_single * b.sub_single), 2 * w, smem, st>>>(b, s, h, c, nz, kp, g0, g1, wait);
+    }
+    if (b.n_tiles > b.n_single) {
+        auto kern = ws_kernel<true, MODE>;
+        if (ring > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring);
+            if (e != cudaSuccess) return e;
+        }
+        kern<<<(unsigned)((b.n_tiles - b.n_single) * b.sub_packed), 2 * w, ring, st>>>(b, s, h, c, nz, kp, g0, g1,
+                                                                                        wait);
+    }
+    return cudaGetLastError();
+}
+
 template <typename R, int PPT, int MODE = kModeEM>
 cudaError_t launch_integrate_t(const Batch &b, const State &s, const Hist &h, const Ckpt &c, const Noise &nz,
-                               int64_t g0, int64_t g1, cudaStream_t st) {
+                               int64_t g0, int64_t g1, cudaStream_t st, const WaitCtl *wait = nullptr) {
     const size_t smem = hist_smem(h);
     auto kern = integrate_kernel<R, PPT, false, MODE>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
+    }
+    if constexpr (sizeof(R) == 4 && PPT == 1 && MODE != kModeXorshift && ABP_WS) {
+        if (b.narrow > 0 && b.narrow <= kWsMaxWidth && wait && wait->status)
+            return launch_ws<MODE>(b, s, h, c, nz, g0, g1, *wait, st);
     }
     const int threads = b.narrow ? b.narrow : kThreads;
     const int64_t sub_s = b.narrow ? b.sub_single : 1, sub_p = b.narrow ? b.sub_packed : 1;
@@ -879,7 +1144,7 @@ cudaError_t launch_init(const Batch &b, const State &s, const Hist &h, const Ckp
 }
 
 cudaError_t launch_integrate(const Batch &b, const State &s, const Hist &h, const Ckpt &c, const Noise &nz, int ppt,
-                             int64_t g0, int64_t g1, cudaStream_t st) {
+                             int64_t g0, int64_t g1, cudaStream_t st, const WaitCtl *wait) {
     if (b.n_tiles == 0 || g1 <= g0) return cudaSuccess;
     if (b.narrow) ppt = 1;
     if (s.fp64) {
@@ -890,7 +1155,7 @@ cudaError_t launch_integrate(const Batch &b, const State &s, const Hist &h, cons
         }
     } else if (nz.scheme == 1) {
         switch (ppt) {
-            case 1: return launch_integrate_t<float, 1, kModeHeun>(b, s, h, c, nz, g0, g1, st);
+            case 1: return launch_integrate_t<float, 1, kModeHeun>(b, s, h, c, nz, g0, g1, st, wait);
             case 2: return launch_integrate_t<float, 2, kModeHeun>(b, s, h, c, nz, g0, g1, st);
             case 4: return launch_integrate_t<float, 4, kModeHeun>(b, s, h, c, nz, g0, g1, st);
         }
@@ -902,7 +1167,7 @@ cudaError_t launch_integrate(const Batch &b, const State &s, const Hist &h, cons
         }
     } else {
         switch (ppt) {
-            case 1: return launch_integrate_t<float, 1>(b, s, h, c, nz, g0, g1, st);
+            case 1: return launch_integrate_t<float, 1>(b, s, h, c, nz, g0, g1, st, wait);
             case 2: return launch_integrate_t<float, 2>(b, s, h, c, nz, g0, g1, st);
             case 4: return launch_integrate_t<float, 4>(b, s, h, c, nz, g0, g1, st);
         }

@@ -3,6 +3,7 @@ trajectories per parameter value) share blocks.  The packed layout must give bit
 state, moments and histograms of the one-set-per-tile layout (the work-queue schedule never
 packs), and packed sets must match the FP64 oracle trajectory by trajectory."""
 import math
+import time
 
 import numpy as np
 import pytest
@@ -127,3 +128,49 @@ def test_narrow_packed_items_against_wide(abp):
         assert torch.equal(sa[k], sb[k]), k
     for k in ra:
         assert torch.equal(ra[k], rb[k]), k
+
+
+@pytest.mark.parametrize("n_traj,scheme", [(4096, 0), (777, 0), (4096, 1), (12800, 0)])
+def test_warp_specialised_narrow_launch_is_bitwise_the_wide_one(abp, n_traj, scheme):
+    # narrow lockstep blocks of 32 stepping threads run warp-specialised (a producer warp draws
+    # the noise into a shared-memory ring of 16-step slots; 777 trajectories leave a ragged
+    # last block); 64-thread blocks (12,800 trajectories) run the plain narrow kernel.  Launch
+    # windows (250 steps), snapshots (every 77 steps) and the run's end (1,003 steps) fall
+    # inside slots; state, histograms and moments must be the work queue's bits (it never
+    # narrows).
+    w = W.single_set(n_traj=n_traj, n_steps=1003, hist_x_bins=32)
+    w.hist_v_bins, w.v_lo, w.v_hi, w.snapshot_every, w.scheme = 16, -2.0, 2.0, 77, scheme
+    ra, sa, ta = run(abp, w, schedule=1, particles_per_thread=1, steps_per_launch=250)
+    rb, sb, tb = run(abp, w, schedule=2, particles_per_thread=1)
+    assert ta["narrow"] == (64 if n_traj == 12800 else 32) and tb["narrow"] == 0
+    for k in sa:
+        assert torch.equal(sa[k], sb[k]), k
+    for k in ra:
+        assert torch.equal(ra[k], rb[k]), k
+
+
+def test_warp_specialised_wait_reports_timeout_and_context_recovers(abp):
+    # the test hook keeps tile 0's producer warps from handing over any noise: its stepping
+    # warps wait until the (0.2 s) limit expires, the launch ends with ABP_ETIMEOUT, and the
+    # context gives a clean run's bits after a reset
+    w = W.single_set(n_traj=4096, n_steps=500)
+    _, ref, _ = run(abp, w, schedule=1, particles_per_thread=1)
+    with abp.Ensemble(w, schedule=1, particles_per_thread=1) as ens:
+        ens.set_params()
+        assert ens.tiles()["narrow"] == 32
+        abp.abp_set_wait_limit(ens.ctx, 200_000_000)
+        abp.abp_test_hold_tile(ens.ctx, 0)
+        t0 = time.time()
+        ens.integrate(-1)
+        with pytest.raises(abp.AbpError) as ei:
+            ens.synchronize()
+        assert ei.value.status == abp.ABP_ETIMEOUT
+        assert time.time() - t0 < 30
+        abp.abp_test_hold_tile(ens.ctx, -1)
+        abp.abp_set_wait_limit(ens.ctx, 0)
+        ens.reset(w.seed)
+        ens.integrate(-1)
+        ens.synchronize()
+        st = ens.state()
+        for k in st:
+            assert torch.equal(st[k], ref[k]), k
