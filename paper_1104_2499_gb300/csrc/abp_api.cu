@@ -126,13 +126,18 @@ int tune_kind(const abp_ctx *ctx) {
     return ctx->cfg.state_fp64 ? 1 : ctx->cfg.scheme == 1 ? 2 : ctx->cfg.noise == 1 ? 3 : 0;
 }
 
+// The autotuner's trial batch: one set of kTrialTrajPerSm trajectories per SM,
+// kTrialSteps timed steps, run by the work queue as kTrialRounds rounds (as
+// real batches run it).
+constexpr int64_t kTrialTrajPerSm = 4096;
+constexpr int64_t kTrialSteps = 8192;
+constexpr int kTrialRounds = 4;
+
 void measure_candidates(abp_ctx *ctx, TuneTable &tt) {
     const int fp = ctx->cfg.state_fp64 ? 1 : 0;
     const bool heun = ctx->cfg.scheme == 1;
-    const int64_t T = (int64_t)std::max(ctx->sm_count, 1) * 4096;
-    // the timed window runs as kTrialRounds work-queue rounds, as real batches do
-    constexpr int kTrialRounds = 4;
-    const int64_t warm = 256, steps = 8192;
+    const int64_t T = (int64_t)std::max(ctx->sm_count, 1) * kTrialTrajPerSm;
+    const int64_t warm = 256, steps = kTrialSteps;
     const size_t rsz = fp ? sizeof(double) : sizeof(float);
     const int cands[3] = {1, 2, 4};
     const int max_tiles = (int)((T + kThreads - 1) / kThreads);
@@ -530,10 +535,15 @@ void autotune(abp_ctx *ctx) {
             if (oe != cudaSuccess) cudaGetLastError();
             const int64_t cap = (int64_t)std::max(bps, 1) * std::max(ctx->sm_count, 1);
             const int64_t spl = c.steps_per_launch > 0 ? c.steps_per_launch : default_steps_per_launch(ctx);
-            const double pred = (double)tt.ms[sch][ci] / batch_efficiency(ctx->n_sets, ctx->n_traj.data(),
-                                                                          ctx->n_steps.data(), sch, cands[ci],
-                                                                          c.checkpoint_every > 0, spl, cap) *
-                                (sch == 2 ? 1.0 + kQueueMargin : 1.0);
+            // the trial's own batch keeps part of the capacity idle too (lockstep at two
+            // trajectories per thread: 2.67 waves, so a third of the last one): its time is
+            // brought to full use before the actual batch's busy fraction is applied
+            const int64_t trial_traj = (int64_t)std::max(ctx->sm_count, 1) * kTrialTrajPerSm, trial_steps = kTrialSteps;
+            const double eff_trial = batch_efficiency(1, &trial_traj, &trial_steps, sch, cands[ci], false,
+                                                      sch == 1 ? kTrialSteps : kTrialSteps / kTrialRounds, cap);
+            const double eff_batch = batch_efficiency(ctx->n_sets, ctx->n_traj.data(), ctx->n_steps.data(), sch,
+                                                      cands[ci], c.checkpoint_every > 0, spl, cap);
+            const double pred = (double)tt.ms[sch][ci] * eff_trial / eff_batch * (sch == 2 ? 1.0 + kQueueMargin : 1.0);
             if (pred < best) {
                 best = pred;
                 bs = sch;
