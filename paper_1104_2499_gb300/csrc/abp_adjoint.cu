@@ -34,6 +34,10 @@ namespace {
 #ifndef ABP_ADJ_REV_THREADS
 #define ABP_ADJ_REV_THREADS 256
 #endif
+// Level 1 with two trajectories per thread in paired FP32 (1) or one (0).
+#ifndef ABP_ADJ_L1_PAIRS
+#define ABP_ADJ_L1_PAIRS 1
+#endif
 // Threads per block of the register-heavy reverse kernel (a multiple of 32).
 constexpr int kRevThreads = ABP_ADJ_REV_THREADS;
 // Threads per block of the level-1 kernel: small blocks, so that one fits on
@@ -195,6 +199,66 @@ __device__ __forceinline__ void level1_segment(const AdjArgs &a, const Coef<floa
     }
 }
 
+// level1_segment for two trajectories (idx0, idx1) of one thread: whole
+// aligned chunks step the pair with paired FP32 instructions (same operations
+// as em_step_f32 / box_muller_f32 on each half, so the sub-checkpoints are the
+// scalar ones bit for bit); other chunks step each trajectory on its own.
+// store1: whether the second trajectory is real (else it duplicates the first
+// one's neighbour and its sub-checkpoints are not written).
+__device__ __forceinline__ void level1_segment2(const AdjArgs &a, const Coef<float> &k, const StepStream (&ss)[2],
+                                                const int64_t (&idx)[2], bool store1, int64_t s0, int64_t s1,
+                                                float4 c0, float4 c1) {
+    const int64_t T = a.b.total_traj;
+    float y[2] = {c0.x, c1.x}, yacc[2] = {c0.y, c1.y}, v[2] = {c0.z, c1.z}, e[2] = {c0.w, c1.w};
+    float pb[2] = {phase_base(y[0]), phase_base(y[1])};
+    const int n_chunks = (int)((s1 - s0 + kSub - 1) / kSub);
+    const bool aligned = (s0 & (kSub - 1)) == 0;
+    const Coef2 k2 = make_coef2(k);
+    NoiseCursor nc[2];
+    nc[0].valid = nc[1].valid = false;
+    nc[0].m = nc[1].m = 0;
+    for (int j = 0; j < n_chunks; ++j) {
+        const int64_t n0 = s0 + (int64_t)j * kSub;
+        a.sub[(size_t)j * T + idx[0]] = make_float4(y[0], yacc[0], v[0], e[0]);
+        if (store1) a.sub[(size_t)j * T + idx[1]] = make_float4(y[1], yacc[1], v[1], e[1]);
+        const int len = (int)(s1 - n0 < kSub ? s1 - n0 : kSub);
+        if (aligned && len == kSub) {
+            float2 Y = make_float2(yacc[0], yacc[1]), V = make_float2(v[0], v[1]), E = make_float2(e[0], e[1]);
+            const float2 PB = make_float2(pb[0], pb[1]);
+#pragma unroll
+            for (int b2 = 0; b2 < kSub / 4; ++b2) {
+                const uint32_t m = (uint32_t)(n0 >> 2) + b2;
+                const uint4 w0 = step_block(m, ss[0], a.K), w1 = step_block(m, ss[1], a.K);
+                float2 nr, cs, sn;
+                box_muller_f32x2(make_uint2(w0.x, w1.x), make_uint2(w0.y, w1.y), k2.bm, nr, cs, sn);
+                em_step_f32x2(k2, nr, cs, PB, Y, V, E);
+                em_step_f32x2(k2, nr, sn, PB, Y, V, E);
+                box_muller_f32x2(make_uint2(w0.z, w1.z), make_uint2(w0.w, w1.w), k2.bm, nr, cs, sn);
+                em_step_f32x2(k2, nr, cs, PB, Y, V, E);
+                em_step_f32x2(k2, nr, sn, PB, Y, V, E);
+            }
+            yacc[0] = Y.x;
+            yacc[1] = Y.y;
+            v[0] = V.x;
+            v[1] = V.y;
+            e[0] = E.x;
+            e[1] = E.y;
+            if (((n0 + kSub) & (kBlockSteps - 1)) == 0) {
+                fold(y[0], yacc[0], pb[0]);
+                fold(y[1], yacc[1], pb[1]);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 2; ++q)
+                for (int i = 0; i < len; ++i) {
+                    float nrs, tr;
+                    nc[q].at(k, ss[q], a.K, n0 + i, nrs, tr);
+                    fwd(k, nrs, tr, n0 + i, y[q], yacc[q], pb[q], v[q], e[q]);
+                }
+        }
+    }
+}
+
 // Level 2 and the reverse sweep of segment [s0, s1): its kSub-step chunks in
 // reverse order, each re-run from its sub-checkpoint into registers and swept
 // backwards.  Each chunk's sub-checkpoint is loaded one chunk ahead, so its
@@ -286,6 +350,29 @@ __global__ void __launch_bounds__(kL1Threads) adjoint_level1_kernel(AdjArgs a, i
     const int64_t idx = b.tile_first[tile] + li;
     const StepStream ss = step_stream((uint64_t)idx + a.nz.traj_base, a.K);
     level1_segment(a, k, ss, idx, s0, s1, a.ck.ck[(size_t)seg * T + idx]);
+}
+
+// Level 1 with two trajectories per thread (trajectories li and li +
+// blockDim.x of the block's 2 blockDim.x), `sub` blocks per tile.
+__global__ void __launch_bounds__(kL1Threads) adjoint_level1_pair_kernel(AdjArgs a, int64_t seg, int sub) {
+    const Batch &b = a.b;
+    const int tile = (int)blockIdx.x / sub;
+    const int li = ((int)blockIdx.x % sub) * 2 * (int)blockDim.x + (int)threadIdx.x;
+    const int set = b.tile_set[tile];
+    const int64_t N = b.set_steps[set], K = a.ck.every, T = b.total_traj;
+    const int64_t s0 = seg * K;
+    if (s0 >= N) return;  // uniform over the block
+    const int64_t s1 = min(s0 + K, N);
+    const int count = b.tile_count[tile];
+    if (li >= count) return;
+    const abp_params p = b.params[set];
+    const Coef<float> k = make_coef<float>(p.q, p.c, p.d, p.gamma0, p.F0, p.D, p.h, p.L, p.asym, a.nz.dt);
+    const bool second = li + (int)blockDim.x < count;
+    const int64_t idx[2] = {b.tile_first[tile] + li, b.tile_first[tile] + (second ? li + (int)blockDim.x : li)};
+    const StepStream ss[2] = {step_stream((uint64_t)idx[0] + a.nz.traj_base, a.K),
+                              step_stream((uint64_t)idx[1] + a.nz.traj_base, a.K)};
+    level1_segment2(a, k, ss, idx, second, s0, s1, a.ck.ck[(size_t)seg * T + idx[0]],
+                    a.ck.ck[(size_t)seg * T + idx[1]]);
 }
 
 __global__ void __launch_bounds__(kRevThreads, ABP_ADJ_MIN_BLOCKS) adjoint_reverse_kernel(AdjArgs a, SegView sv,
@@ -489,11 +576,16 @@ extern "C" abp_status abp_backward_windowed(abp_ctx *ctx, const double *dJ_dmean
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s2, start, 0);
         // blocks per tile: tiles hold up to kThreads * ppt trajectories
         const int cap = kThreads * std::max(ctx->ppt, 1);
-        const int sub1 = (cap + kL1Threads - 1) / kL1Threads, sub2 = (cap + kRevThreads - 1) / kRevThreads;
+        const int per1 = ABP_ADJ_L1_PAIRS ? 2 * kL1Threads : kL1Threads;
+        const int sub1 = (cap + per1 - 1) / per1, sub2 = (cap + kRevThreads - 1) / kRevThreads;
         auto level1 = [&](int64_t j) {
             AdjArgs aj = a;
             aj.sub = sub[j & 1];
-            adjoint_level1_kernel<<<(unsigned)((int64_t)ctx->n_tiles * sub1), kL1Threads, 0, s2>>>(aj, j, sub1);
+            if (ABP_ADJ_L1_PAIRS)
+                adjoint_level1_pair_kernel<<<(unsigned)((int64_t)ctx->n_tiles * sub1), kL1Threads, 0, s2>>>(aj, j,
+                                                                                                           sub1);
+            else
+                adjoint_level1_kernel<<<(unsigned)((int64_t)ctx->n_tiles * sub1), kL1Threads, 0, s2>>>(aj, j, sub1);
             return cudaEventRecord(l1_done[j & 1], s2);
         };
         if (e == cudaSuccess && n_seg > 0) e = level1(n_seg - 1);
