@@ -34,6 +34,22 @@ namespace {
 #ifndef ABP_ADJ_REV_THREADS
 #define ABP_ADJ_REV_THREADS 256
 #endif
+// Reverse sweep with two trajectories per thread in paired FP32 (1) or one (0),
+// and the block size and minimum resident blocks of the paired reverse kernel.
+// Measured on the full differentiation workload (1M x 1e5, K = 1,000),
+// backward time: one trajectory per thread 318 ms; paired, 210 registers (two
+// 128-thread blocks per SM) 313 ms; paired, capped at 168 registers for three
+// blocks per SM (no spills) 304 ms; paired with 4-step sub-chunks 324 ms.
+#ifndef ABP_ADJ_REV_PAIRS
+#define ABP_ADJ_REV_PAIRS 1
+#endif
+#ifndef ABP_ADJ_REV_PAIR_THREADS
+#define ABP_ADJ_REV_PAIR_THREADS 128
+#endif
+#ifndef ABP_ADJ_REV_PAIR_MIN_BLOCKS
+#define ABP_ADJ_REV_PAIR_MIN_BLOCKS 3
+#endif
+constexpr int kRevPairThreads = ABP_ADJ_REV_PAIR_THREADS;
 // Level 1 with two trajectories per thread in paired FP32 (1) or one (0).
 #ifndef ABP_ADJ_L1_PAIRS
 #define ABP_ADJ_L1_PAIRS 1
@@ -320,6 +336,151 @@ __device__ __forceinline__ void reverse_chunks(const AdjArgs &a, const Coef<floa
     }
 }
 
+// reverse_step of two trajectories in the halves of FP32 pairs, same
+// operations in the same order as the scalar function (each half rounded as
+// the scalar operation), so the gradient sums are the scalar kernel's bits.
+struct RevCoef2 {
+    float2 kx, dtf, twoA4, K, Bd, G, m2Bd, nBd, A, one, mone, two, neg;
+};
+
+__device__ __forceinline__ RevCoef2 make_rev_coef2(const Coef<float> &k, float kx, float dtf) {
+    RevCoef2 c;
+    c.kx = dup2(kx);
+    c.dtf = dup2(dtf);
+    c.twoA4 = dup2(2.0f * k.A4);
+    c.K = dup2(k.K);
+    c.Bd = dup2(k.Bd);
+    c.G = dup2(k.G);
+    c.m2Bd = dup2(-2.0f * k.Bd);
+    c.nBd = dup2(-k.Bd);
+    c.A = dup2(k.A);
+    c.one = dup2(1.0f);
+    c.mone = dup2(-1.0f);
+    c.two = dup2(2.0f);
+    c.neg = dup2(-1.0f);
+    return c;
+}
+
+__device__ __forceinline__ void reverse_step_x2(const RevCoef2 &c, float2 ph, float2 vv, float2 ee, float2 sz,
+                                                float2 &lx, float2 &lv, float2 &le, float2 (&acc)[6]) {
+    float2 sphi, cphi;
+    __sincosf(ph.x, &sphi.x, &cphi.x);
+    __sincosf(ph.y, &sphi.y, &cphi.y);
+    acc[0] = __ffma2_rn(lv, sz, acc[0]);
+    acc[1] = __fadd2_rn(acc[1], le);
+    acc[2] = __ffma2_rn(le, ee, acc[2]);
+    acc[3] = __ffma2_rn(__fmul2_rn(ee, vv), __ffma2_rn(__fmul2_rn(le, c.neg), vv, lv), acc[3]);
+    acc[4] = __ffma2_rn(lv, vv, acc[4]);
+    acc[5] = __ffma2_rn(lv, __ffma2_rn(__fmul2_rn(c.two, cphi), cphi, c.mone), acc[5]);
+    const float2 dvdx = __fmul2_rn(__fmul2_rn(c.kx, sphi), __ffma2_rn(c.twoA4, cphi, c.K));
+    const float2 dvdv = __ffma2_rn(c.Bd, ee, c.G);
+    const float2 dedv = __fmul2_rn(__fmul2_rn(c.m2Bd, ee), vv);
+    const float2 dvde = __fmul2_rn(c.Bd, vv);
+    const float2 dede = __ffma2_rn(c.nBd, __fmul2_rn(vv, vv), c.A);
+    const float2 nlx = __ffma2_rn(dvdx, lv, lx);
+    const float2 nlv = __ffma2_rn(c.dtf, lx, __ffma2_rn(dvdv, lv, __ffma2_rn(dedv, le, c.one)));
+    const float2 nle = __ffma2_rn(dvde, lv, __fmul2_rn(dede, le));
+    lx = nlx;
+    lv = nlv;
+    le = nle;
+}
+
+// reverse_chunks for two trajectories of one thread (idx[0], idx[1]): whole
+// aligned chunks run the level-2 re-run and the reverse sweep on FP32 pairs;
+// other chunks run each trajectory on its own with the scalar functions.
+__device__ __forceinline__ void reverse_chunks2(const AdjArgs &a, const Coef<float> &k, const StepStream (&ss)[2],
+                                                float kx, float dtf, const int64_t (&idx)[2], int64_t s0, int64_t s1,
+                                                float2 &lx, float2 &lv, float2 &le, float2 (&acc)[6]) {
+    const int64_t T = a.b.total_traj;
+    const int n_chunks = (int)((s1 - s0 + kSub - 1) / kSub);
+    const bool aligned = (s0 & (kSub - 1)) == 0;
+    const Coef2 k2 = make_coef2(k);
+    const RevCoef2 rc = make_rev_coef2(k, kx, dtf);
+    float4 n0c = a.sub[(size_t)(n_chunks - 1) * T + idx[0]], n1c = a.sub[(size_t)(n_chunks - 1) * T + idx[1]];
+    for (int j = n_chunks - 1; j >= 0; --j) {
+        const int64_t n0 = s0 + (int64_t)j * kSub;
+        const int len = (int)(s1 - n0 < kSub ? s1 - n0 : kSub);
+        const float4 c0 = n0c, c1 = n1c;
+        if (j > 0) {
+            n0c = a.sub[(size_t)(j - 1) * T + idx[0]];
+            n1c = a.sub[(size_t)(j - 1) * T + idx[1]];
+        }
+        if (aligned && len == kSub) {
+            float2 Y = make_float2(c0.y, c1.y), V = make_float2(c0.z, c1.z), E = make_float2(c0.w, c1.w);
+            const float2 PB = make_float2(phase_base(c0.x), phase_base(c1.x));
+            float2 ys[kSub], vs[kSub], es[kSub], szs[kSub];
+#pragma unroll
+            for (int b2 = 0; b2 < kSub / 4; ++b2) {
+                const uint32_t m = (uint32_t)(n0 >> 2) + b2;
+                const uint4 w0 = step_block(m, ss[0], a.K), w1 = step_block(m, ss[1], a.K);
+                float2 nr[2], tr[4];
+                float2 cs, sn;
+                box_muller_f32x2(make_uint2(w0.x, w1.x), make_uint2(w0.y, w1.y), k2.bm, nr[0], cs, sn);
+                tr[0] = cs;
+                tr[1] = sn;
+                box_muller_f32x2(make_uint2(w0.z, w1.z), make_uint2(w0.w, w1.w), k2.bm, nr[1], cs, sn);
+                tr[2] = cs;
+                tr[3] = sn;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int q = 4 * b2 + i;
+                    ys[q] = __ffma2_rn(Y, dup2(kTwoPiF), PB);
+                    vs[q] = V;
+                    es[q] = E;
+                    szs[q] = __fmul2_rn(nr[i >> 1], tr[i]);
+                    em_step_f32x2(k2, nr[i >> 1], tr[i], PB, Y, V, E);
+                }
+            }
+#pragma unroll
+            for (int i = kSub - 1; i >= 0; --i) reverse_step_x2(rc, ys[i], vs[i], es[i], szs[i], lx, lv, le, acc);
+        } else {
+            // scalar path, one trajectory after the other
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const float4 cq = q ? c1 : c0;
+                float y = cq.x, yacc = cq.y, v = cq.z, e = cq.w;
+                float pb = phase_base(y);
+                float lxq = q ? lx.y : lx.x, lvq = q ? lv.y : lv.x, leq = q ? le.y : le.x;
+                float accq[6];
+#pragma unroll
+                for (int r = 0; r < 6; ++r) accq[r] = q ? acc[r].y : acc[r].x;
+                NoiseCursor nc;
+                nc.valid = false;
+                nc.m = 0;
+                float ysq[kSub], vsq[kSub], esq[kSub], szq[kSub];
+#pragma unroll
+                for (int i = 0; i < kSub; ++i) {
+                    if (i < len) {
+                        float nrs, tr;
+                        nc.at(k, ss[q], a.K, n0 + i, nrs, tr);
+                        ysq[i] = phase_arg(pb, yacc);
+                        vsq[i] = v;
+                        esq[i] = e;
+                        szq[i] = nrs * tr;
+                        fwd(k, nrs, tr, n0 + i, y, yacc, pb, v, e);
+                    }
+                }
+#pragma unroll
+                for (int i = kSub - 1; i >= 0; --i)
+                    if (i < len) reverse_step(k, kx, dtf, ysq[i], vsq[i], esq[i], szq[i], lxq, lvq, leq, accq);
+                if (q) {
+                    lx.y = lxq;
+                    lv.y = lvq;
+                    le.y = leq;
+#pragma unroll
+                    for (int r = 0; r < 6; ++r) acc[r].y = accq[r];
+                } else {
+                    lx.x = lxq;
+                    lv.x = lvq;
+                    le.x = leq;
+#pragma unroll
+                    for (int r = 0; r < 6; ++r) acc[r].x = accq[r];
+                }
+            }
+        }
+    }
+}
+
 // One launch per segment index and level, segments in reverse order: level 1
 // (a plain forward re-run, light on registers) for segment `seg` of every
 // trajectory, then level 2 and the reverse sweep (register-heavy) for the same
@@ -402,6 +563,45 @@ __global__ void __launch_bounds__(kRevThreads, ABP_ADJ_MIN_BLOCKS) adjoint_rever
     sv.lam[idx] = make_float4(lx, lv, le, 0.0f);
 #pragma unroll
     for (int q = 0; q < 6; ++q) sv.G[(size_t)q * T + idx] += (double)acc[q];
+}
+
+// The reverse kernel with two trajectories per thread (trajectories li and
+// li + blockDim.x of the block's 2 blockDim.x), `sub` blocks per tile.
+__global__ void __launch_bounds__(kRevPairThreads, ABP_ADJ_REV_PAIR_MIN_BLOCKS) adjoint_reverse_pair_kernel(AdjArgs a, SegView sv, int64_t seg,
+                                                                               int sub, int64_t window) {
+    const Batch &b = a.b;
+    const int tile = (int)blockIdx.x / sub;
+    const int li = ((int)blockIdx.x % sub) * 2 * (int)blockDim.x + (int)threadIdx.x;
+    const int set = b.tile_set[tile];
+    const int64_t N = b.set_steps[set], K = a.ck.every, T = b.total_traj;
+    const int64_t s0 = seg * K;
+    if (s0 >= N) return;  // uniform over the block
+    const int64_t s1 = min(s0 + K, N);
+    const int count = b.tile_count[tile];
+    if (li >= count) return;
+    const abp_params p = b.params[set];
+    const Coef<float> k = make_coef<float>(p.q, p.c, p.d, p.gamma0, p.F0, p.D, p.h, p.L, p.asym, a.nz.dt);
+    const float dtf = (float)a.nz.dt;
+    const float kx = (float)(-2.0 * kPi / p.L);
+    const bool second = li + (int)blockDim.x < count;
+    const int64_t idx[2] = {b.tile_first[tile] + li, b.tile_first[tile] + (second ? li + (int)blockDim.x : li)};
+    const StepStream ss[2] = {step_stream((uint64_t)idx[0] + a.nz.traj_base, a.K),
+                              step_stream((uint64_t)idx[1] + a.nz.traj_base, a.K)};
+    float4 l0 = sv.lam[idx[0]], l1 = sv.lam[idx[1]];
+    if (window > 0 && ((seg + 1) * K) % window == 0) l0 = l1 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    float2 lx = make_float2(l0.x, l1.x), lv = make_float2(l0.y, l1.y), le = make_float2(l0.z, l1.z);
+    float2 acc[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) acc[q] = make_float2(0.0f, 0.0f);
+    reverse_chunks2(a, k, ss, kx, dtf, idx, s0, s1, lx, lv, le, acc);
+    sv.lam[idx[0]] = make_float4(lx.x, lv.x, le.x, 0.0f);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) sv.G[(size_t)q * T + idx[0]] += (double)acc[q].x;
+    if (second) {
+        sv.lam[idx[1]] = make_float4(lx.y, lv.y, le.y, 0.0f);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) sv.G[(size_t)q * T + idx[1]] += (double)acc[q].y;
+    }
 }
 
 // Per tile: the initial-condition term, the parameter scales and the caller's
@@ -577,7 +777,8 @@ extern "C" abp_status abp_backward_windowed(abp_ctx *ctx, const double *dJ_dmean
         // blocks per tile: tiles hold up to kThreads * ppt trajectories
         const int cap = kThreads * std::max(ctx->ppt, 1);
         const int per1 = ABP_ADJ_L1_PAIRS ? 2 * kL1Threads : kL1Threads;
-        const int sub1 = (cap + per1 - 1) / per1, sub2 = (cap + kRevThreads - 1) / kRevThreads;
+        const int per2 = ABP_ADJ_REV_PAIRS ? 2 * kRevPairThreads : kRevThreads;
+        const int sub1 = (cap + per1 - 1) / per1, sub2 = (cap + per2 - 1) / per2;
         auto level1 = [&](int64_t j) {
             AdjArgs aj = a;
             aj.sub = sub[j & 1];
@@ -597,8 +798,12 @@ extern "C" abp_status abp_backward_windowed(abp_ctx *ctx, const double *dJ_dmean
             if (e == cudaSuccess) e = cudaStreamWaitEvent(s, l1_done[seg & 1], 0);
             AdjArgs as = a;
             as.sub = sub[seg & 1];
-            adjoint_reverse_kernel<<<(unsigned)((int64_t)ctx->n_tiles * sub2), kRevThreads, 0, s>>>(as, sv, seg, sub2,
-                                                                                                   window);
+            if (ABP_ADJ_REV_PAIRS)
+                adjoint_reverse_pair_kernel<<<(unsigned)((int64_t)ctx->n_tiles * sub2), kRevPairThreads, 0, s>>>(
+                    as, sv, seg, sub2, window);
+            else
+                adjoint_reverse_kernel<<<(unsigned)((int64_t)ctx->n_tiles * sub2), kRevThreads, 0, s>>>(as, sv, seg,
+                                                                                                       sub2, window);
             if (e == cudaSuccess) e = cudaEventRecord(rev_done[seg & 1], s);
             ctx->launches += 2;
         }
