@@ -181,6 +181,31 @@ def oracle_sample(w, budget_s: float, gpu_moments=None):
     return done_ps / t_used, cores, desc, parity, one_core
 
 
+def oracle_subset_rate(w, traj_per_set: int, max_steps: int = 0):
+    """The FP64 oracle's throughput on a fixed subset of workload ``w``: the first
+    ``traj_per_set`` trajectories of every set, over all their steps (or the first
+    ``max_steps``), on all host cores."""
+    from oracle import oracle as O
+
+    O.build()
+    cores = os.cpu_count() or 1
+    base = w.traj_base()
+    done, t = 0, 0.0
+    for i in range(w.n_sets):
+        m = min(traj_per_set, w.n_traj[i])
+        n = w.n_steps[i] if max_steps <= 0 else min(max_steps, w.n_steps[i])
+        if m <= 0 or n <= 0:
+            continue
+        t0 = time.perf_counter()
+        O.run_set(w.sets[i], seed=w.seed, dt=w.dt, n_traj=m, n_steps=n, traj_base=base[i], v0_mode=w.v0_mode,
+                  n_threads=cores)
+        t += time.perf_counter() - t0
+        done += m * n
+    desc = "first %d trajectories of each of %d sets, %s (%.3g particle-steps)" % (
+        traj_per_set, w.n_sets, "all steps" if max_steps <= 0 else "%d steps" % max_steps, done)
+    return {"value": done / t, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+
+
 def run_reference(args, rank, world):
     """The reference arm: the FP64 CPU oracle, timed on the host cores."""
     from paper_1104_2499_gb300 import workloads as W
@@ -521,11 +546,15 @@ def configs_leg(A, stream, names):
         if name == "single":
             out[name] = time_workload(A, stream, W.single_set(), 5)[0]
         elif name == "uneven":
-            out[name] = time_workload(A, stream, W.uneven_batch(), 1)[0]
+            w = W.uneven_batch()
+            out[name] = time_workload(A, stream, w, 1)[0]
+            out[name]["cpu_oracle"] = oracle_subset_rate(w, 16)
         elif name == "force":
             out[name] = force_leg(A, stream)
         elif name == "snapshots":
-            out[name] = time_workload(A, stream, W.large_snapshots(), 1)[0]
+            w = W.large_snapshots()
+            out[name] = time_workload(A, stream, w, 1)[0]
+            out[name]["cpu_oracle"] = oracle_subset_rate(w, 65536, 10_000)
         elif name == "heun":
             w = W.sweep_grid()
             w.scheme, w.name = 1, w.name + "_heun"
