@@ -421,8 +421,8 @@ __device__ __forceinline__ void advance(const Coef<R> &k, const RoundKeys &K, Sl
 }
 
 // ------------------------------------------- warp-specialised narrow launch
-// A narrow launch has at most one warp per scheduler, so a warp steps alone and
-// its time per step is the latency of its own instruction chain: the counter
+// A narrow launch of 32-thread blocks puts fewer than two warps on an SM, so a
+// warp steps alone and its time per step is the latency of its own chain: the counter
 // block and Box-Muller of four steps, then four dependent state updates.  In
 // the warp-specialised form every consumer warp (its trajectories stepped as
 // in run_tile) has a producer warp that draws the same (nrs, trig) pairs for
