@@ -499,7 +499,8 @@ struct WsCons {
 };
 
 // advance() with the noise taken from the ring (FP32, one trajectory per
-// thread, counter-based noise).
+// thread; the producer drew it from the counter-based stream or from the
+// trajectory's xorshift generator).
 template <bool HEUN>
 __device__ __forceinline__ void advance_ws(const Coef<float> &k, Slots<float, 1> &S, int64_t n, int64_t n_end,
                                            WsCons &c) {
@@ -552,7 +553,7 @@ __device__ __forceinline__ void run_tile(const Batch &b, const State &st, const 
                                          const Noise &nz, const RoundKeys &K, uint32_t *sh, int tile, int64_t w0,
                                          int64_t w1, int lane_base = 0, WsCons *wc = nullptr) {
     static_assert(!PACKED || PPT == 1, "packed tiles hold one trajectory per thread");
-    static_assert(!WS || (sizeof(R) == 4 && PPT == 1 && MODE != kModeXorshift), "WS: FP32, PPT 1, counter noise");
+    static_assert(!WS || (sizeof(R) == 4 && PPT == 1), "WS: FP32, one trajectory per thread");
     const int64_t first = b.tile_first[tile];
     const int count = b.tile_count[tile];
     const int set_t = b.tile_set[tile];
@@ -582,7 +583,7 @@ __device__ __forceinline__ void run_tile(const Batch &b, const State &st, const 
         S.cell[q] = __ldcg(&s.cell[idx[q]]);
         if constexpr (sizeof(R) == 4) S.pb[q] = phase_base(S.y[q]);
         S.ss[q] = step_stream((uint64_t)idx[q] + nz.traj_base, K);
-        if constexpr (MODE == kModeXorshift) {
+        if constexpr (MODE == kModeXorshift && !WS) {  // in a WS block the producer owns the generator
             const uint4 w = __ldcg(&st.xs[idx[q]]);
             S.xs[q][0] = w.x;
             S.xs[q][1] = w.y;
@@ -654,7 +655,8 @@ __device__ __forceinline__ void run_tile(const Batch &b, const State &st, const 
         s.v[idx[q]] = S.v[q];
         s.e[idx[q]] = S.e[q];
         s.cell[idx[q]] = S.cell[q];
-        if constexpr (MODE == kModeXorshift) st.xs[idx[q]] = make_uint4(S.xs[q][0], S.xs[q][1], S.xs[q][2], S.xs[q][3]);
+        if constexpr (MODE == kModeXorshift && !WS)
+            st.xs[idx[q]] = make_uint4(S.xs[q][0], S.xs[q][1], S.xs[q][2], S.xs[q][3]);
     }
 }
 
@@ -684,11 +686,14 @@ __global__ void ABP_INTEGRATE_BOUNDS integrate_kernel(Batch b, State st, Hist h,
 // Producer side of one warp pair: the (nrs, trig) pairs of every step of the
 // launch's slots for the trajectories of consumer threads ci (lane by lane), in
 // slot order, each slot reused only after its consumer released it.  The
-// values are those single_step / group_step compute: same counter blocks, same
+// values are those single_step / group_step compute: same counter blocks (or,
+// with xorshift noise, the same words of the trajectory's generator, which the
+// producer loads, advances over the launch's steps and stores back), same
 // Box-Muller, same coefficient.
-template <bool PACKED>
-__device__ __forceinline__ void ws_produce(const Batch &b, const Noise &nz, const RoundKeys &K, const WsRing &r,
-                                           int tile, int64_t w0, int64_t w1, int lane_base, int pair, int ci) {
+template <bool PACKED, int MODE>
+__device__ __forceinline__ void ws_produce(const Batch &b, const State &st, const Noise &nz, const RoundKeys &K,
+                                           const WsRing &r, int tile, int64_t w0, int64_t w1, int lane_base, int pair,
+                                           int ci) {
     constexpr int SS = kWsSlotSteps;
     const int64_t first = b.tile_first[tile];
     const int count = b.tile_count[tile];
@@ -708,11 +713,47 @@ __device__ __forceinline__ void ws_produce(const Batch &b, const Noise &nz, cons
     const int lane = threadIdx.x & 31;
     const int64_t a0 = n_begin / SS, a1 = (n_end - 1) / SS;
     bool failed = false;
+    uint32_t xs[4];
+    if constexpr (MODE == kModeXorshift) {
+        const uint4 w = __ldcg(&st.xs[idx]);
+        xs[0] = w.x;
+        xs[1] = w.y;
+        xs[2] = w.z;
+        xs[3] = w.w;
+    }
     for (int64_t a = a0; a <= a1; ++a) {
         const int64_t kf = a - a0;
         const int slot = (int)(kf % kWsSlots);
         if (kf >= kWsSlots) ws_wait(&r.empty[pair * kWsSlots + slot], (uint32_t)((kf / kWsSlots - 1) & 1), r, failed);
         float2 *out = r.buf + ((size_t)(pair * kWsSlots + slot) * SS) * 32 + lane;
+        if constexpr (MODE == kModeXorshift) {
+            // the generator advances only over the launch's own steps (two words and the
+            // Box-Muller cosine per step, as single_step draws them)
+            const int64_t i0 = max(n_begin - a * SS, (int64_t)0), i1 = min(n_end - a * SS, (int64_t)SS);
+            if (i0 == 0 && i1 == SS) {
+                // a whole slot: the words first (the generator's serial chain), then the
+                // transforms, independent of one another
+                uint32_t wv[2 * SS];
+#pragma unroll
+                for (int i = 0; i < 2 * SS; ++i) wv[i] = xorshift128(xs);
+#pragma unroll
+                for (int i = 0; i < SS; ++i) {
+                    float nr, cs, sn;
+                    box_muller_f32(wv[2 * i], wv[2 * i + 1], k.bm, nr, cs, sn);
+                    out[i * 32] = make_float2(nr, cs);
+                }
+            } else {
+                for (int64_t i = i0; i < i1; ++i) {
+                    const uint32_t wa = xorshift128(xs);
+                    const uint32_t wb = xorshift128(xs);
+                    float nr, cs, sn;
+                    box_muller_f32(wa, wb, k.bm, nr, cs, sn);
+                    out[i * 32] = make_float2(nr, cs);
+                }
+            }
+            mbar_arrive(&r.full[pair * kWsSlots + slot]);
+            continue;
+        }
 #pragma unroll
         for (int j = 0; j < SS / 4; ++j) {
             const uint4 wv = step_block((uint32_t)(a * (SS / 4) + j), ss, K);
@@ -726,9 +767,12 @@ __device__ __forceinline__ void ws_produce(const Batch &b, const Noise &nz, cons
         }
         mbar_arrive(&r.full[pair * kWsSlots + slot]);
     }
+    if constexpr (MODE == kModeXorshift) {
+        if (act) st.xs[idx] = make_uint4(xs[0], xs[1], xs[2], xs[3]);
+    }
 }
 
-// Warp-specialised narrow lockstep launch (FP32, counter-based noise): blocks
+// Warp-specialised narrow lockstep launch (FP32, any scheme and noise): blocks
 // of 2 w threads over the w trajectories a narrow block of w threads takes
 // (sub blocks per tile); threads [0, w) step them (run_tile), threads [w, 2 w)
 // produce their noise.  Dynamic shared memory: the histogram bins (one-set
@@ -761,7 +805,7 @@ __global__ void __launch_bounds__(2 * kWsMaxWidth) ws_kernel(Batch b, State st, 
         run_tile<float, 1, PACKED, MODE, kGroupUnroll, true>(b, st, h, ck, nz, kp.K, sh, tile, g0, g1, lane_base, &c);
     } else {
         const int ci = (int)threadIdx.x - w;
-        ws_produce<PACKED>(b, nz, kp.K, r, tile, g0, g1, lane_base, ci >> 5, ci);
+        ws_produce<PACKED, MODE>(b, st, nz, kp.K, r, tile, g0, g1, lane_base, ci >> 5, ci);
     }
 }
 
@@ -1109,7 +1153,7 @@ cudaError_t launch_integrate_t(const Batch &b, const State &s, const Hist &h, co
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    if constexpr (sizeof(R) == 4 && PPT == 1 && MODE != kModeXorshift && ABP_WS) {
+    if constexpr (sizeof(R) == 4 && PPT == 1 && ABP_WS) {
         if (b.narrow > 0 && b.narrow <= kWsMaxWidth && wait && wait->status)
             return launch_ws<MODE>(b, s, h, c, nz, g0, g1, *wait, st);
     }
@@ -1161,7 +1205,7 @@ cudaError_t launch_integrate(const Batch &b, const State &s, const Hist &h, cons
         }
     } else if (nz.noise == 1) {
         switch (ppt) {
-            case 1: return launch_integrate_t<float, 1, kModeXorshift>(b, s, h, c, nz, g0, g1, st);
+            case 1: return launch_integrate_t<float, 1, kModeXorshift>(b, s, h, c, nz, g0, g1, st, wait);
             case 2: return launch_integrate_t<float, 2, kModeXorshift>(b, s, h, c, nz, g0, g1, st);
             case 4: return launch_integrate_t<float, 4, kModeXorshift>(b, s, h, c, nz, g0, g1, st);
         }
