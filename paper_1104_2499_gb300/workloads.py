@@ -71,10 +71,15 @@ class Workload:
         return np.array([[float(s[k]) for k in PARAM_NAMES] for s in self.sets], dtype=np.float64)
 
 
-def _with(**kw) -> dict:
+def params(**kw) -> dict:
+    """One parameter set: the defaults (q, c, d, gamma0, F0, D, h, L, asym) with the given
+    overrides."""
     p = dict(DEFAULTS)
     p.update(kw)
     return p
+
+
+_with = params
 
 
 def single_set(n_traj=4096, n_steps=10_000, D=0.1, seed=0, hist_x_bins=256, **kw) -> Workload:
