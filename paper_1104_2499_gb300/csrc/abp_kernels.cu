@@ -439,9 +439,13 @@ constexpr int kWsSlots = 4;
 // (fewer than two stepping warps per SM) is latency-bound enough to gain.
 // Measured on the work-items sweep (10^4 steps per cycle): 0.30 against 0.42 ms
 // per cycle up to 2^13 items (32 threads), but 0.433 against 0.425 at 2^14 (64)
-// and 0.593 against 0.549 at 2^15 (128), where several stepping warps share a
-// scheduler and the producers' instructions cost more than the chain saves.
-constexpr int kWsMaxWidth = 32;
+// and 0.593 against 0.549 at 2^15 (128), where stepping and producer warps share
+// schedulers (1.74 warps per scheduler at 2^14) and a step takes 87 cycles
+// instead of 59.
+#ifndef ABP_WS_MAX_WIDTH
+#define ABP_WS_MAX_WIDTH 32
+#endif
+constexpr int kWsMaxWidth = ABP_WS_MAX_WIDTH;
 constexpr int kWsMaxPairs = kWsMaxWidth / 32;
 static_assert(kBlockSteps % kWsSlotSteps == 0 && kWsSlotSteps % 4 == 0, "slots hold whole counter blocks");
 
