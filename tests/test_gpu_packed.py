@@ -130,7 +130,7 @@ def test_narrow_packed_items_against_wide(abp):
         assert torch.equal(ra[k], rb[k]), k
 
 
-@pytest.mark.parametrize("n_traj,scheme", [(4096, 0), (777, 0), (4096, 1), (12800, 0)])
+@pytest.mark.parametrize("n_traj,scheme", [(4096, 0), (777, 0), (4096, 1), (12800, 0), (12800, 1)])
 def test_warp_specialised_narrow_launch_is_bitwise_the_wide_one(abp, n_traj, scheme):
     # narrow lockstep blocks of 32 stepping threads run warp-specialised (a producer warp draws
     # the noise into a shared-memory ring of 16-step slots; 777 trajectories leave a ragged
@@ -143,6 +143,23 @@ def test_warp_specialised_narrow_launch_is_bitwise_the_wide_one(abp, n_traj, sch
     ra, sa, ta = run(abp, w, schedule=1, particles_per_thread=1, steps_per_launch=250)
     rb, sb, tb = run(abp, w, schedule=2, particles_per_thread=1)
     assert ta["narrow"] == (64 if n_traj == 12800 else 32) and tb["narrow"] == 0
+    for k in sa:
+        assert torch.equal(sa[k], sb[k]), k
+    for k in ra:
+        assert torch.equal(ra[k], rb[k]), k
+
+
+@pytest.mark.parametrize("scheme,noise", [(0, 0), (1, 0), (0, 1)])
+def test_narrow_packed_64_thread_blocks_are_bitwise_the_wide_ones(abp, scheme, noise):
+    # 16,384 one-trajectory work items fill 64 packed tiles, launched as 64-thread narrow blocks
+    # (the plain narrow kernel); histograms of packed sets go to global memory at every
+    # snapshot, and the launch windows and snapshots fall off the counter blocks
+    w = W.force_sweep(n_F=16384, traj_per_set=1, n_steps=650)
+    w.hist_x_bins, w.hist_v_bins, w.v_lo, w.v_hi, w.snapshot_every = 8, 4, -2.0, 2.0, 97
+    w.scheme, w.noise = scheme, noise
+    ra, sa, ta = run(abp, w, schedule=1, particles_per_thread=1, steps_per_launch=300)
+    rb, sb, tb = run(abp, w, schedule=2, particles_per_thread=1)
+    assert ta["packed"] == 64 and ta["narrow"] == 64 and tb["packed"] == 0
     for k in sa:
         assert torch.equal(sa[k], sb[k]), k
     for k in ra:
