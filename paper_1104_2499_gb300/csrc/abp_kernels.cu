@@ -362,18 +362,22 @@ __device__ __forceinline__ void group_step(const Coef<R> &k, const RoundKeys &K,
     }
 }
 
-// Counter blocks per iteration of the inner loop, per kernel (measured on the
-// D x q sweep): the FP32 Euler-Maruyama kernels with two trajectories per
-// thread run fastest with 8 blocks (32 steps) per iteration, lockstep 1.038e12
+// Counter blocks per iteration of the inner loop, per kernel (measured): the
+// lockstep FP32 Euler-Maruyama kernel with two trajectories per thread runs
+// fastest with 8 blocks (32 steps) per iteration on the D x q sweep, 1.038e12
 // against 1.011e12 particle-steps/s with 2 and 0.98e12 with 12 (a body that no
-// longer fits the instruction cache), the work queue 1.023e12 against
-// 1.002e12; the other kernels keep the default, where longer bodies cost
-// registers and blocks per SM without a measured gain.
+// longer fits the instruction cache).  The work-queue kernel takes 6: it then
+// needs 92 registers and runs two blocks per SM, and on the batches the
+// autotuner gives it (few waves of tiles) fewer resident blocks wait less on
+// their tile's previous round -- load sweep 9.82e11 against 8.9e11-9.0e11 with
+// 8, uneven batch 9.85e11 against 9.8e11 (on the many-tile sweep 8 is 2% faster,
+// but the sweep runs lockstep).  The other kernels keep the default, where longer
+// bodies cost registers and blocks per SM without a measured gain.
 #ifndef ABP_UNROLL_EM2
 #define ABP_UNROLL_EM2 8
 #endif
 #ifndef ABP_UNROLL_EM2_QUEUE
-#define ABP_UNROLL_EM2_QUEUE 8
+#define ABP_UNROLL_EM2_QUEUE 6
 #endif
 #ifndef ABP_UNROLL_HEUN2
 #define ABP_UNROLL_HEUN2 kGroupUnroll
