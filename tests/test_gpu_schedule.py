@@ -107,10 +107,11 @@ def test_autotuner_choices(abp):
 def test_autotuner_weighs_the_batch(abp):
     # the load sweep (64 sets x 4,096 trajectories) fills 1.1 waves of lockstep blocks, so
     # half the second wave idles in every window; the work queue keeps every block busy and
-    # is predicted (and measured, 8.56e11 against 8.04e11 particle-steps/s) faster.  On the
-    # D x q sweep, nine lockstep waves deep, the two schedules run within 1% of each other
-    # at two trajectories per thread (1.008e12 / 1.001e12), and both beat one and four
-    # trajectories per thread by 5% or more: the choice there is PPT 2, either schedule.
+    # is predicted (and measured, 9.82e11 against 8.26e11 particle-steps/s) faster.  On the
+    # D x q sweep, nine lockstep waves deep, the two schedules run within 2% of each other at
+    # two trajectories per thread (lockstep 1.02e12-1.04e12, work queue 1.0e12), and both beat
+    # one and four trajectories per thread by 5% or more: the choice there is PPT 2, either
+    # schedule.
     w = W.force_sweep()
     with abp.Ensemble(w) as ens:
         ens.set_params()
