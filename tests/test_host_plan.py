@@ -79,6 +79,21 @@ def test_busy_fraction_model(A):
     assert A.abp_plan_efficiency([1] * 4096, [1000] * 4096, 2, 1, resident_blocks=16) < 0.01
 
 
+def test_trial_batch_busy_fraction(A):
+    # the autotuner's trial batch (4,096 trajectories per SM, 8,192 timed steps) is itself not
+    # fully busy for every candidate: at two trajectories per thread lockstep runs 1,216 tiles
+    # on 456 resident blocks, 2.67 waves, so a third of the last wave idles; the autotuner
+    # multiplies each trial time by this fraction before dividing by the batch's own
+    T = 152 * 4096
+    lock = {ppt: A.abp_plan_efficiency([T], [8192], 1, ppt, resident_blocks=152 * bps, steps_per_launch=8192)
+            for ppt, bps in ((1, 4), (2, 3), (4, 2))}
+    assert lock[1] == pytest.approx(1.0) and lock[4] == pytest.approx(1.0)
+    assert lock[2] == pytest.approx((1216 / 456) / 3, rel=1e-9)
+    # the work queue, in four rounds of 2,048 steps, loses only its tail
+    wq = A.abp_plan_efficiency([T], [8192], 2, 2, resident_blocks=456, steps_per_launch=2048)
+    assert 0.95 < wq < 1.0
+
+
 def test_invalid_plans_are_refused(A):
     with pytest.raises(A.AbpError):
         A.abp_plan([10], [10], schedule=3, particles_per_thread=1)
