@@ -20,7 +20,8 @@ import numpy as np
 from . import workloads as W
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libabp.so")
+# ABP_LIB selects another build of the library (the checked build, for instance)
+LIB_PATH = os.environ.get("ABP_LIB") or os.path.join(_HERE, "_build", "libabp.so")
 
 ABP_OK, ABP_EINVAL, ABP_ENOMEM, ABP_ECUDA, ABP_ETIMEOUT, ABP_ESTATE = range(6)
 _STATUS = {0: "ABP_OK", 1: "ABP_EINVAL", 2: "ABP_ENOMEM", 3: "ABP_ECUDA", 4: "ABP_ETIMEOUT", 5: "ABP_ESTATE"}

@@ -36,23 +36,28 @@ def _flags():
             "-I", CSRC, "--expt-relaxed-constexpr"]
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS] + [os.path.join(INCLUDE, "abp.h"), __file__]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra: list | None = None) -> str:
-    if not force and not _stale():
-        return LIB
-    os.makedirs(OUT, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra: list | None = None, out_dir: str | None = None) -> str:
+    """Compile the library; ``out_dir`` (default ``_build/``) receives the objects and
+    ``libabp.so``.  The checked build is ``extra=["-DABP_DEBUG_CHECKS=1"]`` into its own
+    directory (``python -m paper_1104_2499_gb300.build --checked``)."""
+    out = out_dir or OUT
+    lib = os.path.join(out, "libabp.so")
+    if not force and not _stale(lib):
+        return lib
+    os.makedirs(out, exist_ok=True)
     cc = nvcc()
     flags = _flags() + list(extra or [])
 
     def compile_one(src):
-        obj = os.path.join(OUT, src.replace(".cu", ".o"))
+        obj = os.path.join(out, src.replace(".cu", ".o"))
         cmd = [cc] + flags + ["-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -63,16 +68,21 @@ def build(force: bool = False, verbose: bool = False, extra: list | None = None)
 
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + ".tmp.%d" % os.getpid()
+    tmp = lib + ".tmp.%d" % os.getpid()
     cmd = [cc, ARCH, "-shared", "-o", tmp] + objs + ["-lcudart_static", "-lrt", "-ldl", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
+
+CHECKED_OUT = os.path.join(PKG, "_build_checked")
 
 if __name__ == "__main__":
     force = "--force" in sys.argv
-    extra = ["-Xptxas", "-v"] if "--ptxas-v" in sys.argv else None
-    print(build(force=force, verbose=True, extra=extra))
+    extra = ["-Xptxas", "-v"] if "--ptxas-v" in sys.argv else []
+    if "--checked" in sys.argv:
+        print(build(force=force, verbose=True, extra=extra + ["-DABP_DEBUG_CHECKS=1"], out_dir=CHECKED_OUT))
+    else:
+        print(build(force=force, verbose=True, extra=extra or None))

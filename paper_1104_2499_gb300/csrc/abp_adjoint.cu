@@ -194,7 +194,7 @@ __device__ __forceinline__ void level1_segment(const AdjArgs &a, const Coef<floa
     nc.m = 0;
     for (int j = 0; j < n_chunks; ++j) {
         const int64_t n0 = s0 + (int64_t)j * kSub;
-        a.sub[(size_t)j * T + idx] = make_float4(y, yacc, v, e);
+        a.sub[(size_t)dchk(j, a.n_sub, a.b.dbg) * T + idx] = make_float4(y, yacc, v, e);
         const int len = (int)(s1 - n0 < kSub ? s1 - n0 : kSub);
         if (aligned && len == kSub) {
 #pragma unroll
@@ -235,8 +235,9 @@ __device__ __forceinline__ void level1_segment2(const AdjArgs &a, const Coef<flo
     nc[0].m = nc[1].m = 0;
     for (int j = 0; j < n_chunks; ++j) {
         const int64_t n0 = s0 + (int64_t)j * kSub;
-        a.sub[(size_t)j * T + idx[0]] = make_float4(y[0], yacc[0], v[0], e[0]);
-        if (store1) a.sub[(size_t)j * T + idx[1]] = make_float4(y[1], yacc[1], v[1], e[1]);
+        const size_t js = (size_t)dchk(j, a.n_sub, a.b.dbg);
+        a.sub[js * T + idx[0]] = make_float4(y[0], yacc[0], v[0], e[0]);
+        if (store1) a.sub[js * T + idx[1]] = make_float4(y[1], yacc[1], v[1], e[1]);
         const int len = (int)(s1 - n0 < kSub ? s1 - n0 : kSub);
         if (aligned && len == kSub) {
             float2 Y = make_float2(yacc[0], yacc[1]), V = make_float2(v[0], v[1]), E = make_float2(e[0], e[1]);
@@ -288,12 +289,12 @@ __device__ __forceinline__ void reverse_chunks(const AdjArgs &a, const Coef<floa
     NoiseCursor nc;
     nc.valid = false;
     nc.m = 0;
-    float4 c_next = a.sub[(size_t)(n_chunks - 1) * T + idx];
+    float4 c_next = a.sub[(size_t)dchk(n_chunks - 1, a.n_sub, a.b.dbg) * T + idx];
     for (int j = n_chunks - 1; j >= 0; --j) {
         const int64_t n0 = s0 + (int64_t)j * kSub;
         const int len = (int)(s1 - n0 < kSub ? s1 - n0 : kSub);
         const float4 cj = c_next;
-        if (j > 0) c_next = a.sub[(size_t)(j - 1) * T + idx];
+        if (j > 0) c_next = a.sub[(size_t)dchk(j - 1, a.n_sub, a.b.dbg) * T + idx];
         float y = cj.x, yacc = cj.y, v = cj.z, e = cj.w;
         float pb = phase_base(y);
         float ys[kSub], vs[kSub], es[kSub], szs[kSub];  // ys: the force phase of each step
@@ -396,14 +397,16 @@ __device__ __forceinline__ void reverse_chunks2(const AdjArgs &a, const Coef<flo
     const bool aligned = (s0 & (kSub - 1)) == 0;
     const Coef2 k2 = make_coef2(k);
     const RevCoef2 rc = make_rev_coef2(k, kx, dtf);
-    float4 n0c = a.sub[(size_t)(n_chunks - 1) * T + idx[0]], n1c = a.sub[(size_t)(n_chunks - 1) * T + idx[1]];
+    const size_t jl = (size_t)dchk(n_chunks - 1, a.n_sub, a.b.dbg);
+    float4 n0c = a.sub[jl * T + idx[0]], n1c = a.sub[jl * T + idx[1]];
     for (int j = n_chunks - 1; j >= 0; --j) {
         const int64_t n0 = s0 + (int64_t)j * kSub;
         const int len = (int)(s1 - n0 < kSub ? s1 - n0 : kSub);
         const float4 c0 = n0c, c1 = n1c;
         if (j > 0) {
-            n0c = a.sub[(size_t)(j - 1) * T + idx[0]];
-            n1c = a.sub[(size_t)(j - 1) * T + idx[1]];
+            const size_t jp = (size_t)dchk(j - 1, a.n_sub, a.b.dbg);
+            n0c = a.sub[jp * T + idx[0]];
+            n1c = a.sub[jp * T + idx[1]];
         }
         if (aligned && len == kSub) {
             float2 Y = make_float2(c0.y, c1.y), V = make_float2(c0.z, c1.z), E = make_float2(c0.w, c1.w);
@@ -508,9 +511,9 @@ __global__ void __launch_bounds__(kL1Threads) adjoint_level1_kernel(AdjArgs a, i
     const abp_params p = b.params[set];
     const Coef<float> k = make_coef<float>(p.q, p.c, p.d, p.gamma0, p.F0, p.D, p.h, p.L, p.asym, a.nz.dt);
     if (li >= b.tile_count[tile]) return;
-    const int64_t idx = b.tile_first[tile] + li;
+    const int64_t idx = dchk(b.tile_first[tile] + li, T, b.dbg);
     const StepStream ss = step_stream((uint64_t)idx + a.nz.traj_base, a.K);
-    level1_segment(a, k, ss, idx, s0, s1, a.ck.ck[(size_t)seg * T + idx]);
+    level1_segment(a, k, ss, idx, s0, s1, a.ck.ck[(size_t)dchk(seg, a.ck.n_slots, b.dbg) * T + idx]);
 }
 
 // Level 1 with two trajectories per thread (trajectories li and li +
@@ -529,11 +532,13 @@ __global__ void __launch_bounds__(kL1Threads) adjoint_level1_pair_kernel(AdjArgs
     const abp_params p = b.params[set];
     const Coef<float> k = make_coef<float>(p.q, p.c, p.d, p.gamma0, p.F0, p.D, p.h, p.L, p.asym, a.nz.dt);
     const bool second = li + (int)blockDim.x < count;
-    const int64_t idx[2] = {b.tile_first[tile] + li, b.tile_first[tile] + (second ? li + (int)blockDim.x : li)};
+    const int64_t idx[2] = {dchk(b.tile_first[tile] + li, T, b.dbg),
+                            dchk(b.tile_first[tile] + (second ? li + (int)blockDim.x : li), T, b.dbg)};
     const StepStream ss[2] = {step_stream((uint64_t)idx[0] + a.nz.traj_base, a.K),
                               step_stream((uint64_t)idx[1] + a.nz.traj_base, a.K)};
-    level1_segment2(a, k, ss, idx, second, s0, s1, a.ck.ck[(size_t)seg * T + idx[0]],
-                    a.ck.ck[(size_t)seg * T + idx[1]]);
+    const int64_t slot = dchk(seg, a.ck.n_slots, b.dbg);
+    level1_segment2(a, k, ss, idx, second, s0, s1, a.ck.ck[(size_t)slot * T + idx[0]],
+                    a.ck.ck[(size_t)slot * T + idx[1]]);
 }
 
 __global__ void __launch_bounds__(kRevThreads, ABP_ADJ_MIN_BLOCKS) adjoint_reverse_kernel(AdjArgs a, SegView sv,
@@ -552,7 +557,7 @@ __global__ void __launch_bounds__(kRevThreads, ABP_ADJ_MIN_BLOCKS) adjoint_rever
     const float dtf = (float)a.nz.dt;
     const float kx = (float)(-2.0 * kPi / p.L);  // d phi / dx with the sign of d cos / d phi
     if (li >= b.tile_count[tile]) return;
-    const int64_t idx = b.tile_first[tile] + li;
+    const int64_t idx = dchk(b.tile_first[tile] + li, T, b.dbg);
     const StepStream ss = step_stream((uint64_t)idx + a.nz.traj_base, a.K);
     float4 l0 = sv.lam[idx];
     // windowed adjoint: the window ending at step (seg + 1) K starts from zero
@@ -584,7 +589,8 @@ __global__ void __launch_bounds__(kRevPairThreads, ABP_ADJ_REV_PAIR_MIN_BLOCKS) 
     const float dtf = (float)a.nz.dt;
     const float kx = (float)(-2.0 * kPi / p.L);
     const bool second = li + (int)blockDim.x < count;
-    const int64_t idx[2] = {b.tile_first[tile] + li, b.tile_first[tile] + (second ? li + (int)blockDim.x : li)};
+    const int64_t idx[2] = {dchk(b.tile_first[tile] + li, T, b.dbg),
+                            dchk(b.tile_first[tile] + (second ? li + (int)blockDim.x : li), T, b.dbg)};
     const StepStream ss[2] = {step_stream((uint64_t)idx[0] + a.nz.traj_base, a.K),
                               step_stream((uint64_t)idx[1] + a.nz.traj_base, a.K)};
     float4 l0 = sv.lam[idx[0]], l1 = sv.lam[idx[1]];
@@ -686,6 +692,7 @@ extern "C" abp_status abp_backward(abp_ctx *ctx, const double *dJ_dmean_v, doubl
 }
 
 extern "C" abp_status abp_backward_windowed(abp_ctx *ctx, const double *dJ_dmean_v, double *grad, int64_t window) {
+    const NvtxRange nvtx("abp_backward");
     if (!ctx) return ABP_EINVAL;
     if (window < 0 || (window > 0 && (ctx->cfg.checkpoint_every <= 0 || window % ctx->cfg.checkpoint_every != 0)))
         return set_err(ctx, ABP_EINVAL, "abp_backward_windowed: window must be a multiple of checkpoint_every");

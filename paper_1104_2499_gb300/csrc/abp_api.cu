@@ -602,6 +602,7 @@ const char *abp_last_error(const abp_ctx *ctx) {
 }
 
 abp_status abp_create(abp_ctx **out, const abp_config *cfg, void *cuda_stream) {
+    const NvtxRange nvtx("abp_create");
     if (!out || !cfg) return ABP_EINVAL;
     *out = nullptr;
     if (!(cfg->dt > 0.0) || !std::isfinite(cfg->dt)) return ABP_EINVAL;
@@ -656,6 +657,7 @@ void abp_destroy(abp_ctx *ctx) {
 
 abp_status abp_set_params(abp_ctx *ctx, int32_t n_sets, const abp_params *sets, const int64_t *n_traj,
                           const int64_t *n_steps) {
+    const NvtxRange nvtx("abp_set_params");
     if (!ctx) return ABP_EINVAL;
     if (n_sets < 0) return fail(ctx, ABP_EINVAL, "n_sets = %d < 0", n_sets);
     if (n_sets > 0 && (!sets || !n_traj || !n_steps)) return fail(ctx, ABP_EINVAL, "NULL parameter array");
@@ -796,6 +798,7 @@ abp_status abp_set_params(abp_ctx *ctx, int32_t n_sets, const abp_params *sets, 
 }
 
 abp_status abp_reset(abp_ctx *ctx, uint64_t seed) {
+    const NvtxRange nvtx("abp_reset");
     if (!ctx) return ABP_EINVAL;
     if (!ctx->have_batch) return fail(ctx, ABP_ESTATE, "abp_reset before abp_set_params");
     ctx->cfg.seed = seed;
@@ -988,6 +991,7 @@ abp_status send_snapshot(abp_ctx *ctx, int64_t k) {
 extern "C" {
 
 abp_status abp_integrate(abp_ctx *ctx, int64_t max_steps) {
+    const NvtxRange nvtx("abp_integrate");
     if (!ctx) return ABP_EINVAL;
     if (!ctx->have_batch) return fail(ctx, ABP_ESTATE, "abp_integrate before abp_set_params");
     const int64_t target = max_steps < 0 ? ctx->max_steps : std::min(ctx->max_steps, ctx->g + max_steps);
@@ -1012,6 +1016,7 @@ abp_status abp_integrate(abp_ctx *ctx, int64_t max_steps) {
 }
 
 abp_status abp_live(abp_ctx *ctx, double *moments, uint32_t *hist_x, uint32_t *hist_v) {
+    const NvtxRange nvtx("abp_live");
     if (!ctx) return ABP_EINVAL;
     if (!ctx->have_batch) return fail(ctx, ABP_ESTATE, "abp_live before abp_set_params");
     if (ctx->live_stream) {
@@ -1179,6 +1184,7 @@ abp_status abp_num_snapshots(const abp_ctx *ctx, int64_t *n_snap) {
 }
 
 abp_status abp_reduce(abp_ctx *ctx, double *moments, uint32_t *hist_x, uint32_t *hist_v) {
+    const NvtxRange nvtx("abp_reduce");
     if (!ctx) return ABP_EINVAL;
     if (!ctx->have_batch) return fail(ctx, ABP_ESTATE, "abp_reduce before abp_set_params");
     bool synced = false;
@@ -1244,6 +1250,7 @@ std::vector<std::pair<DevBuf *, size_t>> image_parts(abp_ctx *ctx) {
 extern "C" {
 
 abp_status abp_save(abp_ctx *ctx, void *buf, size_t *bytes) {
+    const NvtxRange nvtx("abp_save");
     if (!ctx || !bytes) return ABP_EINVAL;
     if (!ctx->have_batch) return fail(ctx, ABP_ESTATE, "abp_save before abp_set_params");
     size_t need = sizeof(SaveHeader);
@@ -1284,6 +1291,7 @@ abp_status abp_save(abp_ctx *ctx, void *buf, size_t *bytes) {
 }
 
 abp_status abp_load(abp_ctx *ctx, const void *buf, size_t bytes) {
+    const NvtxRange nvtx("abp_load");
     if (!ctx || !buf) return ABP_EINVAL;
     if (!ctx->have_batch) return fail(ctx, ABP_ESTATE, "abp_load before abp_set_params");
     SaveHeader hd{};
@@ -1322,6 +1330,7 @@ abp_status abp_load(abp_ctx *ctx, const void *buf, size_t bytes) {
 }
 
 abp_status abp_get_state(abp_ctx *ctx, double *x, double *x0, double *v, double *e, double *vbar) {
+    const NvtxRange nvtx("abp_get_state");
     if (!ctx) return ABP_EINVAL;
     if (!ctx->have_batch) return fail(ctx, ABP_ESTATE, "abp_get_state before abp_set_params");
     double *outs[5] = {x, x0, v, e, vbar};
@@ -1357,6 +1366,7 @@ abp_status abp_get_state(abp_ctx *ctx, double *x, double *x0, double *v, double 
 }
 
 abp_status abp_synchronize(abp_ctx *ctx) {
+    const NvtxRange nvtx("abp_synchronize");
     if (!ctx) return ABP_EINVAL;
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e == cudaSuccess && ctx->live_stream) e = cudaStreamSynchronize(ctx->live_stream);
@@ -1365,6 +1375,7 @@ abp_status abp_synchronize(abp_ctx *ctx) {
     e = cudaMemcpy(&status, ctx->d_status.p, sizeof(int32_t), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "status readback");
     if (status == 1) return fail(ctx, ABP_ETIMEOUT, "a bounded device-side wait expired");
+    if (status == 3) return fail(ctx, ABP_ESTATE, "an index check of the checked build failed on the device");
     if (status != 0) return fail(ctx, ABP_ESTATE, "device reported status %d", status);
     return ABP_OK;
 }

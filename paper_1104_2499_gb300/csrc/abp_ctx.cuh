@@ -122,6 +122,7 @@ struct abp_ctx {
         b.tile_first = (const int64_t *)d_tile_first.p;
         b.tile_count = (const int32_t *)d_tile_count.p;
         b.tile_set = (const int32_t *)d_tile_set.p;
+        b.dbg = (int32_t *)d_status.p;
         return b;
     }
     State state() const {

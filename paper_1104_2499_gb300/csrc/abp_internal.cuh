@@ -5,6 +5,7 @@
 #include <cstdint>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "abp.h"
 
@@ -40,7 +41,27 @@ struct Batch {
     const int64_t *tile_first;     // [n_tiles] first global trajectory id (= state index)
     const int32_t *tile_count;     // [n_tiles] trajectories in the tile (>= 1)
     const int32_t *tile_set;       // [n_tiles] the set (packed tile: its first set)
+    int32_t *dbg = nullptr;        // status word of the checked build (ABP_DEBUG_CHECKS)
 };
+
+// Checked build (-DABP_DEBUG_CHECKS=1, the stand-in for a memory checker): an
+// index outside [0, n) records status 3 in *st and is replaced by 0, so the
+// access stays inside its buffer and the launch runs to its end; the host
+// then reports ABP_ESTATE.  Release builds compile the check away.
+#ifndef ABP_DEBUG_CHECKS
+#define ABP_DEBUG_CHECKS 0
+#endif
+__device__ __forceinline__ int64_t dchk(int64_t i, int64_t n, int32_t *st) {
+#if ABP_DEBUG_CHECKS
+    if (i < 0 || i >= n) {
+        if (st) atomicCAS(st, 0, 3);
+        return 0;
+    }
+#endif
+    (void)n;
+    (void)st;
+    return i;
+}
 
 // Structure-of-arrays trajectory state.  Element type is float (fp64 = false)
 // or double (fp64 = true) for y, yacc, ylo, v, e, y0.
@@ -101,6 +122,16 @@ struct Queue {
 
 cudaError_t launch_init(const Batch &b, const State &s, const Hist &h, const Ckpt &c, const Noise &nz,
                         cudaStream_t st);
+// NVTX range over one C ABI call (nested ranges of the calling thread), for
+// profilers that trace the host timeline; without a tool attached the push
+// and pop return at once.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 // Device-side waits of a lockstep launch (the warp-specialised narrow form):
 // the context's status word, the wait limit and the test hook's held tile.
 struct WaitCtl {

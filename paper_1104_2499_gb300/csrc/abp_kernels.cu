@@ -144,8 +144,8 @@ __global__ void __launch_bounds__(kThreads) init_kernel(Batch b, State st, Hist 
         __syncthreads();
     }
     for (int li = threadIdx.x; li < count; li += blockDim.x) {
-        const int64_t t = first + li;
-        const int my_set = packed ? find_set(b, t) : set;
+        const int64_t t = dchk(first + li, b.total_traj, b.dbg);
+        const int my_set = packed ? (int)dchk(find_set(b, t), b.n_sets, b.dbg) : set;
         const abp_params p = b.params[my_set];
         const uint4 w = noise_block(kInitCounter, (uint64_t)t + nz.traj_base, nz.k0, nz.k1);
         const R y0 = (R)(w.x >> 8) * (R)0x1p-24;
@@ -562,16 +562,18 @@ __device__ __forceinline__ void run_tile(const Batch &b, const State &st, const 
                                          int64_t w1, int lane_base = 0, WsCons *wc = nullptr) {
     static_assert(!PACKED || PPT == 1, "packed tiles hold one trajectory per thread");
     static_assert(!WS || (sizeof(R) == 4 && PPT == 1), "WS: FP32, one trajectory per thread");
+    tile = (int)dchk(tile, b.n_tiles, b.dbg);
     const int64_t first = b.tile_first[tile];
     const int count = b.tile_count[tile];
-    const int set_t = b.tile_set[tile];
+    const int set_t = (int)dchk(b.tile_set[tile], b.n_sets, b.dbg);
     const int64_t N = b.set_steps[set_t];
     const int64_t n_begin = min(w0, N);
     const int64_t n_end = min(w1, N);
     if (n_begin >= n_end) return;  // uniform over the block
 
     const SV<R> s = view<R>(st);
-    const int set = PACKED ? find_set(b, first + min(lane_base + (int)threadIdx.x, count - 1)) : set_t;
+    const int set =
+        PACKED ? (int)dchk(find_set(b, first + min(lane_base + (int)threadIdx.x, count - 1)), b.n_sets, b.dbg) : set_t;
     const abp_params p = b.params[set];
     const Coef<R> k = make_coef<R>(p.q, p.c, p.d, p.gamma0, p.F0, p.D, p.h, p.L, p.asym, nz.dt);
 
@@ -582,7 +584,7 @@ __device__ __forceinline__ void run_tile(const Batch &b, const State &st, const 
     for (int q = 0; q < PPT; ++q) {
         const int li = lane_base + threadIdx.x + q * kThreads;
         act[q] = li < count;
-        idx[q] = first + (act[q] ? li : count - 1);
+        idx[q] = dchk(first + (act[q] ? li : count - 1), b.total_traj, b.dbg);
         S.y[q] = __ldcg(&s.y[idx[q]]);
         S.yacc[q] = __ldcg(&s.yacc[idx[q]]);
         S.ylo[q] = __ldcg(&s.ylo[idx[q]]);
@@ -626,7 +628,7 @@ __device__ __forceinline__ void run_tile(const Batch &b, const State &st, const 
         }
         n = seg_end;
         if (hist && (h.snap_every > 0 ? (n % h.snap_every == 0) : (n == N))) {
-            const int64_t snap = h.snap_every > 0 ? n / h.snap_every - 1 : 0;
+            const int64_t snap = dchk(h.snap_every > 0 ? n / h.snap_every - 1 : 0, h.n_snap, b.dbg);
             if constexpr (PACKED) {
                 if (act[0]) {
                     const size_t row = (size_t)snap * b.n_sets + set;
@@ -645,7 +647,7 @@ __device__ __forceinline__ void run_tile(const Batch &b, const State &st, const 
             }
         }
         if (ck.every > 0 && n % ck.every == 0 && sizeof(R) == 4) {
-            const int64_t slot = n / ck.every;
+            const int64_t slot = dchk(n / ck.every, ck.n_slots, b.dbg);
 #pragma unroll
             for (int q = 0; q < PPT; ++q)
                 if (act[q])
@@ -711,10 +713,10 @@ __device__ __forceinline__ void ws_produce(const Batch &b, const State &st, cons
     if (n_begin >= n_end) return;  // uniform over the block, as for the consumers
     const int li = lane_base + ci;
     const bool act = li < count;
-    const int64_t idx = first + (act ? li : count - 1);
+    const int64_t idx = dchk(first + (act ? li : count - 1), b.total_traj, b.dbg);
     if (!__any_sync(0xffffffffu, act)) return;  // the consumer warp does not step either
     if (tile == r.hold_tile) return;            // test hook: the consumers' waits run out
-    const int set = PACKED ? find_set(b, first + min(li, count - 1)) : set_t;
+    const int set = PACKED ? (int)dchk(find_set(b, first + min(li, count - 1)), b.n_sets, b.dbg) : set_t;
     const abp_params p = b.params[set];
     const Coef<float> k = make_coef<float>(p.q, p.c, p.d, p.gamma0, p.F0, p.D, p.h, p.L, p.asym, nz.dt);
     const StepStream ss = step_stream((uint64_t)idx + nz.traj_base, K);
@@ -759,19 +761,18 @@ __device__ __forceinline__ void ws_produce(const Batch &b, const State &st, cons
                     out[i * 32] = make_float2(nr, cs);
                 }
             }
-            mbar_arrive(&r.full[pair * kWsSlots + slot]);
-            continue;
-        }
+        } else {
 #pragma unroll
-        for (int j = 0; j < SS / 4; ++j) {
-            const uint4 wv = step_block((uint32_t)(a * (SS / 4) + j), ss, K);
-            float nr, cs, sn;
-            box_muller_f32(wv.x, wv.y, k.bm, nr, cs, sn);
-            out[(4 * j) * 32] = make_float2(nr, cs);
-            out[(4 * j + 1) * 32] = make_float2(nr, sn);
-            box_muller_f32(wv.z, wv.w, k.bm, nr, cs, sn);
-            out[(4 * j + 2) * 32] = make_float2(nr, cs);
-            out[(4 * j + 3) * 32] = make_float2(nr, sn);
+            for (int j = 0; j < SS / 4; ++j) {
+                const uint4 wv = step_block((uint32_t)(a * (SS / 4) + j), ss, K);
+                float nr, cs, sn;
+                box_muller_f32(wv.x, wv.y, k.bm, nr, cs, sn);
+                out[(4 * j) * 32] = make_float2(nr, cs);
+                out[(4 * j + 1) * 32] = make_float2(nr, sn);
+                box_muller_f32(wv.z, wv.w, k.bm, nr, cs, sn);
+                out[(4 * j + 2) * 32] = make_float2(nr, cs);
+                out[(4 * j + 3) * 32] = make_float2(nr, sn);
+            }
         }
         mbar_arrive(&r.full[pair * kWsSlots + slot]);
     }
@@ -937,14 +938,15 @@ __global__ void __launch_bounds__(kThreads) tile_reduce_kernel(Batch b, State st
     __shared__ double red[kThreads / 32][4];
     const SV<R> s = view<R>(st);
     const int tile = blockIdx.x;
-    const int set = b.tile_set[tile];
+    const int set = (int)dchk(b.tile_set[tile], b.n_sets, b.dbg);
     const int64_t n = min(g, b.set_steps[set]);
     const double L = b.params[set].L;
     const double inv_T = n > 0 ? 1.0 / ((double)n * dt) : 0.0;
     const int64_t first = b.tile_first[tile];
     const int count = b.tile_count[tile];
     double a[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int li = threadIdx.x; li < count; li += blockDim.x) traj_terms<R>(s, first + li, L, inv_T, a);
+    for (int li = threadIdx.x; li < count; li += blockDim.x)
+        traj_terms<R>(s, dchk(first + li, b.total_traj, b.dbg), L, inv_T, a);
     block_sum4(a, red);
     if (threadIdx.x == 0)
 #pragma unroll
@@ -1003,7 +1005,7 @@ __global__ void __launch_bounds__(kThreads) packed_reduce_kernel(Batch b, State 
     if ((k & ~31) >= n_packed) return;  // whole warps
     const int lane = threadIdx.x & 31;
     const bool mine = k < n_packed;
-    const int set = mine ? b.set_order[b.n_unpacked + k] : 0;
+    const int set = mine ? (int)dchk(b.set_order[b.n_unpacked + k], b.n_sets, b.dbg) : 0;
     const SV<R> s = view<R>(st);
     const int64_t n = min(g, b.set_steps[set]);
     const double L = b.params[set].L;
@@ -1012,7 +1014,7 @@ __global__ void __launch_bounds__(kThreads) packed_reduce_kernel(Batch b, State 
     const int m = (int)(t1 - t0);
     double a[4] = {0.0, 0.0, 0.0, 0.0};
     if (m <= 2)
-        for (int64_t t = t0; t < t1; ++t) traj_terms<R>(s, t, L, inv_T, a);
+        for (int64_t t = t0; t < t1; ++t) traj_terms<R>(s, dchk(t, b.total_traj, b.dbg), L, inv_T, a);
     unsigned big = __ballot_sync(0xffffffffu, m > 2);
     while (big) {
         const int src = __ffs(big) - 1;
@@ -1061,8 +1063,8 @@ __global__ void __launch_bounds__(kThreads) get_state_kernel(Batch b, State st, 
     const int64_t first = b.tile_first[tile];
     const int count = b.tile_count[tile];
     for (int li = threadIdx.x; li < count; li += blockDim.x) {
-        const int64_t t = first + li;
-        const int set = packed ? find_set(b, t) : b.tile_set[tile];
+        const int64_t t = dchk(first + li, b.total_traj, b.dbg);
+        const int set = (int)dchk(packed ? find_set(b, t) : b.tile_set[tile], b.n_sets, b.dbg);
         const int64_t n = min(g, b.set_steps[set]);
         const double L = b.params[set].L;
         const double x0t = L * (double)s.y0[t];
