@@ -40,9 +40,10 @@
  *   - Returns ABP_OK or an error code; the message of the last error of a
  *     context is available from abp_last_error().  Nothing is printed.
  *   - Work is enqueued asynchronously on the context's CUDA stream; a device
- *     side failure recorded by a kernel (for example an expired bounded wait)
- *     surfaces as ABP_ETIMEOUT / ABP_ESTATE from abp_synchronize() or from the
- *     next call that synchronises.
+ *     side failure recorded by a kernel (an expired bounded wait, or in the
+ *     checked build, compiled with ABP_DEBUG_CHECKS=1, an index outside its
+ *     buffer) surfaces as ABP_ETIMEOUT / ABP_ESTATE from abp_synchronize() or
+ *     from the next call that synchronises.
  *   - Output pointers documented as "host or device" may point to either; the
  *     library inspects them with cudaPointerGetAttributes and copies device ->
  *     host itself when they are host memory (pinned or pageable), in which case
