@@ -500,8 +500,13 @@ bool plan_tiles(int32_t n_sets, const int64_t *n_traj, const int64_t *n_steps, i
 // The work queue is chosen only when predicted faster than lockstep by more
 // than this fraction (about the run-to-run spread of the trial): between
 // near-equal candidates the lockstep schedule, which has no device-side waits,
-// is kept, and the choice stays the same from one machine to the next.
-constexpr double kQueueMargin = 0.02;
+// is kept, and the choice stays the same from one machine to the next.  (At 1%
+// the measured choices were the same: where the work queue measures 2% faster
+// -- the uneven batch, xorshift noise -- the model itself predicts lockstep.)
+#ifndef ABP_QUEUE_MARGIN
+#define ABP_QUEUE_MARGIN 0.02
+#endif
+constexpr double kQueueMargin = ABP_QUEUE_MARGIN;
 
 void autotune(abp_ctx *ctx) {
     const int want_sched = ctx->cfg.schedule;          // 0 auto, 1 lockstep, 2 work queue
