@@ -285,7 +285,8 @@ ABP_API abp_status abp_tiles(const abp_ctx *ctx, int32_t *n_tiles, int32_t *n_pa
  * schedule / particles_per_thread out of range gives ABP_EINVAL.
  * abp_plan_efficiency: the fraction of the launch capacity (resident_blocks
  * blocks of 256 * particles_per_thread trajectories) the batch keeps busy, in
- * particle-steps, which the autotuner divides each candidate's trial time by;
+ * particle-steps; the autotuner predicts a candidate's time on a batch as its
+ * trial time x the trial batch's fraction / the batch's fraction;
  * steps_per_launch 0 = the default lockstep window. */
 ABP_API abp_status abp_plan(int32_t n_sets, const int64_t *n_traj, const int64_t *n_steps, int32_t schedule,
                             int32_t particles_per_thread, int32_t checkpoints, int32_t sm_count, int32_t *n_tiles,
