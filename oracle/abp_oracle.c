@@ -232,7 +232,9 @@ static void tangent_step(const or_params *p, double dt, double z, const double s
     const double dx = t[0], dv = t[1], de = t[2];
     const double dD = dth[0], dq = dth[1], dc = dth[2], dd = dth[3], dg = dth[4], da = dth[5];
     const double sigma = sqrt(2.0 * p->D * dt);
-    const double dsigma = (p->D > 0.0) ? dD * sigma / (2.0 * p->D) : 0.0;
+    /* sigma grows like sqrt(D): at D = 0 its derivative in D does not exist, and
+     * the D-direction of the tangent is undefined (NaN) from the first noise term on. */
+    const double dsigma = (p->D > 0.0) ? dD * sigma / (2.0 * p->D) : (dD != 0.0 ? NAN : 0.0);
     const double de_rate = dq - dc * e - p->c * de - dd * e * v * v - p->d * de * v * v
                            - 2.0 * p->d * e * v * dv;
     const double dv_rate = dd * e * v + p->d * de * v + p->d * e * dv - dg * v - p->gamma0 * dv
@@ -392,8 +394,8 @@ static void *run_range(void *arg)
             /* v0 = sqrt(D) z depends on D in mode 1. */
             for (int j = 0; j < 6; ++j)
                 t[j][0] = t[j][1] = t[j][2] = 0.0;
-            if (a->v0_mode == 1 && p->D > 0.0)
-                t[0][1] = s[1] / (2.0 * p->D);
+            if (a->v0_mode == 1)
+                t[0][1] = p->D > 0.0 ? s[1] / (2.0 * p->D) : NAN;
         }
         double vsum = 0.0;
         int64_t snap = 0;

@@ -257,6 +257,32 @@ def test_free_passive_ou_variance_and_msd():
     assert abs(msd - var_dx) < 4 * var_dx * math.sqrt(2.0 / M)
     # long-time diffusion: D_eff -> D / gamma0^2 (Einstein), to O(1/(gamma0 T))
     assert r["d_eff"] == pytest.approx(p["D"] / p["gamma0"] ** 2, rel=0.08)
+    # the moments the oracle derives from its four ensemble sums, against the same closed
+    # form: E[dx] = 0, so msd -> Var(dx); vbar = dx / (N dt), so the standard error of the
+    # mean velocity is sqrt(Var(dx) / M) / (N dt).  The sample variance of M Gaussian values
+    # has relative spread sqrt(2 / (M - 1)), its square root half of that.
+    T = N * dt
+    assert abs(r["msd"] - var_dx) < 4 * var_dx * math.sqrt(2.0 / M)
+    se_exact = math.sqrt(var_dx / M) / T
+    assert abs(r["se_v"] - se_exact) < 4 * se_exact * math.sqrt(0.5 / (M - 1))
+    assert abs(r["mean_v"]) < 4 * se_exact
+    assert r["d_eff"] == pytest.approx((r["msd"] - (r["sums"][2] / M) ** 2) / (2 * T), rel=1e-12)
+
+
+def test_standard_error_of_a_two_point_ensemble():
+    # brute force on the smallest ensemble with a standard error: two trajectories whose
+    # time averages are a and b have mean (a + b) / 2 and standard error |a - b| / 2
+    # (sample variance (a - b)^2 / 2 over M = 2), whatever the dynamics
+    r = O.run_set(P(D=0.4), seed=15, dt=1e-3, n_traj=2, n_steps=300, want_states=True)
+    a, b = r["vbar"]
+    assert r["mean_v"] == pytest.approx((a + b) / 2, rel=1e-12)
+    assert r["se_v"] == pytest.approx(abs(a - b) / 2, rel=1e-12)
+    dx = r["x"] - r["x0"]
+    assert r["msd"] == pytest.approx((dx[0] ** 2 + dx[1] ** 2) / 2, rel=1e-12)
+    assert r["d_eff"] == pytest.approx(((dx[0] - dx[1]) / 2) ** 2 / (2 * 300 * 1e-3), rel=1e-9)
+    # one trajectory has no standard error, an empty ensemble no moments
+    r1 = O.run_set(P(D=0.4), seed=15, dt=1e-3, n_traj=1, n_steps=300)
+    assert r1["se_v"] == 0.0 and r1["mean_v"] == pytest.approx(a, rel=1e-12)
 
 
 def test_initial_conditions():
@@ -321,6 +347,24 @@ def test_tangent_linear_matches_central_differences():
         dn = O.run_set(dict(base, **{name: base[name] - h}), **kw)["mean_v"]
         fd = (up - dn) / (2 * h)
         assert g[j] == pytest.approx(fd, rel=2e-5, abs=1e-9), name
+
+
+def test_tangent_in_D_is_undefined_at_zero_noise():
+    # sigma = sqrt(2 D dt) has no derivative at D = 0: the D-component is NaN there (for any
+    # run of two or more steps, or a random initial velocity); the other five components
+    # are those of the deterministic model, checked against central differences
+    base = P(D=0.0, F0=0.1)
+    for v0_mode, n_steps in ((0, 400), (1, 400), (1, 1)):
+        kw = dict(seed=14, dt=1e-3, n_traj=8, n_steps=n_steps, v0_mode=v0_mode)
+        g = O.run_set(base, want_grad=True, **kw)["grad"]
+        assert math.isnan(g[0]), (v0_mode, n_steps)
+        for j, name in enumerate(O.GRAD_PARAMS[1:], start=1):
+            h = 1e-4 * abs(base[name])
+            up = O.run_set(dict(base, **{name: base[name] + h}), **kw)["mean_v"]
+            dn = O.run_set(dict(base, **{name: base[name] - h}), **kw)["mean_v"]
+            assert g[j] == pytest.approx((up - dn) / (2 * h), rel=2e-5, abs=1e-9), (v0_mode, name)
+    # no step taken: the time average is defined as 0, and so is every derivative
+    assert np.all(O.run_set(base, want_grad=True, seed=14, dt=1e-3, n_traj=4, n_steps=0)["grad"] == 0.0)
 
 
 # --------------------------------------------------------------------------- bookkeeping
