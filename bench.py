@@ -641,7 +641,7 @@ def main():
         A.abp_reduce(ens.ctx, mom, hx, None)
         if dist is not None:
             with torch.cuda.stream(stream):
-                shard.all_reduce_sums_(mom, dist.all_reduce)
+                shard.all_reduce_sums_(mom, dist.all_reduce, [m * world for m in w.n_traj], w.n_steps, w.dt, stream)
 
     for _ in range(args.warmup):
         with torch.cuda.stream(stream):

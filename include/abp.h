@@ -47,7 +47,9 @@
  *   - Output pointers documented as "host or device" may point to either; the
  *     library inspects them with cudaPointerGetAttributes and copies device ->
  *     host itself when they are host memory (pinned or pageable), in which case
- *     the call returns after the copy has completed.
+ *     the call returns after the copy has completed.  Device memory must belong
+ *     to the context's device (or be managed memory); another GPU's memory is
+ *     rejected with ABP_EINVAL, since kernels may write the outputs directly.
  *   - The context owns every device buffer it allocates (state, histograms,
  *     checkpoints, scratch); callers own the buffers they pass in.
  *   - Calls on one context must not run concurrently from several host threads.
@@ -344,19 +346,48 @@ ABP_API abp_status abp_xorshift(uint64_t seed, uint64_t traj, int64_t count, uin
  * until the process exits.  Limits: 0 <= n_traj <= ABP_NOALLOC_MAX_TRAJ, FP32
  * state only (state_fp64 = 0), no checkpoints (checkpoint_every = 0); anything
  * else returns ABP_EINVAL with a message in err (err_len bytes, may be NULL).
- * Outputs, all DEVICE memory owned by the caller: moments [8] doubles as in
- * abp_reduce; hist_x [n_snap][hist_x_bins] and hist_v [n_snap][hist_v_bins + 2]
- * uint32 (required when their bins are > 0, zeroed by the call).
+ * It runs the lockstep schedule (one block per tile, cfg->particles_per_thread
+ * trajectories per thread, 0 meaning 1; never the narrow small-batch launch) in
+ * launches of cfg->steps_per_launch steps (0: one launch); cfg->schedule must be
+ * 0 or 1 (the work queue needs per-tile counters this call has no room for).
+ * Outputs, all memory of the CURRENT device owned by the caller (host memory or
+ * another GPU's memory is rejected): moments [8] doubles as in abp_reduce;
+ * hist_x [n_snap][hist_x_bins] and hist_v [n_snap][hist_v_bins + 2] uint32
+ * (required when their bins are > 0, zeroed by the call), n_snap as in
+ * abp_num_snapshots for one set of n_steps steps.  The caller sizes them: the
+ * call cannot see their extent.
  * The call only enqueues work on cuda_stream; results are ready when the stream
  * is.  The first call on a device looks up the array's device address (with
- * that device current); make that first call before any stream capture.  All
- * calls share the one array, so calls whose work overlaps on the GPU (other
+ * that device current) and keeps it for the life of the process; make that
+ * first call before any stream capture, and do not use the call again on a
+ * device after cudaDeviceReset (the array may then live at another address).
+ * All calls share the one array, so calls whose work overlaps on the GPU (other
  * streams, other host threads) race and must be serialised by the caller. */
 #define ABP_NOALLOC_MAX_TRAJ 65536
 #define ABP_NOALLOC_SCRATCH_BYTES 1848064
 ABP_API abp_status abp_run_set_noalloc(const abp_params *params, const abp_config *cfg, int64_t n_traj,
                                        int64_t n_steps, double *moments, uint32_t *hist_x, uint32_t *hist_v,
                                        void *cuda_stream, char *err, size_t err_len);
+
+/* Moments of an ensemble integrated in shards.  A batch may be split into
+ * trajectory ranges run by several processes (one GPU each, abp_config.traj_base =
+ * the global id of each range's first trajectory).  The averages of Sec. 2 over
+ * noise realisations are sums over trajectories divided by their number, so adding
+ * the per-set sums (columns 4..7 of abp_reduce) of all shards gives the sums of the
+ * whole ensemble; this call then forms its moments:
+ *   moments: [n_sets][8] doubles, host or device memory, read and written in place;
+ *     on entry columns 4..7 hold the combined sums, on return columns 0..3 hold
+ *     mean_v, se_v, msd and d_eff as abp_reduce defines them (bitwise the values
+ *     abp_reduce gives for the same sums);
+ *   n_traj, n_steps: host arrays of n_sets values -- the trajectories of set s in
+ *     all shards together and the steps they have run; dt: the time step.
+ * Device memory (of the current device) is processed by a kernel on cuda_stream
+ * (the call returns at once; results are ready with the stream); host memory is
+ * processed before the call returns and needs no GPU.  No context is needed.
+ * ABP_EINVAL for n_sets < 0, NULL arrays, negative counts, dt not finite and > 0,
+ * or moments in another GPU's memory. */
+ABP_API abp_status abp_combine_moments(int32_t n_sets, double *moments, const int64_t *n_traj,
+                                       const int64_t *n_steps, double dt, void *cuda_stream);
 
 /* Library version string. */
 ABP_API const char *abp_version(void);

@@ -137,6 +137,11 @@ def lib():
         L.abp_normals.restype = st
         L.abp_version.argtypes = []
         L.abp_version.restype = C.c_char_p
+        L.abp_combine_moments.argtypes = [C.c_int32, _VP, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_double, _VP]
+        L.abp_combine_moments.restype = st
+        L.abp_run_set_noalloc.argtypes = [C.POINTER(abp_params), C.POINTER(abp_config), C.c_int64, C.c_int64, _VP,
+                                          _VP, _VP, _VP, C.c_char_p, C.c_size_t]
+        L.abp_run_set_noalloc.restype = st
         _lib = L
         return L
 
@@ -334,6 +339,23 @@ def abp_version() -> str:
     return lib().abp_version().decode()
 
 
+def abp_combine_moments(moments, n_traj, n_steps, dt: float, stream=None):
+    """In place: columns 0..3 of ``moments`` [n_sets, 8] (float64, host array / tensor or device
+    tensor) from the combined per-set sums in its columns 4..7, for n_traj[s] trajectories in all
+    after n_steps[s] steps.  Host memory is processed at once, device memory on ``stream``."""
+    shape = tuple(moments.shape)
+    dtype_ok = (moments.dtype == np.float64) if isinstance(moments, np.ndarray) else (str(moments.dtype) == "torch.float64")
+    if len(shape) != 2 or shape[1] != 8 or not dtype_ok:
+        raise ValueError("moments must be a float64 array of shape [n_sets, 8], got %s %s" % (moments.dtype, shape))
+    n = shape[0]
+    if len(n_traj) != n or len(n_steps) != n:
+        raise ValueError("n_traj and n_steps need one value per set")
+    M = (C.c_int64 * max(n, 1))(*[int(v) for v in n_traj])
+    N = (C.c_int64 * max(n, 1))(*[int(v) for v in n_steps])
+    _check(lib().abp_combine_moments(n, _ptr(moments), M, N, float(dt), _stream_ptr(stream)),
+           what="abp_combine_moments rejected its arguments")
+
+
 # ----------------------------------------------------------------------- convenience
 
 def make_config(w: "W.Workload", *, state_fp64: bool = False, particles_per_thread: int = 0,
@@ -508,20 +530,41 @@ class MeanVelocity:
         return cls._fn.apply(theta, w, kw)
 
 
+def noalloc_snapshots(cfg: abp_config, n_steps: int) -> int:
+    """Snapshot rows the allocation-free entry point writes for one set of n_steps steps."""
+    if cfg.hist_x_bins <= 0 and cfg.hist_v_bins <= 0:
+        return 0
+    return int(n_steps) // int(cfg.snapshot_every) if cfg.snapshot_every > 0 else 1
+
+
 def abp_run_set_noalloc(params: dict, cfg: abp_config, n_traj: int, n_steps: int, moments, hist_x=None, hist_v=None,
                         stream=None):
     """One parameter set integrated and reduced by the allocation-free entry point; the
-    outputs are caller-owned device tensors (moments [8] float64, histograms int32)."""
-    L = lib()
-    f = L.abp_run_set_noalloc
-    f.argtypes = [C.POINTER(abp_params), C.POINTER(abp_config), C.c_int64, C.c_int64, _VP, _VP, _VP, _VP,
-                  C.c_char_p, C.c_size_t]
-    f.restype = C.c_int
+    outputs are caller-owned tensors on the current CUDA device (moments >= 8 float64,
+    histograms of a 4-byte integer type and at least n_snap x bins elements).  The C side
+    cannot see the extent of these buffers, so they are checked here before the call."""
+    import torch
+
+    n_snap = noalloc_snapshots(cfg, n_steps)
+    if moments is None or moments.dtype != torch.float64 or moments.numel() < 8:
+        raise ValueError("moments must be a float64 tensor of at least 8 elements")
+    need = (("hist_x", hist_x, cfg.hist_x_bins), ("hist_v", hist_v, cfg.hist_v_bins + 2 if cfg.hist_v_bins else 0))
+    for name, t, bins in need:
+        if bins <= 0:
+            continue
+        if t is None or t.dtype not in (torch.int32, getattr(torch, "uint32", torch.int32)):
+            raise ValueError("%s must be an int32 tensor when its bins are > 0" % name)
+        if t.numel() < n_snap * bins:
+            raise ValueError("%s holds %d elements, %d snapshots x %d bins needed" % (name, t.numel(), n_snap, bins))
+    dev = torch.cuda.current_device() if torch.cuda.is_available() else None
+    for name, t in (("moments", moments), ("hist_x", hist_x), ("hist_v", hist_v)):
+        if t is not None and (t.device.type != "cuda" or t.device.index != dev):
+            raise ValueError("%s must be on the current CUDA device (cuda:%s), not %s" % (name, dev, t.device))
     p = abp_params()
     for k in W.PARAM_NAMES:
         setattr(p, k, float(params[k]))
     err = C.create_string_buffer(512)
-    st = f(C.byref(p), C.byref(cfg), int(n_traj), int(n_steps), _ptr(moments), _ptr(hist_x), _ptr(hist_v),
-           _stream_ptr(stream), err, 512)
+    st = lib().abp_run_set_noalloc(C.byref(p), C.byref(cfg), int(n_traj), int(n_steps), _ptr(moments),
+                                   _ptr(hist_x), _ptr(hist_v), _stream_ptr(stream), err, 512)
     if st != ABP_OK:
         raise AbpError(st, err.value.decode())

@@ -664,15 +664,6 @@ __global__ void __launch_bounds__(kThreads) adjoint_set_kernel(Batch b, const do
         for (int j = 0; j < 6; ++j) grad[(size_t)set * 6 + j] = a[j];
 }
 
-bool device_ptr(const void *p) {
-    cudaPointerAttributes at;
-    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
-}
-
 abp_status set_err(abp_ctx *ctx, abp_status st, const char *msg, cudaError_t e = cudaSuccess) {
     ctx->err = msg;
     if (e != cudaSuccess) {
@@ -697,6 +688,8 @@ extern "C" abp_status abp_backward_windowed(abp_ctx *ctx, const double *dJ_dmean
     if (window < 0 || (window > 0 && (ctx->cfg.checkpoint_every <= 0 || window % ctx->cfg.checkpoint_every != 0)))
         return set_err(ctx, ABP_EINVAL, "abp_backward_windowed: window must be a multiple of checkpoint_every");
     if (!grad) return set_err(ctx, ABP_EINVAL, "abp_backward: grad is NULL");
+    const PtrKind kg = ptr_kind(grad, ctx->device);
+    if (kg == PtrKind::OtherDevice) return set_err(ctx, ABP_EINVAL, "abp_backward: grad on another GPU");
     if (!ctx->have_batch) return set_err(ctx, ABP_ESTATE, "abp_backward before abp_set_params");
     if (ctx->cfg.checkpoint_every <= 0)
         return set_err(ctx, ABP_ESTATE, "abp_backward needs checkpoint_every > 0 during abp_integrate");
@@ -738,7 +731,9 @@ extern "C" abp_status abp_backward_windowed(abp_ctx *ctx, const double *dJ_dmean
     cudaError_t e = cudaSuccess;
     const double *w = nullptr;
     if (dJ_dmean_v) {
-        if (device_ptr(dJ_dmean_v)) {
+        const PtrKind kw = ptr_kind(dJ_dmean_v, ctx->device);
+        if (kw == PtrKind::OtherDevice) return set_err(ctx, ABP_EINVAL, "abp_backward: weights on another GPU");
+        if (kw == PtrKind::Device) {
             w = dJ_dmean_v;
         } else {
             e = cudaMemcpyAsync(wdev, dJ_dmean_v, sizeof(double) * ctx->n_sets, cudaMemcpyHostToDevice, s);
@@ -823,7 +818,7 @@ extern "C" abp_status abp_backward_windowed(abp_ctx *ctx, const double *dJ_dmean
     e = cudaGetLastError();
     if (e != cudaSuccess) return set_err(ctx, ABP_ECUDA, "abp_backward: launch", e);
     const size_t out_bytes = sizeof(double) * 6 * (size_t)ctx->n_sets;
-    if (device_ptr(grad)) {
+    if (kg == PtrKind::Device) {
         e = cudaMemcpyAsync(grad, gdev, out_bytes, cudaMemcpyDeviceToDevice, s);
     } else {
         e = cudaMemcpyAsync(grad, gdev, out_bytes, cudaMemcpyDeviceToHost, s);

@@ -64,17 +64,6 @@ abp_status alloc(abp_ctx *ctx, DevBuf &b, size_t bytes, const char *what) {
     return ABP_OK;
 }
 
-// True if ptr is device-accessible memory (device or managed); false for host
-// memory (pinned or pageable).
-bool is_device_ptr(const void *ptr) {
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
 bool finite_params(const abp_params &p) {
     const double v[9] = {p.q, p.c, p.d, p.gamma0, p.F0, p.D, p.h, p.L, p.asym};
     for (double x : v)
@@ -98,7 +87,11 @@ int64_t default_steps_per_launch(const abp_ctx *ctx) { return default_window(ctx
 // Copy n bytes of a device buffer to a caller pointer that may be host or device.
 abp_status deliver(abp_ctx *ctx, void *dst, const void *src, size_t n, bool *synced) {
     if (!dst || n == 0) return ABP_OK;
-    if (is_device_ptr(dst)) {
+    const PtrKind k = ptr_kind(dst, ctx->device);
+    if (k == PtrKind::OtherDevice)
+        return fail(ctx, ABP_EINVAL, "an output points to another GPU's memory (the context runs on device %d)",
+                    ctx->device);
+    if (k == PtrKind::Device) {
         ABP_CUDA(ctx, cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToDevice, ctx->stream), "copy to device output");
     } else {
         ABP_CUDA(ctx, cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToHost, ctx->stream), "copy to host output");
@@ -1279,7 +1272,9 @@ abp_status abp_save(abp_ctx *ctx, void *buf, size_t *bytes) {
     hd.hx_bytes = ctx->d_hx.bytes;
     hd.hv_bytes = ctx->d_hv.bytes;
     hd.signature = batch_signature(ctx);
-    const bool dev = is_device_ptr(buf);
+    const PtrKind kind = ptr_kind(buf, ctx->device);
+    if (kind == PtrKind::OtherDevice) return fail(ctx, ABP_EINVAL, "abp_save: buffer on another GPU");
+    const bool dev = kind == PtrKind::Device;
     cudaStream_t s = ctx->stream;
     cudaError_t e = cudaMemcpyAsync(buf, &hd, sizeof(hd), dev ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, s);
     size_t off = sizeof(hd);
@@ -1301,7 +1296,9 @@ abp_status abp_load(abp_ctx *ctx, const void *buf, size_t bytes) {
     if (!ctx->have_batch) return fail(ctx, ABP_ESTATE, "abp_load before abp_set_params");
     SaveHeader hd{};
     if (bytes < sizeof(hd)) return fail(ctx, ABP_EINVAL, "abp_load: image too small");
-    const bool dev = is_device_ptr(buf);
+    const PtrKind kind = ptr_kind(buf, ctx->device);
+    if (kind == PtrKind::OtherDevice) return fail(ctx, ABP_EINVAL, "abp_load: image on another GPU");
+    const bool dev = kind == PtrKind::Device;
     cudaStream_t s = ctx->stream;
     cudaError_t e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaMemcpy(&hd, buf, sizeof(hd), dev ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost);
@@ -1341,8 +1338,13 @@ abp_status abp_get_state(abp_ctx *ctx, double *x, double *x0, double *v, double 
     double *outs[5] = {x, x0, v, e, vbar};
     const size_t n = (size_t)ctx->total_traj;
     bool all_dev = true;
-    for (double *p : outs)
-        if (p && !is_device_ptr(p)) all_dev = false;
+    for (double *p : outs) {
+        if (!p) continue;
+        const PtrKind k = ptr_kind(p, ctx->device);
+        if (k == PtrKind::OtherDevice)
+            return fail(ctx, ABP_EINVAL, "abp_get_state: an output points to another GPU's memory");
+        if (k != PtrKind::Device) all_dev = false;
+    }
     if (all_dev) {
         cudaError_t er = launch_get_state(ctx->batch(), ctx->state(), ctx->cfg.dt, ctx->g, x, x0, v, e, vbar, ctx->stream);
         ctx->launches += ctx->n_tiles > 0 ? 1 : 0;
@@ -1391,7 +1393,10 @@ abp_status abp_philox(uint64_t seed, const uint64_t *traj, const uint64_t *m, in
                       void *cuda_stream) {
     if (n < 0) return ABP_EINVAL;
     if (n == 0) return ABP_OK;
-    if (!traj || !m || !out || !is_device_ptr(traj) || !is_device_ptr(m) || !is_device_ptr(out)) return ABP_EINVAL;
+    const int dev = current_device();
+    if (!traj || !m || !out || ptr_kind(traj, dev) != PtrKind::Device || ptr_kind(m, dev) != PtrKind::Device ||
+        ptr_kind(out, dev) != PtrKind::Device)
+        return ABP_EINVAL;
     cudaError_t e = launch_philox((uint32_t)seed, (uint32_t)(seed >> 32), traj, m, n, out, (cudaStream_t)cuda_stream);
     return e == cudaSuccess ? ABP_OK : ABP_ECUDA;
 }
@@ -1399,7 +1404,7 @@ abp_status abp_philox(uint64_t seed, const uint64_t *traj, const uint64_t *m, in
 abp_status abp_normals(uint64_t seed, uint64_t traj, uint64_t n0, int64_t count, float *out, void *cuda_stream) {
     if (count < 0) return ABP_EINVAL;
     if (count == 0) return ABP_OK;
-    if (!out || !is_device_ptr(out)) return ABP_EINVAL;
+    if (!out || ptr_kind(out, current_device()) != PtrKind::Device) return ABP_EINVAL;
     cudaError_t e = launch_normals((uint32_t)seed, (uint32_t)(seed >> 32), traj, n0, count, out,
                                    (cudaStream_t)cuda_stream);
     return e == cudaSuccess ? ABP_OK : ABP_ECUDA;
@@ -1408,9 +1413,31 @@ abp_status abp_normals(uint64_t seed, uint64_t traj, uint64_t n0, int64_t count,
 abp_status abp_xorshift(uint64_t seed, uint64_t traj, int64_t count, uint32_t *out, void *cuda_stream) {
     if (count < 0) return ABP_EINVAL;
     if (count == 0) return ABP_OK;
-    if (!out || !is_device_ptr(out)) return ABP_EINVAL;
+    if (!out || ptr_kind(out, current_device()) != PtrKind::Device) return ABP_EINVAL;
     cudaError_t e = launch_xorshift((uint32_t)seed, (uint32_t)(seed >> 32), traj, count, out, (cudaStream_t)cuda_stream);
     return e == cudaSuccess ? ABP_OK : ABP_ECUDA;
+}
+
+abp_status abp_combine_moments(int32_t n_sets, double *moments, const int64_t *n_traj, const int64_t *n_steps,
+                               double dt, void *cuda_stream) {
+    const NvtxRange nvtx("abp_combine_moments");
+    if (n_sets < 0 || !(dt > 0.0) || !std::isfinite(dt)) return ABP_EINVAL;
+    if (n_sets == 0) return ABP_OK;
+    if (!moments || !n_traj || !n_steps) return ABP_EINVAL;
+    for (int32_t i = 0; i < n_sets; ++i)
+        if (n_traj[i] < 0 || n_steps[i] < 0) return ABP_EINVAL;
+    const PtrKind k = ptr_kind(moments, current_device());
+    if (k == PtrKind::OtherDevice) return ABP_EINVAL;
+    if (k == PtrKind::Device)
+        return launch_combine_moments(n_sets, moments, n_traj, n_steps, dt, (cudaStream_t)cuda_stream) == cudaSuccess
+                   ? ABP_OK
+                   : ABP_ECUDA;
+    for (int32_t i = 0; i < n_sets; ++i) {
+        double *row = moments + (size_t)i * 8;
+        const double a[4] = {row[4], row[5], row[6], row[7]};
+        moments_from_sums(row, a, n_traj[i], n_steps[i], dt);
+    }
+    return ABP_OK;
 }
 
 }  // extern "C"

@@ -120,6 +120,70 @@ struct Queue {
     int64_t wait_limit_ns;
 };
 
+// Derived moments of one set (Sec. 2: averages over noise realisations) from its four
+// FP64 sums a = (sum vbar, sum vbar^2, sum dx, sum dx^2) over M trajectories of n steps
+// of length dt, into o[8] in the layout of abp_reduce.  Host and device run the same
+// correctly rounded operations in the same order (no fused multiply-add on either side),
+// so a set gives the same bits whether its moments are formed by a reduction kernel, by
+// the combining kernel or on the host.
+__host__ __device__ inline double mom_mul(double x, double y) {
+#ifdef __CUDA_ARCH__
+    return __dmul_rn(x, y);
+#else
+    return x * y;
+#endif
+}
+__host__ __device__ inline double mom_sub(double x, double y) {
+#ifdef __CUDA_ARCH__
+    return __dsub_rn(x, y);
+#else
+    return x - y;
+#endif
+}
+__host__ __device__ inline void moments_from_sums(double *o, const double *a, int64_t M, int64_t n, double dt) {
+    const double Md = (double)M;
+    const double mean_v = M > 0 ? a[0] / Md : 0.0;
+    const double var_v = M > 1 ? mom_sub(a[1], mom_mul(mom_mul(Md, mean_v), mean_v)) / (Md - 1.0) : 0.0;
+    const double msd = M > 0 ? a[3] / Md : 0.0;
+    const double mdx = M > 0 ? a[2] / Md : 0.0;
+    const double T = mom_mul((double)n, dt);
+    o[0] = mean_v;
+    o[1] = M > 0 ? sqrt((var_v > 0.0 ? var_v : 0.0) / Md) : 0.0;
+    o[2] = msd;
+    o[3] = T > 0.0 ? mom_sub(msd, mom_mul(mdx, mdx)) / mom_mul(2.0, T) : 0.0;
+    for (int j = 0; j < 4; ++j) o[4 + j] = a[j];
+}
+
+// Where a caller's pointer points, seen from device `dev`: host memory (pageable
+// or page-locked; the library copies to and from it), memory that kernels on `dev`
+// may read and write (that device's own memory, or managed memory), or another
+// GPU's memory, which the entry points reject: a kernel storing to it would write
+// to a peer device or fault.
+enum class PtrKind { Host, Device, OtherDevice };
+inline PtrKind ptr_kind(const void *p, int dev) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return PtrKind::Host;
+    }
+    if (a.type == cudaMemoryTypeManaged) return PtrKind::Device;
+    if (a.type != cudaMemoryTypeDevice) return PtrKind::Host;
+    return a.device == dev ? PtrKind::Device : PtrKind::OtherDevice;
+}
+inline int current_device() {
+    int d = -1;
+    if (cudaGetDevice(&d) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    return d;
+}
+
+// Columns 0..3 of moments [n][8] from its columns 4..7, set i having M[i]
+// trajectories of N[i] steps (host arrays, copied into the launches).
+cudaError_t launch_combine_moments(int32_t n, double *moments, const int64_t *M, const int64_t *N, double dt,
+                                   cudaStream_t st);
+
 cudaError_t launch_init(const Batch &b, const State &s, const Hist &h, const Ckpt &c, const Noise &nz,
                         cudaStream_t st);
 // NVTX range over one C ABI call (nested ranges of the calling thread), for

@@ -953,20 +953,20 @@ __global__ void __launch_bounds__(kThreads) tile_reduce_kernel(Batch b, State st
         for (int j = 0; j < 4; ++j) partials[(size_t)tile * 4 + j] = a[j];
 }
 
-// Derived moments of a set from its four FP64 sums over M trajectories of n steps.
-__device__ __forceinline__ void write_moments(double *o, const double (&a)[4], int64_t M, int64_t n, double dt) {
-    const double Md = (double)M;
-    const double mean_v = M > 0 ? a[0] / Md : 0.0;
-    const double var_v = M > 1 ? (a[1] - Md * mean_v * mean_v) / (Md - 1.0) : 0.0;
-    const double msd = M > 0 ? a[3] / Md : 0.0;
-    const double mdx = M > 0 ? a[2] / Md : 0.0;
-    const double T = (double)n * dt;
-    o[0] = mean_v;
-    o[1] = M > 0 ? sqrt(fmax(var_v, 0.0) / Md) : 0.0;
-    o[2] = msd;
-    o[3] = T > 0.0 ? (msd - mdx * mdx) / (2.0 * T) : 0.0;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) o[4 + j] = a[j];
+// Sets of a combined ensemble: columns 0..3 of their moments rows recomputed from the
+// sums in columns 4..7 (one thread per set; the sizes travel in the kernel arguments).
+constexpr int kCombineChunk = 128;
+struct CombineSizes {
+    int64_t M[kCombineChunk], N[kCombineChunk];
+};
+
+__global__ void __launch_bounds__(kCombineChunk) combine_moments_kernel(double *moments, int32_t n, CombineSizes sz,
+                                                                         double dt) {
+    const int i = threadIdx.x;
+    if (i >= n) return;
+    double *row = moments + (size_t)i * 8;
+    const double a[4] = {row[4], row[5], row[6], row[7]};
+    moments_from_sums(row, a, sz.M[i], sz.N[i], dt);
 }
 
 // Per set in one-set tiles: fixed-order sum of its tiles' partials and the
@@ -985,7 +985,7 @@ __global__ void __launch_bounds__(kThreads) set_reduce_kernel(Batch b, double dt
         for (int j = 0; j < 4; ++j) a[j] += partials[(size_t)t * 4 + j];
     for (int t = t0; t < t1; ++t) M += b.tile_count[t];
     block_sum4(a, red);
-    if (threadIdx.x == 0) write_moments(moments + (size_t)set * 8, a, M, n, dt);
+    if (threadIdx.x == 0) moments_from_sums(moments + (size_t)set * 8, a, M, n, dt);
 }
 
 // Sets in packed tiles (fewer than kThreads trajectories each): one lane per
@@ -1051,7 +1051,7 @@ __global__ void __launch_bounds__(kThreads) packed_reduce_kernel(Batch b, State 
             if (lane == src) a[j] = r;
         }
     }
-    if (mine) write_moments(moments + (size_t)set * 8, a, m, n, dt);
+    if (mine) moments_from_sums(moments + (size_t)set * 8, a, m, n, dt);
 }
 
 template <typename R>
@@ -1319,6 +1319,20 @@ cudaError_t launch_reduce(const Batch &b, const State &s, const Noise &nz, int64
             packed_reduce_kernel<double><<<grid, kThreads, 0, st>>>(b, s, nz.dt, g, moments);
         else
             packed_reduce_kernel<float><<<grid, kThreads, 0, st>>>(b, s, nz.dt, g, moments);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_combine_moments(int32_t n, double *moments, const int64_t *M, const int64_t *N, double dt,
+                                   cudaStream_t st) {
+    for (int32_t i0 = 0; i0 < n; i0 += kCombineChunk) {
+        const int32_t k = std::min<int32_t>(kCombineChunk, n - i0);
+        CombineSizes sz;
+        for (int32_t j = 0; j < kCombineChunk; ++j) {
+            sz.M[j] = j < k ? M[i0 + j] : 0;
+            sz.N[j] = j < k ? N[i0 + j] : 0;
+        }
+        combine_moments_kernel<<<1, kCombineChunk, 0, st>>>(moments + (size_t)i0 * 8, k, sz, dt);
     }
     return cudaGetLastError();
 }

@@ -101,14 +101,9 @@ abp_status say(char *err, size_t err_len, abp_status st, const char *fmt, ...) {
     return st;
 }
 
-bool on_device(const void *p) {
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
+// The outputs are written by kernels on the current device: they must be that
+// device's memory (or managed memory), not host memory nor another GPU's.
+bool on_device(const void *p, int dev) { return ptr_kind(p, dev) == PtrKind::Device; }
 
 }  // namespace
 }  // namespace abp
@@ -139,8 +134,14 @@ extern "C" abp_status abp_run_set_noalloc(const abp_params *params, const abp_co
     if (cfg->scheme != 0 && cfg->scheme != 1) return say(err, err_len, ABP_EINVAL, "scheme must be 0 or 1");
     if (cfg->noise != 0)
         return say(err, err_len, ABP_EINVAL, "the allocation-free entry point uses the counter-based noise only");
-    if (cfg->snapshot_every < 0 || cfg->steps_per_launch < 0 || (cfg->schedule < 0 || cfg->schedule > 2))
-        return say(err, err_len, ABP_EINVAL, "invalid snapshot_every / steps_per_launch / schedule");
+    if (cfg->snapshot_every < 0 || cfg->steps_per_launch < 0)
+        return say(err, err_len, ABP_EINVAL, "invalid snapshot_every / steps_per_launch");
+    // the work queue needs per-tile counters and an autotuner table, which this call has no
+    // room for: it always runs lockstep launches of one block per tile
+    if (cfg->schedule != 0 && cfg->schedule != 1)
+        return say(err, err_len, ABP_EINVAL,
+                   "schedule = %d: the allocation-free entry point runs the lockstep schedule only (0 or 1)",
+                   cfg->schedule);
     const int ppt = cfg->particles_per_thread ? cfg->particles_per_thread : 1;
     if (ppt != 1 && ppt != 2 && ppt != 4) return say(err, err_len, ABP_EINVAL, "particles_per_thread must be 1, 2 or 4");
     if (n_traj < 0 || n_traj > kNoAllocMaxTraj)
@@ -150,16 +151,18 @@ extern "C" abp_status abp_run_set_noalloc(const abp_params *params, const abp_co
                    (long long)n_traj, (long long)kNoAllocMaxTraj);
     if (n_steps < 0 || n_steps >= ((int64_t)1 << 34))
         return say(err, err_len, ABP_EINVAL, "n_steps must be in [0, 2^34)");
-    if (!moments || !on_device(moments)) return say(err, err_len, ABP_EINVAL, "moments must be device memory");
-    if (cfg->hist_x_bins > 0 && (!hist_x || !on_device(hist_x)))
-        return say(err, err_len, ABP_EINVAL, "hist_x must be device memory when hist_x_bins > 0");
-    if (cfg->hist_v_bins > 0 && (!hist_v || !on_device(hist_v)))
-        return say(err, err_len, ABP_EINVAL, "hist_v must be device memory when hist_v_bins > 0");
-
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return say(err, err_len, ABP_ECUDA, "no current device: %s", cudaGetErrorString(e));
+    if (!moments || !on_device(moments, dev))
+        return say(err, err_len, ABP_EINVAL, "moments must be memory of the current device (%d)", dev);
+    if (cfg->hist_x_bins > 0 && (!hist_x || !on_device(hist_x, dev)))
+        return say(err, err_len, ABP_EINVAL, "hist_x must be memory of the current device when hist_x_bins > 0");
+    if (cfg->hist_v_bins > 0 && (!hist_v || !on_device(hist_v, dev)))
+        return say(err, err_len, ABP_EINVAL, "hist_v must be memory of the current device when hist_v_bins > 0");
+
     unsigned char *base = nullptr;
-    if (e == cudaSuccess) e = scratch_address(dev, &base);
+    e = scratch_address(dev, &base);
     if (e != cudaSuccess) return say(err, err_len, ABP_ECUDA, "scratch set-up: %s", cudaGetErrorString(e));
 
     cudaStream_t st = (cudaStream_t)cuda_stream;

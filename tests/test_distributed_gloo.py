@@ -1,8 +1,10 @@
 """Multi-process ensemble on CPU ranks (gloo, world size 2).
 
 Each rank integrates its replica of a batch with the FP64 oracle (trajectory ids offset by
-rank, as abp_config.traj_base does on the GPU) and the per-set sums are all-reduced; the
-combined moments must equal those of the concatenated ensemble computed in one process.
+rank, as abp_config.traj_base does on the GPU), the per-set sums are all-reduced and the
+library's abp_combine_moments (host memory: no GPU needed) forms the moments of the combined
+ensemble on every rank; they must equal those of the concatenated ensemble computed in one
+process from the per-trajectory values.
 Failure detection is tested on the host: a rank that leaves before the collective makes the
 other rank's all-reduce fail after its timeout instead of hanging.
 """
@@ -20,6 +22,17 @@ from paper_1104_2499_gb300 import shard
 from paper_1104_2499_gb300 import workloads as W
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def library():
+    from paper_1104_2499_gb300 import build as B
+
+    try:
+        B.nvcc()
+    except RuntimeError:
+        pytest.skip("nvcc not available to build libabp.so")
+    return B.build()
 
 
 def _free_port():
@@ -72,11 +85,11 @@ def _worker(rank, world, port, out_dir, fail_rank):
     try:
         res = shard.combine(local, w.n_traj, w.n_steps, w.dt, world, all_reduce)
         np.save(os.path.join(out_dir, "rank%d.npy" % rank), res)
-        # the benchmark's in-place form on a torch moments tensor (a strided column view)
+        # the benchmark's in-place form on a torch moments tensor (a strided column view):
+        # every column, the derived moments included, is that of the combined ensemble
         mom = torch.from_numpy(local.copy())
-        shard.all_reduce_sums_(mom, dist.all_reduce)
-        np.testing.assert_array_equal(mom[:, 4:8].numpy(), res[:, 4:8])
-        np.testing.assert_array_equal(mom[:, :4].numpy(), local[:, :4])
+        shard.all_reduce_sums_(mom, dist.all_reduce, [m * world for m in w.n_traj], w.n_steps, w.dt)
+        np.testing.assert_array_equal(mom.numpy(), res)
     except Exception as e:  # the collective ended with an error instead of hanging
         status = "error: " + type(e).__name__
     with open(os.path.join(out_dir, "status%d.txt" % rank), "w") as f:
@@ -130,7 +143,28 @@ def test_a_rank_that_leaves_makes_the_collective_fail_not_hang(tmp_path):
     assert not (tmp_path / "status1.txt").exists()
 
 
-def test_moments_from_sums_edge_cases():
-    m = shard.moments_from_sums([[0, 0, 0, 0], [2.0, 2.0, 4.0, 8.0]], [0, 2], [100, 0], 1e-3)
+def test_combined_moments_edge_cases():
+    from paper_1104_2499_gb300 import abp as A
+
+    # an empty set has no moments; one trajectory has no standard error; zero steps no D_eff
+    m = np.zeros((3, 8))
+    m[1, 4:] = [2.0, 4.0, 4.0, 16.0]  # one trajectory: vbar = 2, dx = 4
+    m[2, 4:] = [2.0, 2.0, 4.0, 8.0]  # two trajectories, vbar = 1 each, dx = 2 each
+    A.abp_combine_moments(m, [0, 1, 2], [100, 2000, 0], 1e-3)
     assert np.all(m[0] == 0)
-    assert m[1, 0] == 1.0 and m[1, 1] == 0.0 and m[1, 2] == 4.0 and m[1, 3] == 0.0
+    assert m[1].tolist() == [2.0, 0.0, 16.0, 0.0, 2.0, 4.0, 4.0, 16.0]
+    assert m[2, :4].tolist() == [1.0, 0.0, 4.0, 0.0]
+    # the sample variance of (a, b) is (a - b)^2 / 2, the standard error |a - b| / 2
+    a, b, dxa, dxb = 0.3, -0.1, 0.6, -0.2
+    m = np.zeros((1, 8))
+    m[0, 4:] = [a + b, a * a + b * b, dxa + dxb, dxa * dxa + dxb * dxb]
+    A.abp_combine_moments(m, [2], [2000], 1e-3)
+    assert m[0, 0] == pytest.approx((a + b) / 2, rel=1e-15)
+    assert m[0, 1] == pytest.approx(abs(a - b) / 2, rel=1e-12)
+    assert m[0, 3] == pytest.approx(((dxa - dxb) / 2) ** 2 / (2 * 2.0), rel=1e-12)
+    with pytest.raises(A.AbpError):
+        A.abp_combine_moments(np.zeros((1, 8)), [-1], [10], 1e-3)
+    with pytest.raises(A.AbpError):
+        A.abp_combine_moments(np.zeros((1, 8)), [1], [10], 0.0)
+    with pytest.raises(ValueError):
+        A.abp_combine_moments(np.zeros((1, 4)), [1], [10], 1e-3)

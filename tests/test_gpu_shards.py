@@ -1,8 +1,8 @@
 """Sharding on one GPU: an ensemble split into contiguous trajectory ranges, each run by its
 own context with abp_config.traj_base = the global id of its first trajectory (as one rank
 per GPU would), must give every trajectory bitwise the state of the unsharded run, and the
-per-set sums combined across shards (shard.combine) the unsharded moments up to the order
-of the FP64 additions.  The weak-scaling replicas of the benchmark are the same construction
+per-set sums combined across shards (abp_combine_moments) the unsharded moments up to the
+order of the FP64 additions.  The weak-scaling replicas of the benchmark are the same construction
 (replica r = trajectories [r T, (r + 1) T) of a larger ensemble)."""
 import numpy as np
 import pytest
@@ -53,8 +53,36 @@ def test_shards_reproduce_the_unsharded_run(abp, world):
                 sums += ens.results(host=True)["moments"].numpy()[:, 4:8]
             for k in st:
                 assert torch.equal(st[k], ref_state[k][r * m:(r + 1) * m]), (s, r, k)
-        got = shard.moments_from_sums(sums, [m * world], [full.n_steps[s]], full.dt)
+        got = np.zeros((1, 8))
+        got[0, 4:] = sums
+        abp.abp_combine_moments(got, [m * world], [full.n_steps[s]], full.dt)
         np.testing.assert_allclose(got[0, :4], ref_mom[0, :4], rtol=1e-12, atol=1e-15)
+        # the same sums combined on the device give the same bits as on the host
+        dev = torch.from_numpy(got.copy()).cuda()
+        dev[:, :4] = float("nan")
+        abp.abp_combine_moments(dev, [m * world], [full.n_steps[s]], full.dt)
+        torch.cuda.synchronize()
+        assert np.array_equal(dev.cpu().numpy(), got)
+
+
+def test_combining_one_shard_reproduces_its_reduction_bitwise(abp):
+    # abp_combine_moments applies the reduction's own formulas: one shard's sums give back
+    # abp_reduce's derived moments exactly, on the device and on the host
+    w = batch(700)
+    w.n_steps = [1500, 0, 333]
+    with abp.Ensemble(w) as ens:
+        ens.run()
+        ref = ens.results()["moments"]
+        torch.cuda.synchronize()
+    dev = ref.clone()
+    dev[:, :4] = -1.0
+    abp.abp_combine_moments(dev, w.n_traj, w.n_steps, w.dt)
+    torch.cuda.synchronize()
+    assert torch.equal(dev, ref)
+    host = ref.cpu().numpy().copy()
+    host[:, :4] = -1.0
+    abp.abp_combine_moments(host, w.n_traj, w.n_steps, w.dt)
+    assert np.array_equal(host, ref.cpu().numpy())
 
 
 def test_replica_ids_follow_the_rank(abp):
