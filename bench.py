@@ -31,6 +31,8 @@ UNIT = "particle-steps/s"
 # Algorithmic FP32/INT32 lane operations per particle-step: drift, depot, position and
 # wrap ~16, Philox4x32-10 amortised over its four steps 15, Box-Muller ~4.
 N_ALG = 35
+# The stochastic Heun step draws the same noise and evaluates drift, depot and position twice.
+N_ALG_HEUN = 51
 LANES_PER_SM = 128
 # DRAM bytes (read + write) per launch of the integrator on the 2,097,152-trajectory sweep grid,
 # from one ncu capture of that kernel (dram__bytes_read.sum + dram__bytes_write.sum); the traffic
@@ -55,14 +57,16 @@ def parse():
     ap.add_argument("--small", action="store_true",
                     help="the sweep grid at 2,000 steps (profiling and quick checks; not a bench line)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the pathwise-adjoint leg")
-    ap.add_argument("--visualisation", action="store_true",
-                    help="also measure the per-cycle cost of reading intermediate results (iterations lost)")
+    ap.add_argument("--no-visualisation", action="store_true",
+                    help="skip the per-cycle cost of reading intermediate results (iterations lost)")
     ap.add_argument("--adjoint-only", default="",
                     help="N_TRAJ,N_STEPS: time only the forward and backward of the differentiation workload at "
                          "this size (profiling; prints one JSON line without the bench keys)")
-    ap.add_argument("--configs", default="",
-                    help="also time other workloads, comma-separated: single, uneven, force, heun, xorshift, snapshots, "
-                         "precision, items (or 'all'); reported under 'configs'")
+    ap.add_argument("--configs", default="default",
+                    help="other workloads timed after the headline, comma-separated: single, uneven, force, heun, "
+                         "xorshift, snapshots_slice, snapshots (the full 64M x 10^6 run, about a minute), precision, "
+                         "items; 'default' = all but the full snapshots run, 'all' = every one, 'none' = skip; "
+                         "reported under 'configs'")
     return ap.parse_args()
 
 
@@ -426,7 +430,7 @@ def visualisation_leg(A, stream):
 
 # ----------------------------------------------------------------------------- other workloads
 
-def time_workload(A, stream, w, reps=1, **kw):
+def time_workload(A, stream, w, reps=1, lane_peak=None, **kw):
     """Integrate and reduce workload ``w`` ``reps`` times from a fresh initial condition (inputs
     resident on the device), timed with CUDA events on the library's stream."""
     import torch
@@ -448,7 +452,12 @@ def time_workload(A, stream, w, reps=1, **kw):
         t = statistics.median(times)
         out = {"workload": w.name, "sets": w.n_sets, "trajectories": w.total_traj,
                "particle_steps": w.particle_steps, "seconds": t, "value": w.particle_steps / t, "unit": UNIT,
-               "reps": reps, "tuning": ens.tuning(), "tiles": ens.tiles()}
+               "reps": reps, "tuning": ens.tuning(), "tiles": ens.tiles(), "timing": "CUDA events, integrate + reduce"}
+        if lane_peak:
+            # the same algorithmic count as the headline (the Heun step evaluates the drift twice)
+            n_alg = N_ALG_HEUN if w.scheme == 1 else N_ALG
+            out["roofline_frac"] = n_alg * out["value"] / (lane_peak * 1e12)
+            out["roofline_basis"] = "%d lane-ops per particle-step over the whole workload time" % n_alg
         return out, res
 
 
@@ -513,7 +522,7 @@ def items_leg(A, stream):
     return out
 
 
-def force_leg(A, stream):
+def force_leg(A, stream, lane_peak=None):
     """The paper's benchmark observable (Fig. 2): mean velocity against the load F0, 64 values in
     [-1, 1], 4,096 trajectories x 10^5 steps each.  Reports the curve, the stall force (where
     <v> crosses zero, linear interpolation) and the efficiency -F0 <v> / q (power delivered
@@ -522,7 +531,7 @@ def force_leg(A, stream):
     from paper_1104_2499_gb300 import workloads as W
 
     w = W.force_sweep()
-    r, res = time_workload(A, stream, w, 1)
+    r, res = time_workload(A, stream, w, 1, lane_peak)
     mom = res["moments"].cpu().numpy()
     F = np.array([p["F0"] for p in w.sets])
     v, se = mom[:, 0], mom[:, 1]
@@ -536,39 +545,60 @@ def force_leg(A, stream):
     return r
 
 
-def configs_leg(A, stream, names):
+def configs_leg(A, stream, names, lane_peak):
+    """Every other workload of the benchmark suite, each timed with CUDA events on the library's
+    stream (inputs resident, integrate + reduce), with its throughput and its fraction of the
+    FP32-lane roofline."""
     from paper_1104_2499_gb300 import workloads as W
 
-    if names == ["all"]:
-        names = ["single", "uneven", "force", "heun", "xorshift", "precision", "items", "snapshots"]
+    if names == ["default"]:
+        names = ["single", "uneven", "force", "heun", "xorshift", "snapshots_slice", "precision", "items"]
+    elif names == ["all"]:
+        names = ["single", "uneven", "force", "heun", "xorshift", "snapshots_slice", "snapshots", "precision",
+                 "items"]
     out = {}
     for name in names:
+        t0 = time.perf_counter()
         if name == "single":
-            out[name] = time_workload(A, stream, W.single_set(), 5)[0]
+            out[name] = time_workload(A, stream, W.single_set(), 5, lane_peak)[0]
         elif name == "uneven":
             w = W.uneven_batch()
-            out[name] = time_workload(A, stream, w, 1)[0]
-            out[name]["cpu_oracle"] = oracle_subset_rate(w, 16)
+            r = time_workload(A, stream, w, 1, lane_peak)[0]
+            # the schedule the autotuner did not choose, at its best trajectories per thread
+            other = 2 if r["tuning"]["schedule"] == 1 else 1
+            alt = time_workload(A, stream, w, 1, lane_peak, schedule=other)[0]
+            r["other_schedule"] = {k: alt[k] for k in ("value", "seconds", "tuning", "roofline_frac")}
+            r["cpu_oracle"] = oracle_subset_rate(w, 16)
+            out[name] = r
         elif name == "force":
-            out[name] = force_leg(A, stream)
+            out[name] = force_leg(A, stream, lane_peak)
         elif name == "snapshots":
             w = W.large_snapshots()
-            out[name] = time_workload(A, stream, w, 1)[0]
+            out[name] = time_workload(A, stream, w, 1, lane_peak)[0]
+            out[name]["cpu_oracle"] = oracle_subset_rate(w, 65536, 10_000)
+        elif name == "snapshots_slice":
+            # every trajectory of the large ensemble (67,108,864) over its first 2 x 10^4 steps, with
+            # its 1,024-bin histograms of x mod L and of v every 10^4 steps
+            w = W.large_snapshots(n_steps=20_000)
+            w.name = "snapshots_67108864x20000_slice"
+            out[name] = time_workload(A, stream, w, 1, lane_peak)[0]
             out[name]["cpu_oracle"] = oracle_subset_rate(w, 65536, 10_000)
         elif name == "heun":
             w = W.sweep_grid()
             w.scheme, w.name = 1, w.name + "_heun"
-            out[name] = time_workload(A, stream, w, 1)[0]
+            out[name] = time_workload(A, stream, w, 1, lane_peak)[0]
         elif name == "xorshift":
             w = W.sweep_grid()
             w.noise, w.name = 1, w.name + "_xorshift"
-            out[name] = time_workload(A, stream, w, 1)[0]
+            out[name] = time_workload(A, stream, w, 1, lane_peak)[0]
         elif name == "precision":
             out[name] = precision_leg(A, stream)
         elif name == "items":
             out[name] = items_leg(A, stream)
         else:
             raise SystemExit("unknown workload in --configs: " + name)
+        if isinstance(out[name], dict):
+            out[name]["leg_wall_s"] = time.perf_counter() - t0
     return out
 
 
@@ -740,8 +770,9 @@ def main():
     adj = None
     if rank == 0 and world == 1 and not args.no_adjoint:
         adj = adjoint_leg(A, stream, small=args.small)
-    vis = visualisation_leg(A, stream) if (rank == 0 and args.visualisation) else None
-    cfgs = configs_leg(A, stream, [c for c in args.configs.split(",") if c]) if (rank == 0 and args.configs) else None
+    vis = visualisation_leg(A, stream) if (rank == 0 and world == 1 and not args.no_visualisation) else None
+    cfg_names = [c for c in args.configs.split(",") if c and c != "none"]
+    cfgs = configs_leg(A, stream, cfg_names, peak) if (rank == 0 and world == 1 and cfg_names) else None
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

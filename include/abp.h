@@ -246,6 +246,15 @@ ABP_API abp_status abp_backward(abp_ctx *ctx, const double *dJ_dmean_v, double *
  * length gives abp_backward's result. */
 ABP_API abp_status abp_backward_windowed(abp_ctx *ctx, const double *dJ_dmean_v, double *grad, int64_t window);
 
+/* Per-trajectory derivatives of the last abp_backward / abp_backward_windowed call:
+ * dvbar (host or device, [total_traj][6] doubles, global trajectory order) receives
+ * d vbar_i / d theta_j for every trajectory i, vbar_i its time-averaged velocity and
+ * theta = (D, q, c, d, gamma0, asym) of its set, noise held fixed (windowed if the last
+ * call was).  The set gradient of abp_backward with unit weights is the mean of these
+ * over the set's trajectories.  ABP_ESTATE when no backward call has run since the
+ * batch was last set, reset or loaded. */
+ABP_API abp_status abp_backward_traj(abp_ctx *ctx, double *dvbar);
+
 /* Upper bound, in nanoseconds, of every device-side wait: in the work-queue
  * schedule (schedule 2) a work item waiting for the previous round of its tile,
  * in a warp-specialised narrow lockstep launch (a batch with fewer tiles than

@@ -125,6 +125,8 @@ def lib():
         L.abp_backward.restype = st
         L.abp_backward_windowed.argtypes = [_VP, _VP, _VP, C.c_int64]
         L.abp_backward_windowed.restype = st
+        L.abp_backward_traj.argtypes = [_VP, _VP]
+        L.abp_backward_traj.restype = st
         L.abp_synchronize.argtypes = [_VP]
         L.abp_synchronize.restype = st
         L.abp_destroy.argtypes = [_VP]
@@ -314,6 +316,11 @@ def abp_backward(ctx, dJ_dmean_v=None, grad=None, window: int = 0):
         _check(lib().abp_backward(ctx, _ptr(dJ_dmean_v), _ptr(grad)), ctx)
 
 
+def abp_backward_traj(ctx, dvbar):
+    """Per-trajectory derivatives [total_traj, 6] of the last backward call into dvbar."""
+    _check(lib().abp_backward_traj(ctx, _ptr(dvbar)), ctx)
+
+
 def abp_synchronize(ctx):
     _check(lib().abp_synchronize(ctx), ctx)
 
@@ -478,6 +485,13 @@ class Ensemble:
         g = torch.empty((self.w.n_sets, 6), dtype=torch.float64, device=dev)
         abp_backward(self.ctx, dJ, g, window)
         return g
+
+    def traj_grad(self, host: bool = False):
+        """d vbar_i / d theta for every trajectory, [total_traj, 6], from the last backward()."""
+        torch = self.torch
+        out = torch.empty((self.w.total_traj, 6), dtype=torch.float64, device="cpu" if host else self.device)
+        abp_backward_traj(self.ctx, out)
+        return out
 
     def synchronize(self):
         abp_synchronize(self.ctx)

@@ -650,6 +650,41 @@ __global__ void __launch_bounds__(kThreads) adjoint_final_kernel(AdjArgs a, SegV
         for (int j = 0; j < 6; ++j) a.partials[(size_t)tile * 6 + j] = gsum[j];
 }
 
+// Per trajectory: d vbar_i / d theta (no caller weight, not averaged), from the same
+// sums as adjoint_final_kernel -- the initial-condition term and the parameter scales
+// applied, divided by the set's step count.  out: [total_traj][6].
+__global__ void __launch_bounds__(kThreads) adjoint_traj_kernel(AdjArgs a, SegView sv, double *out) {
+    const Batch &b = a.b;
+    const int tile = blockIdx.x;
+    const int set = b.tile_set[tile];
+    const int64_t N = b.set_steps[set], T = b.total_traj;
+    const abp_params p = b.params[set];
+    const double dt = a.nz.dt;
+    const double Kd = dt * p.h * 0.453 * (2.0 * kPi / p.L);
+    const double inv_N = N > 0 ? 1.0 / (double)N : 0.0;
+    const int64_t first = b.tile_first[tile];
+    const int count = b.tile_count[tile];
+    for (int li = threadIdx.x; li < count; li += blockDim.x) {
+        const int64_t idx = first + li;
+        double G[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) G[q] = sv.G[(size_t)q * T + idx];
+        if (a.nz.v0_mode == 1) G[0] += (double)sv.lam[idx].y * (double)a.ck.ck[idx].z;
+        double *o = out + (size_t)idx * 6;
+        if (N == 0) {
+#pragma unroll
+            for (int q = 0; q < 6; ++q) o[q] = 0.0;
+            continue;
+        }
+        o[0] = (p.D > 0.0 ? G[0] / (2.0 * p.D) : NAN) * inv_N;
+        o[1] = dt * G[1] * inv_N;
+        o[2] = -dt * G[2] * inv_N;
+        o[3] = dt * G[3] * inv_N;
+        o[4] = -dt * G[4] * inv_N;
+        o[5] = 2.0 * Kd * G[5] * inv_N;
+    }
+}
+
 __global__ void __launch_bounds__(kThreads) adjoint_set_kernel(Batch b, const double *partials, double *grad) {
     __shared__ double red[kThreads / 32][6];
     const int set = blockIdx.x;
@@ -825,5 +860,62 @@ extern "C" abp_status abp_backward_windowed(abp_ctx *ctx, const double *dJ_dmean
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     }
     if (e != cudaSuccess) return set_err(ctx, ABP_ECUDA, "abp_backward: gradient copy", e);
+    ctx->adj_valid = true;
+    return ABP_OK;
+}
+
+extern "C" abp_status abp_backward_traj(abp_ctx *ctx, double *dvbar) {
+    const NvtxRange nvtx("abp_backward_traj");
+    if (!ctx) return ABP_EINVAL;
+    if (!dvbar) return set_err(ctx, ABP_EINVAL, "abp_backward_traj: dvbar is NULL");
+    if (!ctx->have_batch || !ctx->adj_valid)
+        return set_err(ctx, ABP_ESTATE, "abp_backward_traj: no abp_backward since the batch was last (re)started");
+    const PtrKind k = ptr_kind(dvbar, ctx->device);
+    if (k == PtrKind::OtherDevice) return set_err(ctx, ABP_EINVAL, "abp_backward_traj: output on another GPU");
+    const int64_t T = ctx->total_traj;
+    if (T == 0 || ctx->n_tiles == 0) return ABP_OK;
+    // the per-trajectory sums of the last backward call: the same scratch layout as there
+    const int64_t n_sub = (ctx->cfg.checkpoint_every + kSub - 1) / kSub;
+    const size_t sub1_bytes = sizeof(float4) * (size_t)n_sub * (size_t)T;
+    const size_t sub_bytes = 2 * ((sub1_bytes + 255) & ~(size_t)255);
+    const size_t part_bytes = sizeof(double) * 6 * (size_t)std::max(ctx->n_tiles, 1);
+    const size_t grad_bytes = sizeof(double) * 6 * (size_t)std::max(ctx->n_sets, 1);
+    const size_t w_bytes = sizeof(double) * (size_t)std::max(ctx->n_sets, 1);
+    const size_t lam_bytes = sizeof(float4) * (size_t)std::max<int64_t>(T, 1);
+    auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    char *base = (char *)ctx->d_adj.p;
+    SegView sv;
+    sv.lam = (float4 *)(base + align(sub_bytes) + align(part_bytes) + align(grad_bytes) + align(w_bytes));
+    sv.G = (double *)((char *)sv.lam + align(lam_bytes));
+    AdjArgs a;
+    a.b = ctx->batch();
+    a.ck = ctx->ckpt();
+    a.nz = ctx->noise();
+    a.sub = nullptr;
+    a.n_sub = n_sub;
+    a.w = nullptr;
+    a.partials = nullptr;
+    cudaStream_t s = ctx->stream;
+    const size_t bytes = sizeof(double) * 6 * (size_t)T;
+    DevBuf tmp;
+    double *dst = dvbar;
+    if (k != PtrKind::Device) {
+        const cudaError_t ea = cudaMalloc(&tmp.p, bytes);
+        if (ea != cudaSuccess) {
+            tmp.p = nullptr;
+            cudaGetLastError();
+            return set_err(ctx, ABP_ENOMEM, "abp_backward_traj: staging buffer", ea);
+        }
+        dst = (double *)tmp.p;
+    }
+    adjoint_traj_kernel<<<ctx->n_tiles, kThreads, 0, s>>>(a, sv, dst);
+    ctx->launches += 1;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && k != PtrKind::Device) {
+        e = cudaMemcpyAsync(dvbar, dst, bytes, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    tmp.release();
+    if (e != cudaSuccess) return set_err(ctx, ABP_ECUDA, "abp_backward_traj", e);
     return ABP_OK;
 }

@@ -802,6 +802,7 @@ abp_status abp_reset(abp_ctx *ctx, uint64_t seed) {
     ctx->cfg.seed = seed;
     ctx->g = 0;
     ctx->ckpt_complete = true;
+    ctx->adj_valid = false;
     if (ctx->live_stream) cudaStreamSynchronize(ctx->live_stream);  // copies of the previous run end first
     ctx->live_sent = ctx->live_ready = 0;
     cudaStream_t s = ctx->stream;
@@ -1324,6 +1325,7 @@ abp_status abp_load(abp_ctx *ctx, const void *buf, size_t bytes) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "abp_load");
     ctx->g = hd.g;
+    ctx->adj_valid = false;
     ctx->cfg.seed = hd.seed;
     ctx->cfg.traj_base = hd.traj_base;
     ctx->ckpt_complete = hd.g == 0;

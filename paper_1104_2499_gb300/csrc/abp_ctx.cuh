@@ -51,6 +51,7 @@ struct abp_ctx {
     int64_t max_steps = 0;
     int64_t g = 0;  // global steps issued: set s has done min(g, n_steps[s])
     bool ckpt_complete = true;  // adjoint checkpoints cover the run from step 0 (false after abp_load)
+    bool adj_valid = false;     // the adjoint scratch holds the sums of the current run (abp_backward_traj)
     int ppt = 1;
     int sched = 1;                 // 1: lockstep launches, 2: work queue (autotuned when cfg.schedule = 0)
     int64_t steps_per_launch = 0;  // lockstep: steps per launch; work queue: steps per round
@@ -183,6 +184,7 @@ struct abp_ctx {
         if (live_stream) cudaStreamSynchronize(live_stream);
         drop_graphs();
         have_batch = false;
+        adj_valid = false;
         live = false;
         live_mom = nullptr;
         live_hx = live_hv = nullptr;

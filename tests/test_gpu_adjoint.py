@@ -132,3 +132,55 @@ def test_windowed_adjoint_long_horizon(abp):
     se = r["dvbar"].std(axis=0, ddof=1) / np.sqrt(2048)
     assert np.all(np.abs(g - r["grad"]) <= 3 * np.sqrt(2) * se + 1e-3 * np.max(np.abs(r["grad"]))), (g, r["grad"], se)
     assert np.max(np.abs(g)) < 0.1 * np.max(np.abs(full))
+
+
+@pytest.mark.parametrize("K,v0_mode,window", [(250, 1, 0), (64, 0, 0), (250, 1, 500)])
+def test_adjoint_per_trajectory_matches_oracle_tangent(abp, K, v0_mode, window):
+    # every trajectory's derivative d vbar_i / d theta (no averaging, so errors of opposite
+    # sign cannot cancel) against the oracle's FP64 tangent of the same trajectory, over
+    # 1,000 steps where the FP32 and FP64 paths stay together: |gpu - oracle| <=
+    # 1e-3 max(|oracle|, s_j), s_j = the root mean square of component j over the set
+    sets = [W._with(D=0.05), W._with(D=0.2, q=2.0, asym=0.1, gamma0=1.5), W._with(D=0.1, F0=0.3, c=0.3, d=0.7)]
+    w = W.Workload(name="adj_traj", sets=sets, n_traj=[1000, 513, 700], n_steps=[1000, 1000, 750], dt=1e-3, seed=35,
+                   v0_mode=v0_mode, checkpoint_every=K)
+    with abp.Ensemble(w) as ens:
+        ens.run()
+        g = ens.backward(host=True, window=window).numpy()
+        dv = ens.traj_grad(host=True).numpy()
+    base = w.traj_base()
+    for i, p in enumerate(w.sets):
+        r = O.run_set(p, seed=w.seed, dt=w.dt, n_traj=w.n_traj[i], n_steps=w.n_steps[i], traj_base=base[i],
+                      v0_mode=w.v0_mode, want_traj_grad=True, grad_window=window)
+        ref = r["dvbar"]
+        sl = slice(base[i], base[i] + w.n_traj[i])
+        s = np.sqrt(np.mean(ref**2, axis=0))
+        bound = 1e-3 * np.maximum(np.abs(ref), s)
+        ratio = np.abs(dv[sl] - ref) / bound
+        assert np.all(ratio <= 1.0), (i, float(ratio.max()), np.unravel_index(ratio.argmax(), ratio.shape))
+        # the set gradient (unit weights) is the mean of the trajectories' derivatives
+        np.testing.assert_allclose(dv[sl].mean(axis=0), g[i], rtol=1e-9, atol=1e-12 * np.abs(g[i]).max())
+
+
+def test_adjoint_at_zero_noise(abp):
+    # D = 0: sigma = sqrt(2 D dt) has no derivative there, so the D-component is NaN (in the
+    # set gradient and for every trajectory); the other components are those of the
+    # deterministic model and match the oracle's tangent
+    sets = [W._with(D=0.0, F0=0.1), W._with(D=0.1)]
+    w = W.Workload(name="adj_d0", sets=sets, n_traj=[300, 300], n_steps=[800, 800], dt=1e-3, seed=36, v0_mode=0,
+                   checkpoint_every=200)
+    with abp.Ensemble(w) as ens:
+        ens.run()
+        g = ens.backward(host=True).numpy()
+        dv = ens.traj_grad(host=True).numpy()
+    r = O.run_set(sets[0], seed=w.seed, dt=w.dt, n_traj=300, n_steps=800, v0_mode=0, want_traj_grad=True)
+    assert np.isnan(g[0, 0]) and np.isnan(r["grad"][0]) and np.all(np.isnan(dv[:300, 0]))
+    assert np.all(np.isfinite(g[0, 1:])) and np.all(np.isfinite(g[1]))
+    np.testing.assert_allclose(g[0, 1:], r["grad"][1:], rtol=1e-3, atol=1e-3 * np.abs(r["grad"][1:]).max())
+    # the readout is refused once the batch has been restarted
+    with abp.Ensemble(w) as ens:
+        ens.run()
+        ens.backward()
+        ens.reset()
+        with pytest.raises(abp.AbpError) as ei:
+            ens.traj_grad()
+        assert ei.value.status == abp.ABP_ESTATE

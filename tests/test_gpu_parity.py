@@ -272,20 +272,29 @@ def test_paired_steps_match_scalar_steps_bitwise(abp, scheme, noise):
     # with paired FP32 instructions, which round each half as the scalar operation.  Ragged
     # sets (odd counts leave a half of the last pair idle), step counts that are not multiples
     # of 4 (single-step heads and tails), 64-step folds, snapshots and split launches: every
-    # trajectory and every histogram count must be the same bits as the scalar run.
+    # trajectory and every histogram count must be the same bits as the scalar run.  The
+    # ragged sets are followed by 150 sets of 257 trajectories, so that every lockstep launch
+    # has more tiles than SMs and runs wide (a narrow launch steps one trajectory per thread
+    # whatever the setting, which would compare the scalar kernel with itself).
     w = ragged_batch(steps=777, seed=23, hist_x_bins=16, hist_v_bins=8, v_lo=-2.0, v_hi=2.0, snapshot_every=97,
                      scheme=scheme, noise=noise)
+    w.sets = w.sets + [W._with(D=0.05 + 0.002 * k, q=0.5 + 0.02 * k) for k in range(150)]
+    w.n_traj = w.n_traj + [257] * 150
+    w.n_steps = w.n_steps + [777 - (k % 5) for k in range(150)]
 
     def run(**kw):
         with abp.Ensemble(w, **kw) as ens:
             ens.run()
             res, st = ens.results(), ens.state()
             torch.cuda.synchronize()
+            if kw.get("schedule") == 1:
+                assert ens.tiles()["narrow"] == 0 and ens.tiles()["tiles"] >= 152, (kw, ens.tiles())
             return res, st
 
     ref_r, ref_s = run(particles_per_thread=1, schedule=1)
     for kw in (dict(particles_per_thread=2, schedule=1), dict(particles_per_thread=4, schedule=1),
-               dict(particles_per_thread=2, schedule=2), dict(particles_per_thread=2, schedule=1, steps_per_launch=53)):
+               dict(particles_per_thread=2, schedule=2), dict(particles_per_thread=4, schedule=2),
+               dict(particles_per_thread=2, schedule=1, steps_per_launch=53)):
         r, s = run(**kw)
         for k in ref_s:
             assert torch.equal(ref_s[k], s[k]), (kw, k)
