@@ -151,15 +151,13 @@ __global__ void __launch_bounds__(kThreads) init_kernel(Batch b, State st, Hist 
         const R y0 = (R)(w.x >> 8) * (R)0x1p-24;
         R v0 = 0;
         if (nz.v0_mode == 1) {
-            if constexpr (sizeof(R) == 4) {
-                float nr, cs, sn;
-                box_muller_f32(w.y, w.z, kBoxMullerUnit, nr, cs, sn);
-                v0 = (float)sqrt(p.D) * (nr * cs);
-            } else {
-                double ze, zo;
-                box_muller_f64(w.y, w.z, ze, zo);
-                v0 = sqrt(p.D) * ze;
-            }
+            // FP64 Box-Muller for both state types, rounded once: the initial velocity is
+            // the earliest perturbation a trajectory sees, so near an unstable point of
+            // the potential an error of the FP32 fast path (~1e-6 relative) grows by two
+            // orders of magnitude over 10^3 steps.  One transform per trajectory and run.
+            double ze, zo;
+            box_muller_f64(w.y, w.z, ze, zo);
+            v0 = (R)(sqrt(p.D) * ze);
         }
         if (nz.noise == 1 && st.xs) st.xs[t] = xorshift_seed((uint64_t)t + nz.traj_base, nz.k0, nz.k1);
         s.y[t] = y0;
