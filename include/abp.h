@@ -108,12 +108,16 @@ typedef struct {
                                     persistent launch whose blocks pop (tile, round) items, so
                                     uneven sets balance across SMs.  The autotuner times every
                                     (schedule, particles_per_thread) pair once per device and
-                                    library build (table kept beside the library) and predicts
-                                    each pair's time on the batch of abp_set_params from the busy
-                                    fraction of its resident blocks; the work queue must beat
-                                    lockstep by more than 2% to be chosen */
+                                    library build on a synthetic batch (table kept beside the
+                                    library), predicts every (schedule, particles_per_thread,
+                                    steps_per_launch in {10^3, 10^4, 10^5}) candidate's time on
+                                    the batch of abp_set_params from the busy fraction of its
+                                    resident blocks and the state traffic of its launches, then,
+                                    when both schedules are allowed, times the best candidate of
+                                    each on the first steps of the batch itself and keeps the
+                                    faster prediction (abp_tuning_report shows the record) */
     int64_t steps_per_launch;    /* lockstep: steps per launch; work queue: steps per work item
-                                    (round); 0 = chosen automatically */
+                                    (round); 0 = chosen by the autotuner from 10^3, 10^4, 10^5 */
     uint64_t traj_base;          /* added to every global trajectory id: a process that runs
                                     one shard of a larger ensemble passes the id of its first
                                     trajectory, so every trajectory keeps its own noise */
@@ -277,6 +281,14 @@ ABP_API abp_status abp_test_hold_tile(abp_ctx *ctx, int32_t tile);
  * integrator kernel resident on the GPU at once (the work queue's grid). */
 ABP_API abp_status abp_tuning(const abp_ctx *ctx, int32_t *schedule, int32_t *particles_per_thread,
                               int64_t *steps_per_item, int32_t *blocks);
+
+/* The autotuner's record for the current batch, as JSON text: every candidate
+ * (schedule, particles per thread, steps per launch) with its model prediction, the
+ * measured time of the probe on the batch's first steps and the prediction used, and
+ * the choice.  buf (host, len bytes, may be NULL) receives it NUL-terminated and cut to
+ * fit; *needed (may be NULL) the size with the terminator.  "{\"fixed\": true}" when
+ * the configuration fixed every choice. */
+ABP_API abp_status abp_tuning_report(const abp_ctx *ctx, char *buf, size_t len, size_t *needed);
 
 /* Tiling of the current batch (host outputs, any may be NULL): tiles in all, how
  * many of them are packed (several small sets sharing one block), and the block

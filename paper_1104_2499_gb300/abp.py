@@ -93,6 +93,8 @@ def lib():
                                  C.POINTER(C.c_int32)]
         L.abp_tuning.restype = st
         L.abp_tiles.argtypes = [_VP, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+        L.abp_tuning_report.argtypes = [_VP, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]
+        L.abp_tuning_report.restype = st
         P64, P32 = C.POINTER(C.c_int64), C.POINTER(C.c_int32)
         L.abp_plan.argtypes = [C.c_int32, P64, P64, C.c_int32, C.c_int32, C.c_int32, C.c_int32, P32, P32, P32,
                                P64, P32, P32, C.c_int32]
@@ -214,6 +216,17 @@ def abp_tuning(ctx):
     sc, p, s, b = C.c_int32(), C.c_int32(), C.c_int64(), C.c_int32()
     _check(lib().abp_tuning(ctx, C.byref(sc), C.byref(p), C.byref(s), C.byref(b)), ctx)
     return {"schedule": sc.value, "particles_per_thread": p.value, "steps_per_item": s.value, "blocks": b.value}
+
+
+def abp_tuning_report(ctx) -> dict:
+    """The autotuner's record for the current batch (candidates, probe times, choice)."""
+    import json
+
+    n = C.c_size_t()
+    _check(lib().abp_tuning_report(ctx, None, 0, C.byref(n)), ctx)
+    buf = C.create_string_buffer(n.value)
+    _check(lib().abp_tuning_report(ctx, buf, n.value, None), ctx)
+    return json.loads(buf.value.decode() or "{}")
 
 
 def abp_tiles(ctx):
@@ -440,6 +453,9 @@ class Ensemble:
 
     def tiles(self) -> dict:
         return abp_tiles(self.ctx)
+
+    def tuning_report(self) -> dict:
+        return abp_tuning_report(self.ctx)
 
     def integrate(self, max_steps: int = -1):
         abp_integrate(self.ctx, max_steps)

@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <map>
+#include <mutex>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -82,8 +83,6 @@ int64_t default_window(int64_t total_traj, int64_t max_steps) {
     return std::max<int64_t>(1, std::min<int64_t>(s, max_steps));
 }
 
-int64_t default_steps_per_launch(const abp_ctx *ctx) { return default_window(ctx->total_traj, ctx->max_steps); }
-
 // Copy n bytes of a device buffer to a caller pointer that may be host or device.
 abp_status deliver(abp_ctx *ctx, void *dst, const void *src, size_t n, bool *synced) {
     if (!dst || n == 0) return ABP_OK;
@@ -105,8 +104,8 @@ abp_status deliver(abp_ctx *ctx, void *dst, const void *src, size_t n, bool *syn
 // Schedule and particles per thread.  Every (schedule, PPT) candidate is timed
 // once per device and state type on a synthetic single-set batch several
 // waves deep (4,096 trajectories per SM, 8,192 steps after a 256-step warm-up,
-// CUDA events on the context's stream); autotune() weighs the table with the
-// batch at hand.
+// CUDA events on the context's stream); choose_configuration() weighs the
+// table with the batch at hand.
 struct TuneTable {
     bool done = false;
     float ms[3][3] = {};  // [schedule 1 = lockstep, 2 = work queue][ppt 1, 2, 4]
@@ -366,11 +365,13 @@ double batch_efficiency(int32_t n, const int64_t *n_traj, const int64_t *n_steps
     if (useful <= 0.0 || cap <= 0) return 1.0;
     double cost = 0.0;  // particle-step capacity spent
     if (sched == 2) {
-        // list scheduling of the work items: makespan about W / cap plus half an item
+        // list scheduling of the work items: makespan about W / cap plus half an item;
+        // items of spl steps (0: the largest of 10^5, 10^4, 10^3 giving 32 items per block)
         double tile_steps = 0.0;
         for (const auto &t : tiles) tile_steps += (double)t.first * (double)t.second;
-        int64_t item = 1000;
+        int64_t item = spl > 0 ? spl : 1000;
         for (int64_t S : {100000, 10000, 1000}) {
+            if (spl > 0) break;
             int64_t items = 0;
             for (const auto &t : tiles) items += t.first * ((t.second + S - 1) / S);
             if (items >= 32 * cap) {
@@ -487,85 +488,77 @@ bool plan_tiles(int32_t n_sets, const int64_t *n_traj, const int64_t *n_steps, i
     return true;
 }
 
-// Sets ctx->sched and ctx->ppt from the configuration, the timing table and
-// the batch: each allowed candidate's trial time divided by the fraction of
-// its capacity this batch keeps busy; the smallest prediction wins.
-// The work queue is chosen only when predicted faster than lockstep by more
-// than this fraction (about the run-to-run spread of the trial): between
-// near-equal candidates the lockstep schedule, which has no device-side waits,
-// is kept, and the choice stays the same from one machine to the next.  (At 1%
-// the measured choices were the same: where the work queue measures 2% faster
-// -- the uneven batch, xorshift noise -- the model itself predicts lockstep.)
-#ifndef ABP_QUEUE_MARGIN
-#define ABP_QUEUE_MARGIN 0.02
-#endif
-constexpr double kQueueMargin = ABP_QUEUE_MARGIN;
+// The autotuner's model of a candidate (schedule, trajectories per thread, steps per
+// launch) on a batch: the candidate's trial time brought to full use of its capacity,
+// scaled to the batch's particle-steps and divided by the fraction of capacity the batch
+// keeps busy (batch_efficiency), plus what its launches move and cost -- every lockstep
+// window loads and stores the state of the trajectories still running, every work item
+// that of its tile (at the device copy rate), and each launch or item pop has a fixed cost.
+// The constants are measured on GB300: copy rate ~6.7 TB/s, a graph-replayed launch a few
+// microseconds, one item's pop, wait and publish about two microseconds of a block.
+constexpr double kHbmBytesPerMs = 6.5e9;
+constexpr double kLaunchMs = 0.004;
+constexpr double kItemMs = 0.002;
 
-void autotune(abp_ctx *ctx) {
-    const int want_sched = ctx->cfg.schedule;          // 0 auto, 1 lockstep, 2 work queue
-    const int want_ppt = ctx->cfg.particles_per_thread;  // 0 auto
-    if (want_sched != 0 && want_ppt != 0) {
-        ctx->sched = want_sched;
-        ctx->ppt = want_ppt;
-        return;
-    }
-    const int dev = ctx->device, kind = tune_kind(ctx);
-    TuneTable local;
-    TuneTable &tt = (dev >= 0 && dev < 64) ? g_tune[dev][kind] : local;
-    if (!tt.done && !load_tune(ctx, tt)) {
-        measure_candidates(ctx, tt);
-        if (tt.done) save_tune(ctx, tt);
-    }
-    const int cands[3] = {1, 2, 4};
+// Bytes of trajectory state a launch reads and writes per trajectory.
+double state_io_bytes(const abp_config &c) {
+    return 2.0 * ((c.state_fp64 ? 8.0 : 4.0) * 6.0 + 4.0 + (c.noise == 1 ? 16.0 : 0.0));
+}
+
+// Blocks of a candidate's integrator resident at once.
+int64_t candidate_capacity(const abp_ctx *ctx, int sched, int ppt) {
     const abp_config &c = ctx->cfg;
     const size_t smem = sizeof(uint32_t) * (size_t)(c.hist_x_bins + (c.hist_v_bins > 0 ? c.hist_v_bins + 2 : 0));
     const int mode = c.scheme == 1 ? 1 : c.noise == 1 ? 2 : 0;
-    double best = 1e300;
-    int bs = want_sched ? want_sched : 1, bp = want_ppt ? want_ppt : 1;
-    for (int sch = 1; sch <= 2; ++sch) {
-        if (want_sched && sch != want_sched) continue;
-        for (int ci = 0; ci < 3; ++ci) {
-            if (want_ppt && cands[ci] != want_ppt) continue;
-            if (!(tt.ms[sch][ci] < 1e29f)) continue;
-            int bps = 0;
-            const cudaError_t oe = sch == 1 ? integrate_occupancy(c.state_fp64 != 0, cands[ci], smem, &bps, mode)
-                                            : persistent_occupancy(c.state_fp64 != 0, cands[ci], smem, &bps, mode);
-            if (oe != cudaSuccess) cudaGetLastError();
-            const int64_t cap = (int64_t)std::max(bps, 1) * std::max(ctx->sm_count, 1);
-            const int64_t spl = c.steps_per_launch > 0 ? c.steps_per_launch : default_steps_per_launch(ctx);
-            // the trial's own batch keeps part of the capacity idle too (lockstep at two
-            // trajectories per thread: 2.67 waves, so a third of the last one): its time is
-            // brought to full use before the actual batch's busy fraction is applied
-            const int64_t trial_traj = (int64_t)std::max(ctx->sm_count, 1) * kTrialTrajPerSm, trial_steps = kTrialSteps;
-            const double eff_trial = batch_efficiency(1, &trial_traj, &trial_steps, sch, cands[ci], false,
-                                                      sch == 1 ? kTrialSteps : kTrialSteps / kTrialRounds, cap);
-            const double eff_batch = batch_efficiency(ctx->n_sets, ctx->n_traj.data(), ctx->n_steps.data(), sch,
-                                                      cands[ci], c.checkpoint_every > 0, spl, cap);
-            const double pred = (double)tt.ms[sch][ci] * eff_trial / eff_batch * (sch == 2 ? 1.0 + kQueueMargin : 1.0);
-            if (pred < best) {
-                best = pred;
-                bs = sch;
-                bp = cands[ci];
-            }
-        }
-    }
-    ctx->sched = bs;
-    ctx->ppt = bp;
+    int bps = 0;
+    const cudaError_t oe = sched == 1 ? integrate_occupancy(c.state_fp64 != 0, ppt, smem, &bps, mode)
+                                      : persistent_occupancy(c.state_fp64 != 0, ppt, smem, &bps, mode);
+    if (oe != cudaSuccess) cudaGetLastError();
+    return (int64_t)std::max(bps, 1) * std::max(ctx->sm_count, 1);
 }
 
-// Steps per work item of the work-queue schedule: the largest of 10^5, 10^4,
-// 10^3 that still gives at least 32 items per resident block (so the last
-// items leave under ~2% of the launch idle), else 10^3.
-int64_t choose_round_steps(const abp_ctx *ctx) {
-    const int64_t cands[3] = {100000, 10000, 1000};
-    const int64_t cap = std::max(ctx->grid, 1);
-    for (int64_t S : cands) {
-        int64_t items = 0;
-        for (int32_t t = 0; t < ctx->n_tiles; ++t)
-            items += (ctx->n_steps[ctx->tile_set[t]] + S - 1) / S;
-        if (items >= 32 * cap) return S;
+int ppt_index(int ppt) { return ppt == 1 ? 0 : ppt == 2 ? 1 : 2; }
+
+// Predicted milliseconds of the batch (n sets of M[i] trajectories, N[i] steps).
+double model_ms(const abp_ctx *ctx, const TuneTable &tt, int sched, int ppt, int64_t spl, int32_t n,
+                const int64_t *M, const int64_t *N) {
+    const float trial = tt.ms[sched][ppt_index(ppt)];
+    if (!(trial < 1e29f)) return 1e300;
+    const int64_t cap = candidate_capacity(ctx, sched, ppt);
+    const bool ckpt = ctx->cfg.checkpoint_every > 0;
+    const int64_t trial_traj = (int64_t)std::max(ctx->sm_count, 1) * kTrialTrajPerSm, trial_steps = kTrialSteps;
+    const double eff_trial = batch_efficiency(1, &trial_traj, &trial_steps, sched, ppt, false,
+                                              sched == 1 ? kTrialSteps : kTrialSteps / kTrialRounds, cap);
+    const double eff = batch_efficiency(n, M, N, sched, ppt, ckpt, spl, cap);
+    double work = 0.0;
+    int64_t max_n = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        work += (double)M[i] * (double)N[i];
+        max_n = std::max(max_n, N[i]);
     }
-    return 1000;
+    if (work <= 0.0) return 0.0;
+    const double compute = (double)trial * eff_trial / std::max(eff, 1e-9) * work / ((double)trial_traj * trial_steps);
+    const double sb = state_io_bytes(ctx->cfg);
+    double bytes = 0.0, fixed = 0.0;
+    if (sched == 1) {
+        for (int64_t g = 0; g < max_n; g += spl) {
+            double active = 0.0;
+            for (int32_t i = 0; i < n; ++i)
+                if (N[i] > g) active += (double)M[i];
+            bytes += sb * active;
+            fixed += kLaunchMs;
+        }
+    } else {
+        const int64_t tile = (int64_t)kThreads * ppt;
+        double items = 0.0;
+        for (int32_t i = 0; i < n; ++i) {
+            const double rounds = (double)((N[i] + spl - 1) / spl);
+            bytes += sb * (double)M[i] * rounds;
+            items += (double)((M[i] + tile - 1) / tile) * rounds;
+        }
+        fixed = kLaunchMs + items * kItemMs / (double)cap;
+    }
+    return compute + bytes / kHbmBytesPerMs + fixed;
 }
 
 // Round starts of the window [g0, g1): round j holds the tiles whose sets still
@@ -584,6 +577,343 @@ std::vector<int32_t> round_starts(const abp_ctx *ctx, int64_t g0, int64_t g1, in
     }
     rs[n_rounds] = (int32_t)acc;
     return rs;
+}
+
+// The tiling, launch geometry and device tables of the current batch for one
+// (schedule, trajectories per thread, steps per launch or per work item) choice,
+// and the batch's initial condition drawn on the device.  Device buffers are
+// reused when large enough.  Returns after the uploads have completed.
+abp_status configure_batch(abp_ctx *ctx, int sched, int ppt, int64_t spl) {
+    const int32_t n_sets = ctx->n_sets;
+    ctx->sched = sched;
+    ctx->ppt = ppt;
+    ctx->g = 0;
+    ctx->ckpt_complete = true;
+    {
+        TilePlan plan;
+        if (!plan_tiles(n_sets, ctx->n_traj.data(), ctx->n_steps.data(), ctx->sched, ctx->ppt, ctx->cfg.checkpoint_every > 0, ctx->sm_count,
+                        plan))
+            return fail(ctx, ABP_EINVAL, "too many tiles");
+        ctx->set_first.swap(plan.set_first);
+        ctx->set_packed.swap(plan.set_packed);
+        ctx->set_tile_begin.swap(plan.set_tile_begin);
+        ctx->tile_first.swap(plan.tile_first);
+        ctx->tile_count.swap(plan.tile_count);
+        ctx->tile_set.swap(plan.tile_set);
+        ctx->set_order.swap(plan.set_order);
+        ctx->n_single = plan.n_single;
+        ctx->n_tiles = (int32_t)ctx->tile_first.size();
+        ctx->n_unpacked = plan.n_unpacked;
+        ctx->narrow = plan.narrow;
+        ctx->sub_single = plan.sub_single;
+        ctx->sub_packed = plan.sub_packed;
+    }
+    const abp_config &c = ctx->cfg;
+    const bool any_hist = c.hist_x_bins > 0 || c.hist_v_bins > 0;
+    // snapshot slots: one per S steps when snapshot_every = S > 0 (histograms and live
+    // results use them), else one final histogram snapshot when there are histograms
+    ctx->n_snap = c.snapshot_every > 0 ? ctx->max_steps / c.snapshot_every : (any_hist ? 1 : 0);
+    ctx->n_ckpt = c.checkpoint_every > 0 ? ctx->max_steps / c.checkpoint_every + 1 : 0;
+    // Work-queue order: tiles by decreasing step count of their set (stable).
+    ctx->perm.resize(ctx->n_tiles);
+    for (int32_t t = 0; t < ctx->n_tiles; ++t) ctx->perm[t] = t;
+    std::stable_sort(ctx->perm.begin(), ctx->perm.end(), [&](int32_t a, int32_t b) {
+        return ctx->n_steps[ctx->tile_set[a]] > ctx->n_steps[ctx->tile_set[b]];
+    });
+    ctx->perm_steps.resize(ctx->n_tiles);
+    for (int32_t k = 0; k < ctx->n_tiles; ++k) ctx->perm_steps[k] = ctx->n_steps[ctx->tile_set[ctx->perm[k]]];
+    {
+        int bps = 0;
+        const size_t smem = sizeof(uint32_t) * (size_t)(std::max(c.hist_x_bins, 0) +
+                                                        (c.hist_v_bins > 0 ? c.hist_v_bins + 2 : 0));
+        cudaError_t oe =
+            persistent_occupancy(c.state_fp64 != 0, ctx->ppt, smem, &bps, c.scheme == 1 ? 1 : c.noise == 1 ? 2 : 0);
+        if (oe != cudaSuccess) return cuda_fail(ctx, oe, "occupancy query");
+        ctx->grid = std::max(bps, 1) * std::max(ctx->sm_count, 1);
+    }
+    ctx->steps_per_launch = std::max<int64_t>(spl, 1);
+
+    const size_t T = (size_t)ctx->total_traj;
+    const size_t rsz = c.state_fp64 ? sizeof(double) : sizeof(float);
+    abp_status st = ABP_OK;
+#define ALLOC(buf, bytes, what) \
+    if ((st = alloc(ctx, ctx->buf, (bytes), what)) != ABP_OK) { ctx->release_all(); return st; }
+    ALLOC(d_params, sizeof(abp_params) * (size_t)n_sets, "parameters");
+    ALLOC(d_steps, sizeof(int64_t) * (size_t)n_sets, "step counts");
+    ALLOC(d_set_tile_begin, sizeof(int32_t) * ((size_t)n_sets + 1), "set tiles");
+    ALLOC(d_tile_first, sizeof(int64_t) * (size_t)ctx->n_tiles, "tile table");
+    ALLOC(d_tile_count, sizeof(int32_t) * (size_t)ctx->n_tiles, "tile table");
+    ALLOC(d_tile_set, sizeof(int32_t) * (size_t)ctx->n_tiles, "tile table");
+    ALLOC(d_y, rsz * T, "state y");
+    ALLOC(d_yacc, rsz * T, "state yacc");
+    ALLOC(d_ylo, rsz * T, "state ylo");
+    ALLOC(d_v, rsz * T, "state v");
+    ALLOC(d_e, rsz * T, "state e");
+    ALLOC(d_y0, rsz * T, "state y0");
+    ALLOC(d_cell, sizeof(int32_t) * T, "state cell");
+    if (c.noise == 1) ALLOC(d_xs, sizeof(uint4) * T, "xorshift states");
+    ALLOC(d_hx, sizeof(uint32_t) * (size_t)ctx->n_snap * n_sets * (size_t)std::max(c.hist_x_bins, 0), "x histograms");
+    ALLOC(d_hv, sizeof(uint32_t) * (size_t)ctx->n_snap * n_sets * (size_t)(c.hist_v_bins > 0 ? c.hist_v_bins + 2 : 0),
+          "v histograms");
+    ALLOC(d_ckpt, sizeof(float4) * (size_t)ctx->n_ckpt * T, "checkpoints");
+    ALLOC(d_partials, sizeof(double) * 4 * (size_t)std::max(ctx->n_tiles, 1), "reduction scratch");
+    ALLOC(d_moments, sizeof(double) * 8 * (size_t)std::max(n_sets, 1), "moments");
+    ALLOC(d_queue, sizeof(int32_t) * ((size_t)ctx->n_tiles + 1), "work queue");
+    ALLOC(d_perm, sizeof(int32_t) * (size_t)std::max(ctx->n_tiles, 1), "work queue order");
+    ALLOC(d_set_first, sizeof(int64_t) * ((size_t)n_sets + 1), "set offsets");
+    ALLOC(d_set_order, sizeof(int32_t) * (size_t)std::max(n_sets, 1), "set order");
+#undef ALLOC
+
+    cudaStream_t s = ctx->stream;
+    auto up = [&](DevBuf &b, const void *src, size_t n) -> cudaError_t {
+        return n ? cudaMemcpyAsync(b.p, src, n, cudaMemcpyHostToDevice, s) : cudaSuccess;
+    };
+    cudaError_t e = up(ctx->d_params, ctx->params.data(), sizeof(abp_params) * n_sets);
+    if (e == cudaSuccess) e = up(ctx->d_steps, ctx->n_steps.data(), sizeof(int64_t) * n_sets);
+    if (e == cudaSuccess) e = up(ctx->d_set_tile_begin, ctx->set_tile_begin.data(), sizeof(int32_t) * (n_sets + 1));
+    if (e == cudaSuccess) e = up(ctx->d_tile_first, ctx->tile_first.data(), sizeof(int64_t) * ctx->n_tiles);
+    if (e == cudaSuccess) e = up(ctx->d_tile_count, ctx->tile_count.data(), sizeof(int32_t) * ctx->n_tiles);
+    if (e == cudaSuccess) e = up(ctx->d_tile_set, ctx->tile_set.data(), sizeof(int32_t) * ctx->n_tiles);
+    if (e == cudaSuccess) e = up(ctx->d_perm, ctx->perm.data(), sizeof(int32_t) * ctx->n_tiles);
+    if (e == cudaSuccess) e = up(ctx->d_set_first, ctx->set_first.data(), sizeof(int64_t) * (n_sets + 1));
+    if (e == cudaSuccess) e = up(ctx->d_set_order, ctx->set_order.data(), sizeof(int32_t) * n_sets);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_status.p, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess && ctx->d_hx.bytes) e = cudaMemsetAsync(ctx->d_hx.p, 0, ctx->d_hx.bytes, s);
+    if (e == cudaSuccess && ctx->d_hv.bytes) e = cudaMemsetAsync(ctx->d_hv.p, 0, ctx->d_hv.bytes, s);
+    if (e == cudaSuccess) {
+        e = launch_init(ctx->batch(), ctx->state(), ctx->hist(), ctx->ckpt(), ctx->noise(), s);
+        ctx->launches += ctx->n_tiles > 0 ? 1 : 0;
+    }
+    // The host arrays above are pageable vectors owned by the context; make the
+    // uploads complete before the context can be modified again.
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        ctx->release_batch();
+        return cuda_fail(ctx, e, "upload / initial condition");
+    }
+    return ABP_OK;
+}
+
+
+cudaError_t enqueue_window(abp_ctx *ctx, int64_t g0, int64_t g1, const int32_t *round_start, int32_t n_rounds,
+                           int32_t n_items, int64_t *kernels);
+
+// Enqueue the window [g0, g1) of the configured batch without graph capture (the
+// work queue's round starts uploaded to the context's buffer).
+abp_status enqueue_direct(abp_ctx *ctx, int64_t g0, int64_t g1) {
+    std::vector<int32_t> rs;
+    int32_t n_rounds = 0, n_items = 0;
+    const int32_t *d_rs = nullptr;
+    if (ctx->sched == 2) {
+        rs = round_starts(ctx, g0, g1, ctx->steps_per_launch);
+        n_rounds = (int32_t)rs.size() - 1;
+        n_items = rs.back();
+        if (n_items == 0) return ABP_OK;
+        abp_status st = alloc(ctx, ctx->d_round, sizeof(int32_t) * rs.size(), "work-queue rounds");
+        if (st != ABP_OK) return st;
+        ABP_CUDA(ctx, cudaMemcpyAsync(ctx->d_round.p, rs.data(), sizeof(int32_t) * rs.size(), cudaMemcpyHostToDevice,
+                                      ctx->stream),
+                 "work-queue rounds upload");
+        d_rs = (const int32_t *)ctx->d_round.p;
+    }
+    int64_t k = 0;
+    ABP_CUDA(ctx, enqueue_window(ctx, g0, g1, d_rs, n_rounds, n_items, &k), "integrator launch");
+    ctx->launches += k;
+    return ABP_OK;
+}
+
+// The autotuner's choice for the current batch and how it was reached.
+struct TuneChoice {
+    int sched = 1, ppt = 1;
+    int64_t spl = 1;
+};
+
+struct Candidate {
+    int sched, ppt;
+    int64_t spl;
+    double model_ms;           // model prediction for the whole batch
+    double probe_ms = -1.0;    // measured time of the probe prefix (-1: not probed)
+    double probe_model = 0.0;  // model prediction for the probe prefix
+    double pred_ms = 0.0;      // prediction the choice used
+};
+
+// Choices already made, by batch and configuration, so that a batch set again (a
+// benchmark loop, a resumed run) is not probed again.
+std::mutex g_choice_mu;
+std::map<std::pair<int, uint64_t>, std::pair<TuneChoice, std::string>> g_choices;
+
+uint64_t choice_key(const abp_ctx *ctx) {
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](const void *q, size_t n) {
+        const unsigned char *c = (const unsigned char *)q;
+        for (size_t i = 0; i < n; ++i) {
+            h ^= c[i];
+            h *= 1099511628211ull;
+        }
+    };
+    mix(ctx->params.data(), sizeof(abp_params) * ctx->params.size());
+    mix(ctx->n_traj.data(), sizeof(int64_t) * ctx->n_traj.size());
+    mix(ctx->n_steps.data(), sizeof(int64_t) * ctx->n_steps.size());
+    const abp_config &c = ctx->cfg;
+    const int64_t f[] = {c.state_fp64, c.hist_x_bins, c.hist_v_bins, c.snapshot_every, c.checkpoint_every > 0,
+                         c.particles_per_thread, c.schedule, c.steps_per_launch, c.scheme, c.noise};
+    mix(f, sizeof(f));
+    return h;
+}
+
+// Steps of the probe prefix: about 8e9 particle-steps of the batch (several ms on a
+// GB300), 256 to 16,384 steps, and never more than the longest set.
+int64_t probe_steps(const abp_ctx *ctx) {
+    const double per_step = (double)std::max<int64_t>(ctx->total_traj, 1);
+    int64_t P = (int64_t)std::ceil(8e9 / per_step);
+    P = std::min<int64_t>(std::max<int64_t>(P, 256), 16384);
+    P = (P + 63) / 64 * 64;
+    return std::min(P, ctx->max_steps);
+}
+
+// Configure the batch for candidate c and time its first P steps on the device
+// (after a warm-up window, so that kernel loading is not timed).
+abp_status probe_candidate(abp_ctx *ctx, Candidate &c, int64_t P) {
+    abp_status st = configure_batch(ctx, c.sched, c.ppt, std::min(c.spl, P));
+    if (st != ABP_OK) return st;
+    const int32_t hold = ctx->hold_tile;
+    ctx->hold_tile = -1;
+    cudaStream_t s = ctx->stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) st = enqueue_direct(ctx, 0, std::min<int64_t>(P, 64));
+    if (e == cudaSuccess && st == ABP_OK) {
+        e = launch_init(ctx->batch(), ctx->state(), ctx->hist(), ctx->ckpt(), ctx->noise(), s);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+        if (e == cudaSuccess) st = enqueue_direct(ctx, 0, P);
+        if (e == cudaSuccess && st == ABP_OK) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess && st == ABP_OK) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess && st == ABP_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) c.probe_ms = ms;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    ctx->hold_tile = hold;
+    if (e == cudaSuccess && st == ABP_OK) {
+        int32_t status = 0;  // a probe whose bounded waits expired does not count
+        if (cudaMemcpy(&status, ctx->d_status.p, sizeof(int32_t), cudaMemcpyDeviceToHost) == cudaSuccess && status)
+            c.probe_ms = -1.0;
+        cudaMemsetAsync(ctx->d_status.p, 0, sizeof(int32_t), s);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        c.probe_ms = -1.0;
+    }
+    return st;
+}
+
+// The autotuner: every allowed (schedule, trajectories per thread, steps per launch
+// in {10^3, 10^4, 10^5} up to the longest set) is ranked by the model; when both
+// schedules are allowed, the best candidate of each is then timed on the first steps of
+// this very batch (its tiles, parameters and step counts) and each prediction becomes
+// that measured time scaled by the model's ratio of the whole batch to the prefix; the
+// smaller wins.  The choice is kept per batch and configuration.
+TuneChoice choose_configuration(abp_ctx *ctx) {
+    const abp_config &c = ctx->cfg;
+    TuneChoice tc;
+    const int want_sched = c.schedule, want_ppt = c.particles_per_thread;
+    std::vector<int64_t> spls;
+    if (c.steps_per_launch > 0) {
+        spls.push_back(c.steps_per_launch);
+    } else {
+        for (int64_t S : {1000, 10000, 100000}) {
+            const int64_t v = std::max<int64_t>(1, std::min(S, ctx->max_steps));
+            if (std::find(spls.begin(), spls.end(), v) == spls.end()) spls.push_back(v);
+        }
+    }
+    if (want_sched && want_ppt && spls.size() == 1) {
+        tc.sched = want_sched;
+        tc.ppt = want_ppt;
+        tc.spl = spls[0];
+        ctx->tune_report = "{\"fixed\": true}";
+        return tc;
+    }
+    const std::pair<int, uint64_t> key(ctx->device, choice_key(ctx));
+    {
+        std::lock_guard<std::mutex> lock(g_choice_mu);
+        auto it = g_choices.find(key);
+        if (it != g_choices.end()) {
+            ctx->tune_report = it->second.second;
+            return it->second.first;
+        }
+    }
+    const int dev = ctx->device, kind = tune_kind(ctx);
+    TuneTable local;
+    TuneTable &tt = (dev >= 0 && dev < 64) ? g_tune[dev][kind] : local;
+    if (!tt.done && !load_tune(ctx, tt)) {
+        measure_candidates(ctx, tt);
+        if (tt.done) save_tune(ctx, tt);
+    }
+    std::vector<Candidate> cands;
+    for (int sch = 1; sch <= 2; ++sch) {
+        if (want_sched && sch != want_sched) continue;
+        for (int ppt : {1, 2, 4}) {
+            if (want_ppt && ppt != want_ppt) continue;
+            for (int64_t spl : spls) {
+                Candidate cd{sch, ppt, spl, 0.0};
+                cd.model_ms = model_ms(ctx, tt, sch, ppt, spl, ctx->n_sets, ctx->n_traj.data(), ctx->n_steps.data());
+                cd.pred_ms = cd.model_ms;
+                if (cd.model_ms < 1e299) cands.push_back(cd);
+            }
+        }
+    }
+    if (cands.empty()) cands.push_back(Candidate{want_sched ? want_sched : 1, want_ppt ? want_ppt : 1, spls[0], 0.0});
+    // the best candidate of each schedule by the model
+    int best_of[3] = {-1, -1, -1};
+    for (int i = 0; i < (int)cands.size(); ++i) {
+        int &b = best_of[cands[i].sched];
+        if (b < 0 || cands[i].model_ms < cands[b].model_ms) b = i;
+    }
+    const int64_t P = probe_steps(ctx);
+    const bool probe = best_of[1] >= 0 && best_of[2] >= 0 && ctx->total_traj > 0 && P > 0;
+    if (probe) {
+        std::vector<int64_t> Np(ctx->n_steps);
+        for (int64_t &v : Np) v = std::min(v, P);
+        for (int sch = 1; sch <= 2; ++sch) {
+            Candidate &cd = cands[best_of[sch]];
+            cd.probe_model = model_ms(ctx, tt, cd.sched, cd.ppt, std::min(cd.spl, P), ctx->n_sets,
+                                      ctx->n_traj.data(), Np.data());
+            if (probe_candidate(ctx, cd, P) != ABP_OK) cd.probe_ms = -1.0;
+            if (cd.probe_ms > 0.0 && cd.probe_model > 0.0) cd.pred_ms = cd.probe_ms * cd.model_ms / cd.probe_model;
+        }
+        // a schedule whose probe failed is not chosen over one that was measured
+        for (int sch = 1; sch <= 2; ++sch)
+            if (cands[best_of[sch]].probe_ms < 0.0 && cands[best_of[3 - sch]].probe_ms > 0.0)
+                cands[best_of[sch]].pred_ms = 1e300;
+    }
+    int best = -1;
+    for (int i = 0; i < (int)cands.size(); ++i) {
+        if (probe && i != best_of[1] && i != best_of[2]) continue;  // the two probed candidates decide
+        if (best < 0 || cands[i].pred_ms < cands[best].pred_ms) best = i;
+    }
+    tc.sched = cands[best].sched;
+    tc.ppt = cands[best].ppt;
+    tc.spl = cands[best].spl;
+    std::string rep = "{\"probe_steps\": " + std::to_string(probe ? P : 0) + ", \"candidates\": [";
+    char buf[256];
+    for (size_t i = 0; i < cands.size(); ++i) {
+        const Candidate &cd = cands[i];
+        snprintf(buf, sizeof(buf),
+                 "%s{\"schedule\": %d, \"ppt\": %d, \"steps\": %lld, \"model_ms\": %.4g, \"probe_ms\": %.4g, "
+                 "\"predicted_ms\": %.4g}",
+                 i ? ", " : "", cd.sched, cd.ppt, (long long)cd.spl, cd.model_ms, cd.probe_ms, cd.pred_ms);
+        rep += buf;
+    }
+    snprintf(buf, sizeof(buf), "], \"chosen\": {\"schedule\": %d, \"ppt\": %d, \"steps\": %lld}}", tc.sched, tc.ppt,
+             (long long)tc.spl);
+    rep += buf;
+    ctx->tune_report = rep;
+    {
+        std::lock_guard<std::mutex> lock(g_choice_mu);
+        g_choices[key] = std::make_pair(tc, rep);
+    }
+    return tc;
 }
 
 }  // namespace
@@ -685,112 +1015,9 @@ abp_status abp_set_params(abp_ctx *ctx, int32_t n_sets, const abp_params *sets, 
     ctx->g = 0;
     ctx->ckpt_complete = true;
 
-    autotune(ctx);
-    {
-        TilePlan plan;
-        if (!plan_tiles(n_sets, n_traj, n_steps, ctx->sched, ctx->ppt, ctx->cfg.checkpoint_every > 0, ctx->sm_count,
-                        plan))
-            return fail(ctx, ABP_EINVAL, "too many tiles");
-        ctx->set_first.swap(plan.set_first);
-        ctx->set_packed.swap(plan.set_packed);
-        ctx->set_tile_begin.swap(plan.set_tile_begin);
-        ctx->tile_first.swap(plan.tile_first);
-        ctx->tile_count.swap(plan.tile_count);
-        ctx->tile_set.swap(plan.tile_set);
-        ctx->set_order.swap(plan.set_order);
-        ctx->n_single = plan.n_single;
-        ctx->n_tiles = (int32_t)ctx->tile_first.size();
-        ctx->n_unpacked = plan.n_unpacked;
-        ctx->narrow = plan.narrow;
-        ctx->sub_single = plan.sub_single;
-        ctx->sub_packed = plan.sub_packed;
-    }
-    const abp_config &c = ctx->cfg;
-    const bool any_hist = c.hist_x_bins > 0 || c.hist_v_bins > 0;
-    // snapshot slots: one per S steps when snapshot_every = S > 0 (histograms and live
-    // results use them), else one final histogram snapshot when there are histograms
-    ctx->n_snap = c.snapshot_every > 0 ? max_n / c.snapshot_every : (any_hist ? 1 : 0);
-    ctx->n_ckpt = c.checkpoint_every > 0 ? max_n / c.checkpoint_every + 1 : 0;
-    // Work-queue order: tiles by decreasing step count of their set (stable).
-    ctx->perm.resize(ctx->n_tiles);
-    for (int32_t t = 0; t < ctx->n_tiles; ++t) ctx->perm[t] = t;
-    std::stable_sort(ctx->perm.begin(), ctx->perm.end(), [&](int32_t a, int32_t b) {
-        return ctx->n_steps[ctx->tile_set[a]] > ctx->n_steps[ctx->tile_set[b]];
-    });
-    ctx->perm_steps.resize(ctx->n_tiles);
-    for (int32_t k = 0; k < ctx->n_tiles; ++k) ctx->perm_steps[k] = ctx->n_steps[ctx->tile_set[ctx->perm[k]]];
-    {
-        int bps = 0;
-        const size_t smem = sizeof(uint32_t) * (size_t)(std::max(c.hist_x_bins, 0) +
-                                                        (c.hist_v_bins > 0 ? c.hist_v_bins + 2 : 0));
-        cudaError_t oe =
-            persistent_occupancy(c.state_fp64 != 0, ctx->ppt, smem, &bps, c.scheme == 1 ? 1 : c.noise == 1 ? 2 : 0);
-        if (oe != cudaSuccess) return cuda_fail(ctx, oe, "occupancy query");
-        ctx->grid = std::max(bps, 1) * std::max(ctx->sm_count, 1);
-    }
-    if (c.steps_per_launch > 0)
-        ctx->steps_per_launch = c.steps_per_launch;
-    else
-        ctx->steps_per_launch = ctx->sched == 1 ? default_steps_per_launch(ctx) : choose_round_steps(ctx);
-
-    const size_t T = (size_t)total;
-    const size_t rsz = c.state_fp64 ? sizeof(double) : sizeof(float);
-    abp_status st = ABP_OK;
-#define ALLOC(buf, bytes, what) \
-    if ((st = alloc(ctx, ctx->buf, (bytes), what)) != ABP_OK) { ctx->release_all(); return st; }
-    ALLOC(d_params, sizeof(abp_params) * (size_t)n_sets, "parameters");
-    ALLOC(d_steps, sizeof(int64_t) * (size_t)n_sets, "step counts");
-    ALLOC(d_set_tile_begin, sizeof(int32_t) * ((size_t)n_sets + 1), "set tiles");
-    ALLOC(d_tile_first, sizeof(int64_t) * (size_t)ctx->n_tiles, "tile table");
-    ALLOC(d_tile_count, sizeof(int32_t) * (size_t)ctx->n_tiles, "tile table");
-    ALLOC(d_tile_set, sizeof(int32_t) * (size_t)ctx->n_tiles, "tile table");
-    ALLOC(d_y, rsz * T, "state y");
-    ALLOC(d_yacc, rsz * T, "state yacc");
-    ALLOC(d_ylo, rsz * T, "state ylo");
-    ALLOC(d_v, rsz * T, "state v");
-    ALLOC(d_e, rsz * T, "state e");
-    ALLOC(d_y0, rsz * T, "state y0");
-    ALLOC(d_cell, sizeof(int32_t) * T, "state cell");
-    if (c.noise == 1) ALLOC(d_xs, sizeof(uint4) * T, "xorshift states");
-    ALLOC(d_hx, sizeof(uint32_t) * (size_t)ctx->n_snap * n_sets * (size_t)std::max(c.hist_x_bins, 0), "x histograms");
-    ALLOC(d_hv, sizeof(uint32_t) * (size_t)ctx->n_snap * n_sets * (size_t)(c.hist_v_bins > 0 ? c.hist_v_bins + 2 : 0),
-          "v histograms");
-    ALLOC(d_ckpt, sizeof(float4) * (size_t)ctx->n_ckpt * T, "checkpoints");
-    ALLOC(d_partials, sizeof(double) * 4 * (size_t)std::max(ctx->n_tiles, 1), "reduction scratch");
-    ALLOC(d_moments, sizeof(double) * 8 * (size_t)std::max(n_sets, 1), "moments");
-    ALLOC(d_queue, sizeof(int32_t) * ((size_t)ctx->n_tiles + 1), "work queue");
-    ALLOC(d_perm, sizeof(int32_t) * (size_t)std::max(ctx->n_tiles, 1), "work queue order");
-    ALLOC(d_set_first, sizeof(int64_t) * ((size_t)n_sets + 1), "set offsets");
-    ALLOC(d_set_order, sizeof(int32_t) * (size_t)std::max(n_sets, 1), "set order");
-#undef ALLOC
-
-    cudaStream_t s = ctx->stream;
-    auto up = [&](DevBuf &b, const void *src, size_t n) -> cudaError_t {
-        return n ? cudaMemcpyAsync(b.p, src, n, cudaMemcpyHostToDevice, s) : cudaSuccess;
-    };
-    cudaError_t e = up(ctx->d_params, ctx->params.data(), sizeof(abp_params) * n_sets);
-    if (e == cudaSuccess) e = up(ctx->d_steps, ctx->n_steps.data(), sizeof(int64_t) * n_sets);
-    if (e == cudaSuccess) e = up(ctx->d_set_tile_begin, ctx->set_tile_begin.data(), sizeof(int32_t) * (n_sets + 1));
-    if (e == cudaSuccess) e = up(ctx->d_tile_first, ctx->tile_first.data(), sizeof(int64_t) * ctx->n_tiles);
-    if (e == cudaSuccess) e = up(ctx->d_tile_count, ctx->tile_count.data(), sizeof(int32_t) * ctx->n_tiles);
-    if (e == cudaSuccess) e = up(ctx->d_tile_set, ctx->tile_set.data(), sizeof(int32_t) * ctx->n_tiles);
-    if (e == cudaSuccess) e = up(ctx->d_perm, ctx->perm.data(), sizeof(int32_t) * ctx->n_tiles);
-    if (e == cudaSuccess) e = up(ctx->d_set_first, ctx->set_first.data(), sizeof(int64_t) * (n_sets + 1));
-    if (e == cudaSuccess) e = up(ctx->d_set_order, ctx->set_order.data(), sizeof(int32_t) * n_sets);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_status.p, 0, sizeof(int32_t), s);
-    if (e == cudaSuccess && ctx->d_hx.bytes) e = cudaMemsetAsync(ctx->d_hx.p, 0, ctx->d_hx.bytes, s);
-    if (e == cudaSuccess && ctx->d_hv.bytes) e = cudaMemsetAsync(ctx->d_hv.p, 0, ctx->d_hv.bytes, s);
-    if (e == cudaSuccess) {
-        e = launch_init(ctx->batch(), ctx->state(), ctx->hist(), ctx->ckpt(), ctx->noise(), s);
-        ctx->launches += ctx->n_tiles > 0 ? 1 : 0;
-    }
-    // The host arrays above are pageable vectors owned by the context; make the
-    // uploads complete before the context can be modified again.
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) {
-        ctx->release_batch();
-        return cuda_fail(ctx, e, "upload / initial condition");
-    }
+    const TuneChoice tc = choose_configuration(ctx);
+    const abp_status st = configure_batch(ctx, tc.sched, tc.ppt, tc.spl);
+    if (st != ABP_OK) return st;
     ctx->have_batch = true;
     return ABP_OK;
 }
@@ -1120,7 +1347,7 @@ abp_status abp_plan_efficiency(int32_t n_sets, const int64_t *n_traj, const int6
         total += n_traj[i];
         max_n = std::max(max_n, n_steps[i]);
     }
-    const int64_t spl = steps_per_launch > 0 ? steps_per_launch : default_window(total, max_n);
+    const int64_t spl = steps_per_launch > 0 ? steps_per_launch : schedule == 1 ? default_window(total, max_n) : 0;
     *efficiency = batch_efficiency(n_sets, n_traj, n_steps, schedule, particles_per_thread, checkpoints != 0, spl,
                                    resident_blocks);
     return ABP_OK;
@@ -1166,6 +1393,18 @@ abp_status abp_tuning(const abp_ctx *ctx, int32_t *schedule, int32_t *particles_
             else
                 cudaGetLastError();
         }
+    }
+    return ABP_OK;
+}
+
+abp_status abp_tuning_report(const abp_ctx *ctx, char *buf, size_t len, size_t *needed) {
+    if (!ctx) return ABP_EINVAL;
+    const std::string &r = ctx->tune_report;
+    if (needed) *needed = r.size() + 1;
+    if (buf && len) {
+        const size_t n = std::min(len - 1, r.size());
+        memcpy(buf, r.data(), n);
+        buf[n] = '\0';
     }
     return ABP_OK;
 }

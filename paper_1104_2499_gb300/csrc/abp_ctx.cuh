@@ -55,6 +55,7 @@ struct abp_ctx {
     int ppt = 1;
     int sched = 1;                 // 1: lockstep launches, 2: work queue (autotuned when cfg.schedule = 0)
     int64_t steps_per_launch = 0;  // lockstep: steps per launch; work queue: steps per round
+    std::string tune_report;       // the autotuner's candidates and choice for the batch (JSON text)
     int grid = 0;                  // work queue: resident blocks of the persistent launch
     int32_t hold_tile = -1;        // test hook (abp_test_hold_tile)
     int64_t wait_limit_ns = 60000000000LL;

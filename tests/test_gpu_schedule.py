@@ -97,11 +97,8 @@ def test_autotuner_choices(abp):
     with abp.Ensemble(w, schedule=2) as ens:
         ens.set_params()
         t = ens.tuning()
-    assert t["schedule"] == 2 and t["steps_per_item"] in (1000, 10_000, 100_000)
-    # enough items per resident block for the last ones to be a small tail
-    items = sum(math.ceil(n / t["steps_per_item"]) * math.ceil(m / (256 * t["particles_per_thread"]))
-                for m, n in zip(w.n_traj, w.n_steps))
-    assert items >= 32 * t["blocks"] or t["steps_per_item"] == 1000
+    # steps per work item from 10^3, 10^4, 10^5, capped at the longest set (2 x 10^4 here)
+    assert t["schedule"] == 2 and t["steps_per_item"] in (1000, 10_000, 20_000)
 
 
 def test_autotuner_weighs_the_batch(abp):
@@ -145,3 +142,50 @@ def test_bounded_wait_reports_timeout_and_context_recovers(abp):
         st = ens.state()
         for k in st:
             assert torch.equal(st[k], ref_state[k]), k
+
+
+def _timed(abp, w, **kw):
+    stream = torch.cuda.Stream()
+    with abp.Ensemble(w, stream=stream, **kw) as ens, torch.cuda.stream(stream):
+        ens.set_params()
+        ens.integrate(-1)
+        ens.results()
+        ens.reset(w.seed)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ens.integrate(-1)
+        ens.results()
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b), ens.tuning(), ens.tuning_report()
+
+
+def test_autotuner_report_records_the_probe(abp):
+    # with both schedules allowed, the best candidate of each is timed on the batch's first
+    # steps; the choice is the smaller prediction among the two probed candidates
+    w = W.force_sweep(n_steps=20_000)
+    with abp.Ensemble(w) as ens:
+        ens.set_params()
+        rep = ens.tuning_report()
+        t = ens.tuning()
+    probed = [c for c in rep["candidates"] if c["probe_ms"] > 0]
+    assert rep["probe_steps"] > 0 and sorted(c["schedule"] for c in probed) == [1, 2]
+    best = min(probed, key=lambda c: c["predicted_ms"])
+    assert rep["chosen"] == {"schedule": best["schedule"], "ppt": best["ppt"], "steps": best["steps"]}
+    assert (t["schedule"], t["particles_per_thread"], t["steps_per_item"]) == (best["schedule"], best["ppt"],
+                                                                               best["steps"])
+    assert all(c["steps"] in (1000, 10_000, 20_000) for c in rep["candidates"])
+
+
+@pytest.mark.parametrize("name", ["uneven", "single"])
+def test_autotuned_choice_is_not_beaten_by_the_other_schedule(abp, name):
+    # the uneven batch (512 sets, 256 to 65,536 trajectories, 10^4 to 10^6 steps) is what the
+    # persistent work queue exists for; the single 4,096-trajectory set runs narrow lockstep
+    # blocks.  Measured before the probe: the uneven batch got lockstep at 2.4% below the
+    # work queue, the single set the work queue at a third of lockstep's rate.  The autotuned
+    # run must be within 2% of the other schedule's best (at its own autotuned settings).
+    w = W.uneven_batch() if name == "uneven" else W.single_set()
+    t_auto, tun, rep = _timed(abp, w)
+    other = 2 if tun["schedule"] == 1 else 1
+    t_other, _, _ = _timed(abp, w, schedule=other)
+    assert t_auto <= 1.02 * t_other, (name, t_auto, t_other, tun, rep)
