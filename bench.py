@@ -314,9 +314,9 @@ def adjoint_leg(A, stream, small=False, size=None, accuracy=True):
         g_win = ens.backward(window=win).cpu().numpy()[0] if win % w.checkpoint_every == 0 else None
     windowed = None
     if g_win is not None and accuracy:
-        # the oracle's windowed tangent on 1,024 trajectories of the same set: its mean and
+        # the oracle's windowed tangent on 8,192 trajectories of the same set: its mean and
         # standard error (paths decorrelate over the horizon, so this is a statistical check)
-        sub = 1024
+        sub = 8192
         r = O.run_set(w.sets[0], seed=w.seed, dt=w.dt, n_traj=sub, n_steps=w.n_steps[0], v0_mode=w.v0_mode,
                       want_traj_grad=True, grad_window=win)
         se = r["dvbar"].std(axis=0, ddof=1) / math.sqrt(sub)
@@ -324,7 +324,10 @@ def adjoint_leg(A, stream, small=False, size=None, accuracy=True):
         windowed = {"window_steps": win, "grad_gpu": dict(zip(A.GRAD_PARAMS, map(float, g_win))),
                     "oracle_subset_mean": dict(zip(A.GRAD_PARAMS, map(float, r["grad"]))),
                     "oracle_subset_se": dict(zip(A.GRAD_PARAMS, map(float, se))),
+                    "oracle_se_over_abs_grad": dict(zip(A.GRAD_PARAMS, map(float, se / np.maximum(np.abs(g_win),
+                                                                                                  1e-300)))),
                     "max_abs_diff_over_se": float(z.max()), "oracle_subset_trajectories": sub}
+    per_traj = per_trajectory_check(A, stream, w) if accuracy and size is None and not small else None
 
     def check(n_steps, rel_h, K):
         wa = W.differentiation(n_traj=4096, n_steps=n_steps, checkpoint_every=K)
@@ -353,7 +356,36 @@ def adjoint_leg(A, stream, small=False, size=None, accuracy=True):
     return {"workload": w.name, "particle_steps": w.particle_steps, "checkpoint_every": w.checkpoint_every,
             "forward_ms": fwd_ms, "backward_ms": bwd_ms, "backward_over_forward": bwd_ms / fwd_ms,
             "max_abs_pathwise_grad_full_horizon": float(np.max(np.abs(g_full))),
-            "windowed": windowed, "accuracy": acc}
+            "windowed": windowed, "per_trajectory": per_traj, "accuracy": acc}
+
+
+def per_trajectory_check(A, stream, w_full, n_steps=2000, n_check=4096):
+    """The differentiation workload's set (all 1,048,576 trajectories, D = 0.05, seed 3) over
+    its first 2,000 steps, where the frozen-noise paths of the FP32 GPU and the FP64 oracle stay
+    together, so the comparison is deterministic trajectory by trajectory: the GPU's pathwise
+    d vbar_i / d theta (abp_backward_traj) of the first 4,096 trajectories against the oracle's
+    tangent-linear of the same trajectories.  Bar: 1e-3 max(|oracle|, rms_j), rms_j the root
+    mean square of component j over the checked trajectories."""
+    import numpy as np
+    import torch
+    from oracle import oracle as O
+    from paper_1104_2499_gb300 import workloads as W
+
+    w = W.differentiation(n_traj=w_full.n_traj[0], n_steps=n_steps)
+    with A.Ensemble(w, stream=stream) as ens, torch.cuda.stream(stream):
+        ens.run()
+        g = ens.backward(host=True).numpy()[0]
+        dv = ens.traj_grad()[:n_check].cpu().numpy()
+    r = O.run_set(w.sets[0], seed=w.seed, dt=w.dt, n_traj=n_check, n_steps=n_steps, v0_mode=w.v0_mode,
+                  want_traj_grad=True)
+    ref = r["dvbar"]
+    rms = np.sqrt(np.mean(ref ** 2, axis=0))
+    ratio = np.abs(dv - ref) / (1e-3 * np.maximum(np.abs(ref), rms))
+    return {"workload": w.name, "trajectories_checked": n_check, "bar": "1e-3 max(|oracle|, rms over trajectories)",
+            "max_ratio": dict(zip(A.GRAD_PARAMS, map(float, ratio.max(axis=0)))),
+            "fraction_within_bar": float(np.mean(np.all(ratio <= 1.0, axis=1))),
+            "gpu_set_gradient_all_trajectories": dict(zip(A.GRAD_PARAMS, map(float, g))),
+            "oracle_mean_checked_trajectories": dict(zip(A.GRAD_PARAMS, map(float, r["grad"])))}
 
 
 # ----------------------------------------------------------------------------- visualisation leg
