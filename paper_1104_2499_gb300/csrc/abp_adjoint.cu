@@ -54,6 +54,11 @@ constexpr int kRevPairThreads = ABP_ADJ_REV_PAIR_THREADS;
 #ifndef ABP_ADJ_L1_PAIRS
 #define ABP_ADJ_L1_PAIRS 1
 #endif
+// Aligned whole chunks of the paired level 1 stepped in groups of this many per
+// loop iteration (1: one chunk per iteration).
+#ifndef ABP_ADJ_L1_GROUP
+#define ABP_ADJ_L1_GROUP 4
+#endif
 // Threads per block of the register-heavy reverse kernel (a multiple of 32).
 constexpr int kRevThreads = ABP_ADJ_REV_THREADS;
 // Threads per block of the level-1 kernel: small blocks, so that one fits on
@@ -233,7 +238,52 @@ __device__ __forceinline__ void level1_segment2(const AdjArgs &a, const Coef<flo
     NoiseCursor nc[2];
     nc[0].valid = nc[1].valid = false;
     nc[0].m = nc[1].m = 0;
-    for (int j = 0; j < n_chunks; ++j) {
+    int j = 0;
+#if ABP_ADJ_L1_GROUP > 1
+    // aligned whole chunks in groups of ABP_ADJ_L1_GROUP: one loop iteration per group
+    if (aligned) {
+        const int full = (int)((s1 - s0) / kSub);
+        float2 Y = make_float2(yacc[0], yacc[1]), V = make_float2(v[0], v[1]), E = make_float2(e[0], e[1]);
+        float2 PB = make_float2(pb[0], pb[1]);
+        for (; j + ABP_ADJ_L1_GROUP <= full; j += ABP_ADJ_L1_GROUP) {
+#pragma unroll
+            for (int c = 0; c < ABP_ADJ_L1_GROUP; ++c) {
+                const int jc = j + c;
+                const int64_t n0 = s0 + (int64_t)jc * kSub;
+                const size_t js = (size_t)dchk(jc, a.n_sub, a.b.dbg);
+                a.sub[js * T + idx[0]] = make_float4(y[0], Y.x, V.x, E.x);
+                if (store1) a.sub[js * T + idx[1]] = make_float4(y[1], Y.y, V.y, E.y);
+#pragma unroll
+                for (int b2 = 0; b2 < kSub / 4; ++b2) {
+                    const uint32_t m = (uint32_t)(n0 >> 2) + b2;
+                    const uint4 w0 = step_block(m, ss[0], a.K), w1 = step_block(m, ss[1], a.K);
+                    float2 nr, cs, sn;
+                    box_muller_f32x2(make_uint2(w0.x, w1.x), make_uint2(w0.y, w1.y), k2.bm, nr, cs, sn);
+                    em_step_f32x2(k2, nr, cs, PB, Y, V, E);
+                    em_step_f32x2(k2, nr, sn, PB, Y, V, E);
+                    box_muller_f32x2(make_uint2(w0.z, w1.z), make_uint2(w0.w, w1.w), k2.bm, nr, cs, sn);
+                    em_step_f32x2(k2, nr, cs, PB, Y, V, E);
+                    em_step_f32x2(k2, nr, sn, PB, Y, V, E);
+                }
+                if (((n0 + kSub) & (kBlockSteps - 1)) == 0) {
+                    yacc[0] = Y.x;
+                    yacc[1] = Y.y;
+                    fold(y[0], yacc[0], pb[0]);
+                    fold(y[1], yacc[1], pb[1]);
+                    Y = make_float2(yacc[0], yacc[1]);
+                    PB = make_float2(pb[0], pb[1]);
+                }
+            }
+        }
+        yacc[0] = Y.x;
+        yacc[1] = Y.y;
+        v[0] = V.x;
+        v[1] = V.y;
+        e[0] = E.x;
+        e[1] = E.y;
+    }
+#endif
+    for (; j < n_chunks; ++j) {
         const int64_t n0 = s0 + (int64_t)j * kSub;
         const size_t js = (size_t)dchk(j, a.n_sub, a.b.dbg);
         a.sub[js * T + idx[0]] = make_float4(y[0], yacc[0], v[0], e[0]);
