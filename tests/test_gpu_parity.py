@@ -301,3 +301,24 @@ def test_paired_steps_match_scalar_steps_bitwise(abp, scheme, noise):
         for k in ref_r:
             if k != "moments":  # the FP64 summation tree follows the tiles, and so PPT
                 assert torch.equal(ref_r[k], r[k]), (kw, k)
+
+
+def test_trajectory_ids_across_the_32_bit_boundary(abp):
+    # the Philox counter carries the global trajectory id as (lo, hi) 32-bit words: a shard
+    # whose ids run from 2^32 - 300 across 2^32, and one just below 2^40, must step every
+    # trajectory as the oracle does (first 10^3 steps, the 1e-4 bar)
+    sets = [W._with(D=0.1), W._with(D=0.3, q=2.0, asym=0.1)]
+    for first in (2**32 - 300, 2**40 - 700):
+        w = W.Workload(name="ids", sets=sets, n_traj=[400, 300], n_steps=[1000, 999], dt=1e-3, seed=19, v0_mode=1)
+        with abp.Ensemble(w, traj_base=first) as ens:
+            ens.run()
+            st = {k: v.cpu().numpy() for k, v in ens.state().items()}
+        base = w.traj_base()
+        for i, p in enumerate(w.sets):
+            r = O.run_set(p, seed=w.seed, dt=w.dt, n_traj=w.n_traj[i], n_steps=w.n_steps[i],
+                          traj_base=first + base[i], v0_mode=w.v0_mode, want_states=True)
+            sl = slice(base[i], base[i] + w.n_traj[i])
+            sv = math.sqrt(p["D"] / p["gamma0"])
+            for key, s in (("x", p["L"]), ("v", sv), ("e", p["q"] / p["c"]), ("x0", p["L"])):
+                bound = 1e-4 * np.maximum(np.abs(r[key]), s)
+                assert np.all(np.abs(st[key][sl] - r[key]) <= bound), (first, i, key)
