@@ -101,3 +101,18 @@ def test_invalid_plans_are_refused(A):
         A.abp_plan([10], [10], schedule=1, particles_per_thread=3)
     with pytest.raises(A.AbpError):
         A.abp_plan([-1], [10], schedule=1, particles_per_thread=1)
+
+
+def test_work_queue_tail_follows_the_item_size(A):
+    # the work queue's model: the tile-steps spread over the resident blocks plus half a work
+    # item of tail, at the item size the candidate uses (the autotuner ranks 10^3, 10^4, 10^5)
+    M, N, cap = [4096] * 64, [100_000] * 64, 304
+    tile_steps = 512 * 100_000  # 64 sets x 8 tiles of 512 trajectories (two per thread)
+    useful = 64 * 4096 * 100_000
+    for S in (1000, 10_000, 100_000):
+        e = A.abp_plan_efficiency(M, N, 2, 2, resident_blocks=cap, steps_per_launch=S)
+        span = tile_steps / cap + 0.5 * S
+        assert e == pytest.approx(useful / (cap * span * 512), rel=1e-12), S
+    e1 = A.abp_plan_efficiency(M, N, 2, 2, resident_blocks=cap, steps_per_launch=1000)
+    e5 = A.abp_plan_efficiency(M, N, 2, 2, resident_blocks=cap, steps_per_launch=100_000)
+    assert e1 > 0.99 and e5 < 0.8
