@@ -309,8 +309,11 @@ ABP_API abp_status abp_tiles(const abp_ctx *ctx, int32_t *n_tiles, int32_t *n_pa
  * abp_plan_efficiency: the fraction of the launch capacity (resident_blocks
  * blocks of 256 * particles_per_thread trajectories) the batch keeps busy, in
  * particle-steps; the autotuner predicts a candidate's time on a batch as its
- * trial time x the trial batch's fraction / the batch's fraction;
- * steps_per_launch 0 = the default lockstep window. */
+ * trial time x the trial batch's fraction / the batch's fraction (plus the
+ * state traffic and fixed costs of its launches);  steps_per_launch = the
+ * lockstep window or the work queue's item size, 0 = a window of about 2e10
+ * particle-steps (lockstep) or the largest of 10^5, 10^4, 10^3 steps that gives
+ * every resident block 32 items (work queue). */
 ABP_API abp_status abp_plan(int32_t n_sets, const int64_t *n_traj, const int64_t *n_steps, int32_t schedule,
                             int32_t particles_per_thread, int32_t checkpoints, int32_t sm_count, int32_t *n_tiles,
                             int32_t *n_packed, int32_t *narrow, int64_t *tile_first, int32_t *tile_count,
