@@ -100,3 +100,26 @@ def test_replica_ids_follow_the_rank(abp):
         ref = ens.state()
     for k in rep:
         assert torch.equal(rep[k], ref[k][T:]), k
+
+
+def test_combining_many_sets_on_the_device(abp):
+    # the device form takes the sets in launches of 128: 300 sets, random sums and sizes (zero
+    # trajectories, one, zero steps included), bitwise the host form
+    rng = np.random.default_rng(5)
+    n = 300
+    m = np.zeros((n, 8))
+    m[:, 4] = rng.normal(size=n)
+    m[:, 5] = m[:, 4] ** 2 + rng.uniform(0, 1, n)
+    m[:, 6] = rng.normal(size=n)
+    m[:, 7] = m[:, 6] ** 2 + rng.uniform(0, 1, n)
+    M = rng.integers(0, 5000, n)
+    M[:3] = [0, 1, 2]
+    N = rng.integers(0, 10 ** 5, n)
+    N[3] = 0
+    host = m.copy()
+    abp.abp_combine_moments(host, M.tolist(), N.tolist(), 1e-3)
+    dev = torch.from_numpy(m).cuda()
+    abp.abp_combine_moments(dev, M.tolist(), N.tolist(), 1e-3)
+    torch.cuda.synchronize()
+    assert np.array_equal(dev.cpu().numpy(), host)
+    assert np.all(host[0, :4] == 0) and host[1, 1] == 0.0 and host[3, 3] == 0.0
