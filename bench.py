@@ -37,7 +37,7 @@ LANES_PER_SM = 128
 # DRAM bytes (read + write) per launch of the integrator on the 2,097,152-trajectory sweep grid,
 # from one ncu capture of that kernel (dram__bytes_read.sum + dram__bytes_write.sum); the traffic
 # is the state load/store, independent of the steps per launch.
-TRAFFIC_PER_LAUNCH = {"integrate_kernel<float,2>": (52523776 + 1556736, 2097152)}
+TRAFFIC_PER_LAUNCH = {"integrate_kernel<float,2>": (52523008 + 1700352, 2097152)}
 
 
 def parse():
