@@ -813,10 +813,12 @@ uint64_t choice_key(const abp_ctx *ctx) {
 }
 
 // Steps of the probe prefix: about 8e9 particle-steps of the batch (several ms on a
-// GB300), 256 to 16,384 steps, and never more than the longest set.
+// GB300; 1/64 of that for the FP64 state, which steps ~100x slower), 256 to 16,384
+// steps, and never more than the longest set.
 int64_t probe_steps(const abp_ctx *ctx) {
     const double per_step = (double)std::max<int64_t>(ctx->total_traj, 1);
-    int64_t P = (int64_t)std::ceil(8e9 / per_step);
+    const double target = ctx->cfg.state_fp64 ? 8e9 / 64.0 : 8e9;
+    int64_t P = (int64_t)std::ceil(target / per_step);
     P = std::min<int64_t>(std::max<int64_t>(P, 256), 16384);
     P = (P + 63) / 64 * 64;
     return std::min(P, ctx->max_steps);
