@@ -715,7 +715,7 @@ __global__ void __launch_bounds__(kThreads) adjoint_traj_kernel(AdjArgs a, SegVi
     const int64_t first = b.tile_first[tile];
     const int count = b.tile_count[tile];
     for (int li = threadIdx.x; li < count; li += blockDim.x) {
-        const int64_t idx = first + li;
+        const int64_t idx = dchk(first + li, T, b.dbg);
         double G[6];
 #pragma unroll
         for (int q = 0; q < 6; ++q) G[q] = sv.G[(size_t)q * T + idx];

@@ -4,8 +4,9 @@ access and records status 3 (reported as ABP_ESTATE) on a violation.
 
 Bar: a child process runs the same workloads against the release and the checked library --
 ragged batches with one-set and packed tiles, snapshots and split launches under both
-schedules, stochastic Heun, xorshift noise, a warp-specialised narrow launch, and the full and
-windowed adjoint -- and no check may fail, and every state, result and gradient must be the
+schedules, stochastic Heun, xorshift noise, a warp-specialised narrow launch, the full and
+windowed adjoint with its per-trajectory readout, and the combination of moments on the device --
+and no check may fail, and every state, result and gradient must be the
 release library's bits (the checks change no arithmetic)."""
 import os
 import subprocess
@@ -57,7 +58,18 @@ with A.Ensemble(w, schedule=1, particles_per_thread=2) as ens:
     ens.run()
     out["adjoint/grad"] = ens.backward(host=True).numpy()
     out["adjoint/windowed"] = ens.backward(host=True, window=666).numpy()
+    out["adjoint/traj"] = ens.traj_grad(host=True).numpy()
     ens.synchronize()
+w.checkpoint_every = 500
+with A.Ensemble(w, schedule=1, particles_per_thread=2) as ens:
+    ens.run()
+    out["adjoint500/grad"] = ens.backward(host=True).numpy()
+    out["adjoint500/traj"] = ens.traj_grad(host=True).numpy()
+    mom = ens.results()["moments"]
+    mom[:, :4] = 0.0
+    A.abp_combine_moments(mom, w.n_traj, w.n_steps, w.dt)
+    ens.synchronize()
+    out["combine"] = mom.cpu().numpy()
 np.savez(sys.argv[1], **out)
 '''
 
