@@ -359,18 +359,17 @@ __device__ __forceinline__ void group_step(const Coef<R> &k, const RoundKeys &K,
 // lockstep FP32 Euler-Maruyama kernel with two trajectories per thread runs
 // fastest with 8 blocks (32 steps) per iteration on the D x q sweep, 1.038e12
 // against 1.011e12 particle-steps/s with 2 and 0.98e12 with 12 (a body that no
-// longer fits the instruction cache).  The work-queue kernel takes 6: it then
-// needs 92 registers and runs two blocks per SM, and on the batches the
-// autotuner gives it (few waves of tiles) fewer resident blocks wait less on
-// their tile's previous round -- load sweep 9.82e11 against 8.9e11-9.0e11 with
-// 8, uneven batch 9.85e11 against 9.8e11 (on the many-tile sweep 8 is 2% faster,
-// but the sweep runs lockstep).  The other kernels keep the default, where longer
-// bodies cost registers and blocks per SM without a measured gain.
+// longer fits the instruction cache).  The work-queue kernel takes 8 as well, at
+// 92 registers and two blocks per SM: against 6 (the same registers), uneven
+// batch 1.005e12 against 9.89e11, load sweep 9.95e11 against 9.83e11, D x q sweep
+// 1.020e12 against 1.006e12; capped at 80 registers for three blocks per SM it
+// spills and loses 8% on the load sweep.  The other kernels keep the default,
+// where longer bodies cost registers and blocks per SM without a measured gain.
 #ifndef ABP_UNROLL_EM2
 #define ABP_UNROLL_EM2 8
 #endif
 #ifndef ABP_UNROLL_EM2_QUEUE
-#define ABP_UNROLL_EM2_QUEUE 6
+#define ABP_UNROLL_EM2_QUEUE 8
 #endif
 #ifndef ABP_UNROLL_HEUN2
 #define ABP_UNROLL_HEUN2 kGroupUnroll
