@@ -363,8 +363,10 @@ __device__ __forceinline__ void group_step(const Coef<R> &k, const RoundKeys &K,
 // 92 registers and two blocks per SM: against 6 (the same registers), uneven
 // batch 1.005e12 against 9.89e11, load sweep 9.95e11 against 9.83e11, D x q sweep
 // 1.020e12 against 1.006e12; capped at 80 registers for three blocks per SM it
-// spills and loses 8% on the load sweep.  The other kernels keep the default,
-// where longer bodies cost registers and blocks per SM without a measured gain.
+// spills and loses 8% on the load sweep.  The stochastic Heun kernel at two per
+// thread takes 4 (D x q sweep 6.92e11 against 6.88e11 with 2 and 3).  The other
+// kernels keep the default, where longer bodies cost registers and blocks per SM
+// without a measured gain.
 #ifndef ABP_UNROLL_EM2
 #define ABP_UNROLL_EM2 8
 #endif
@@ -372,7 +374,7 @@ __device__ __forceinline__ void group_step(const Coef<R> &k, const RoundKeys &K,
 #define ABP_UNROLL_EM2_QUEUE 8
 #endif
 #ifndef ABP_UNROLL_HEUN2
-#define ABP_UNROLL_HEUN2 kGroupUnroll
+#define ABP_UNROLL_HEUN2 4
 #endif
 template <typename R, int PPT, int MODE, bool QUEUE>
 constexpr int group_unroll() {
