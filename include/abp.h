@@ -108,8 +108,10 @@ typedef struct {
                                     persistent launch whose blocks pop (tile, round) items, so
                                     uneven sets balance across SMs.  The autotuner times every
                                     (schedule, particles_per_thread) pair once per device and
-                                    library build on a synthetic batch (table kept beside the
-                                    library), predicts every (schedule, particles_per_thread,
+                                    library build on a synthetic batch (table kept in
+                                    abp_tune_cache.txt beside the library, or in the file the
+                                    environment variable ABP_TUNE_FILE names; empty: none),
+                                    predicts every (schedule, particles_per_thread,
                                     steps_per_launch in {10^3, 10^4, 10^5}) candidate's time on
                                     the batch of abp_set_params from the busy fraction of its
                                     resident blocks and the state traffic of its launches, then,

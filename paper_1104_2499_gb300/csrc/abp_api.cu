@@ -13,6 +13,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -270,6 +271,9 @@ void measure_candidates(abp_ctx *ctx, TuneTable &tt) {
 // process on the machine -- including a profiled rerun, whose own timings
 // would be distorted by the profiler -- makes the same choice.
 std::string tune_cache_path() {
+    // ABP_TUNE_FILE relocates the file (a read-only installation, or one file shared by
+    // several builds' users); an empty value switches the file off
+    if (const char *env = getenv("ABP_TUNE_FILE")) return std::string(env);
     Dl_info info;
     if (!dladdr((const void *)&abp_version, &info) || !info.dli_fname) return std::string();
     std::string p(info.dli_fname);
