@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the pathwise-adjoint leg")
     ap.add_argument("--no-visualisation", action="store_true",
                     help="skip the per-cycle cost of reading intermediate results (iterations lost)")
+    ap.add_argument("--profile-config", default="",
+                    help="run only this workload of --configs (no headline, no other legs) and print its entry; "
+                         "for profiling one kernel; 'uneven_slice' = the uneven batch over its first 2 x 10^4 steps, work queue")
     ap.add_argument("--adjoint-only", default="",
                     help="N_TRAJ,N_STEPS: time only the forward and backward of the differentiation workload at "
                          "this size (profiling; prints one JSON line without the bench keys)")
@@ -615,6 +618,13 @@ def configs_leg(A, stream, names, lane_peak):
             w.name = "snapshots_67108864x20000_slice"
             out[name] = time_workload(A, stream, w, 1, lane_peak)[0]
             out[name]["cpu_oracle"] = oracle_subset_rate(w, 65536, 10_000)
+        elif name == "uneven_slice":
+            # all 512 sets of the uneven batch over their first 2 x 10^4 steps (1.3e11 particle-steps)
+            # in the configuration chosen for the whole batch (work queue, 2 trajectories per thread,
+            # items of 10^4 steps): its kernel in a launch short enough to profile
+            w = W.shrink(W.uneven_batch(), max_steps=20_000, name="uneven_512sets_2e4steps")
+            out[name] = time_workload(A, stream, w, 1, lane_peak, schedule=2, particles_per_thread=2,
+                                      steps_per_launch=10_000)[0]
         elif name == "heun":
             w = W.sweep_grid()
             w.scheme, w.name = 1, w.name + "_heun"
@@ -674,6 +684,11 @@ def main():
     w = workload(args)
     props = torch.cuda.get_device_properties(local)
     n_sm = props.multi_processor_count
+    if args.profile_config:
+        pk, _ = peaks()
+        lane_peak = n_sm * LANES_PER_SM * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+        print(json.dumps({"configs": configs_leg(A, stream, [args.profile_config], lane_peak)}), flush=True)
+        return
     # weak scaling: every rank integrates its own copy of the sweep with distinct trajectory ids
     ens = A.Ensemble(w, stream=stream, particles_per_thread=args.ppt, steps_per_launch=args.steps_per_launch,
                      traj_base=shard.replica_traj_base(rank, w.total_traj), schedule=args.schedule)
