@@ -238,7 +238,14 @@ ABP_API abp_status abp_load(abp_ctx *ctx, const void *buf, size_t bytes);
  * doubles (NULL = all ones); grad: host or device, [n_sets][6] doubles.
  * Requires a completed abp_integrate with checkpoint_every > 0 (otherwise
  * ABP_ESTATE); recomputes each checkpoint interval forward and sweeps it in
- * reverse, accumulating in FP64. */
+ * reverse, accumulating in FP64.  Device scratch (context-owned, kept for the
+ * next call): 32 bytes per trajectory per 8 steps of checkpoint_every plus 64
+ * bytes per trajectory; when checkpoint_every is a multiple of 8, also 8 bytes
+ * per trajectory per step of checkpoint_every for handing the noise of each
+ * interval's first re-run to its reverse sweep, if that fits in the budget the
+ * environment variable ABP_ADJ_HANDOFF_BYTES gives (0: never), by default half
+ * the free device memory -- else the noise is drawn again.  The results are the
+ * same bit for bit either way. */
 ABP_API abp_status abp_backward(abp_ctx *ctx, const double *dJ_dmean_v, double *grad);
 
 /* Windowed pathwise adjoint: as abp_backward, with the adjoint state restarted

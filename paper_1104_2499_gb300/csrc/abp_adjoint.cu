@@ -16,6 +16,7 @@
 // FP32 within a segment and in FP64 across segments and trajectories.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 
 #include "abp.h"
 #include "abp_ctx.cuh"
@@ -75,9 +76,37 @@ struct AdjArgs {
     RoundKeys K;        // Philox round keys of the seed (constant bank)
     float4 *sub;        // [n_sub][total_traj] sub-checkpoints (scratch)
     int64_t n_sub;      // sub-checkpoint slots per segment
+    uint4 *words;       // [block][n_blk][2][threads] noise hand-off of the segment (scratch), WORDS kernels only
+    int64_t n_blk;      // Philox blocks per segment (checkpoint_every / 4)
     const double *w;    // [n_sets] dJ/dmean_v, NULL = 1
     double *partials;   // [n_tiles][6]
 };
+
+// Noise hand-off from level 1 to the reverse sweep.  Level 1 draws every
+// Philox block of its segment anyway; with WORDS it also stores, per block, the
+// scaled radii of its two Box-Muller pairs and their two angle words (16 B per
+// four steps of a trajectory), and the reverse sweep's level-2 re-run takes them
+// from there instead of drawing the block and forming the radii a second time
+// (it still forms the angles' sine and cosine).  The reverse kernel holds all the
+// registers its three blocks per SM can have, so the blocks are not loaded into
+// registers ahead of use: each thread copies its own chunk's blocks into shared
+// memory with cp.async, kStages - 1 chunks ahead, and reads them when the chunk
+// runs.  The radii are the bits box_muller_f32x2 returned in level 1, and the
+// angles are formed by the same code, so every state and gradient is the same
+// bit for bit with or without the hand-off.
+#ifndef ABP_ADJ_STAGES
+#define ABP_ADJ_STAGES 3
+#endif
+constexpr int kStages = ABP_ADJ_STAGES;
+
+__device__ __forceinline__ void cp_async16(void *dst_smem, const void *src_gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(dst_smem)), "l"(src_gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
 // Noise of the four steps 4m .. 4m+3 as the forward integrator consumes it:
 // the pair (nrs, trig) of each step is exactly what it feeds its fused
@@ -226,10 +255,30 @@ __device__ __forceinline__ void level1_segment(const AdjArgs &a, const Coef<floa
 // scalar ones bit for bit); other chunks step each trajectory on its own.
 // store1: whether the second trajectory is real (else it duplicates the first
 // one's neighbour and its sub-checkpoints are not written).
+// One Philox block of the hand-off for the thread's two trajectories: the
+// scaled Box-Muller radii of its two word pairs (nrA, nrB, as their bits) and
+// the two angle words, (nrA, wb_A, nrB, wb_B).  The buffer is laid out by
+// kernel block -- [block][block index mrel in the segment][trajectory 0 / 1]
+// [thread], the level-1 and reverse kernels mapping blocks and threads to
+// trajectories alike -- so that wp (the thread's slot of mrel 0) plus a
+// constant reaches every block of a chunk.  Both halves are stored, also where
+// the thread's second trajectory repeats its first.
+template <bool WORDS>
+__device__ __forceinline__ void store_words(const AdjArgs &a, uint4 *wp, int64_t mrel, uint4 w0, uint4 w1, float2 nrA,
+                                            float2 nrB) {
+    if (WORDS) {
+        const int64_t r = dchk(mrel, a.n_blk, a.b.dbg) * (2 * kL1Threads);
+        wp[r] = make_uint4(__float_as_uint(nrA.x), w0.y, __float_as_uint(nrB.x), w0.w);
+        wp[r + kL1Threads] = make_uint4(__float_as_uint(nrA.y), w1.y, __float_as_uint(nrB.y), w1.w);
+    }
+}
+
+template <bool WORDS>
 __device__ __forceinline__ void level1_segment2(const AdjArgs &a, const Coef<float> &k, const StepStream (&ss)[2],
                                                 const int64_t (&idx)[2], bool store1, int64_t s0, int64_t s1,
                                                 float4 c0, float4 c1) {
     const int64_t T = a.b.total_traj;
+    uint4 *const wp = WORDS ? a.words + (size_t)blockIdx.x * (size_t)a.n_blk * (2 * kL1Threads) + threadIdx.x : nullptr;
     float y[2] = {c0.x, c1.x}, yacc[2] = {c0.y, c1.y}, v[2] = {c0.z, c1.z}, e[2] = {c0.w, c1.w};
     float pb[2] = {phase_base(y[0]), phase_base(y[1])};
     const int n_chunks = (int)((s1 - s0 + kSub - 1) / kSub);
@@ -257,13 +306,14 @@ __device__ __forceinline__ void level1_segment2(const AdjArgs &a, const Coef<flo
                 for (int b2 = 0; b2 < kSub / 4; ++b2) {
                     const uint32_t m = (uint32_t)(n0 >> 2) + b2;
                     const uint4 w0 = step_block(m, ss[0], a.K), w1 = step_block(m, ss[1], a.K);
-                    float2 nr, cs, sn;
-                    box_muller_f32x2(make_uint2(w0.x, w1.x), make_uint2(w0.y, w1.y), k2.bm, nr, cs, sn);
-                    em_step_f32x2(k2, nr, cs, PB, Y, V, E);
-                    em_step_f32x2(k2, nr, sn, PB, Y, V, E);
-                    box_muller_f32x2(make_uint2(w0.z, w1.z), make_uint2(w0.w, w1.w), k2.bm, nr, cs, sn);
-                    em_step_f32x2(k2, nr, cs, PB, Y, V, E);
-                    em_step_f32x2(k2, nr, sn, PB, Y, V, E);
+                    float2 nrA, nrB, cs, sn;
+                    box_muller_f32x2(make_uint2(w0.x, w1.x), make_uint2(w0.y, w1.y), k2.bm, nrA, cs, sn);
+                    em_step_f32x2(k2, nrA, cs, PB, Y, V, E);
+                    em_step_f32x2(k2, nrA, sn, PB, Y, V, E);
+                    box_muller_f32x2(make_uint2(w0.z, w1.z), make_uint2(w0.w, w1.w), k2.bm, nrB, cs, sn);
+                    em_step_f32x2(k2, nrB, cs, PB, Y, V, E);
+                    em_step_f32x2(k2, nrB, sn, PB, Y, V, E);
+                    store_words<WORDS>(a, wp, 2 * (int64_t)jc + b2, w0, w1, nrA, nrB);
                 }
                 if (((n0 + kSub) & (kBlockSteps - 1)) == 0) {
                     yacc[0] = Y.x;
@@ -296,13 +346,14 @@ __device__ __forceinline__ void level1_segment2(const AdjArgs &a, const Coef<flo
             for (int b2 = 0; b2 < kSub / 4; ++b2) {
                 const uint32_t m = (uint32_t)(n0 >> 2) + b2;
                 const uint4 w0 = step_block(m, ss[0], a.K), w1 = step_block(m, ss[1], a.K);
-                float2 nr, cs, sn;
-                box_muller_f32x2(make_uint2(w0.x, w1.x), make_uint2(w0.y, w1.y), k2.bm, nr, cs, sn);
-                em_step_f32x2(k2, nr, cs, PB, Y, V, E);
-                em_step_f32x2(k2, nr, sn, PB, Y, V, E);
-                box_muller_f32x2(make_uint2(w0.z, w1.z), make_uint2(w0.w, w1.w), k2.bm, nr, cs, sn);
-                em_step_f32x2(k2, nr, cs, PB, Y, V, E);
-                em_step_f32x2(k2, nr, sn, PB, Y, V, E);
+                float2 nrA, nrB, cs, sn;
+                box_muller_f32x2(make_uint2(w0.x, w1.x), make_uint2(w0.y, w1.y), k2.bm, nrA, cs, sn);
+                em_step_f32x2(k2, nrA, cs, PB, Y, V, E);
+                em_step_f32x2(k2, nrA, sn, PB, Y, V, E);
+                box_muller_f32x2(make_uint2(w0.z, w1.z), make_uint2(w0.w, w1.w), k2.bm, nrB, cs, sn);
+                em_step_f32x2(k2, nrB, cs, PB, Y, V, E);
+                em_step_f32x2(k2, nrB, sn, PB, Y, V, E);
+                store_words<WORDS>(a, wp, 2 * (int64_t)j + b2, w0, w1, nrA, nrB);
             }
             yacc[0] = Y.x;
             yacc[1] = Y.y;
@@ -439,14 +490,39 @@ __device__ __forceinline__ void reverse_step_x2(const RevCoef2 &c, float2 ph, fl
 // reverse_chunks for two trajectories of one thread (idx[0], idx[1]): whole
 // aligned chunks run the level-2 re-run and the reverse sweep on FP32 pairs;
 // other chunks run each trajectory on its own with the scalar functions.
+// Shared-memory stage of the hand-off: [kStages][kSub / 4 blocks][2 trajectories][thread].
+typedef uint4 WordStage[kSub / 4][2][kRevPairThreads];
+
+template <bool WORDS>
 __device__ __forceinline__ void reverse_chunks2(const AdjArgs &a, const Coef<float> &k, const StepStream (&ss)[2],
                                                 float kx, float dtf, const int64_t (&idx)[2], int64_t s0, int64_t s1,
-                                                float2 &lx, float2 &lv, float2 &le, float2 (&acc)[6]) {
+                                                float2 &lx, float2 &lv, float2 &le, float2 (&acc)[6],
+                                                WordStage *stage) {
     const int64_t T = a.b.total_traj;
     const int n_chunks = (int)((s1 - s0 + kSub - 1) / kSub);
     const bool aligned = (s0 & (kSub - 1)) == 0;
+    const int full = aligned ? (int)((s1 - s0) / kSub) : 0;  // chunks 0 .. full - 1 are whole
     const Coef2 k2 = make_coef2(k);
     const RevCoef2 rc = make_rev_coef2(k, kx, dtf);
+    // WORDS: copy whole chunk jj's blocks into stage[jj % kStages]; one commit group per
+    // call, empty for chunks that are not whole, so that groups and chunks stay in step
+    const uint4 *const wr =
+        WORDS ? a.words + (size_t)blockIdx.x * (size_t)a.n_blk * (2 * kRevPairThreads) + threadIdx.x : nullptr;
+    auto fetch = [&](int jj) {
+        if (jj >= 0 && jj < full) {
+            WordStage &st = stage[jj % kStages];
+#pragma unroll
+            for (int b2 = 0; b2 < kSub / 4; ++b2) {
+                const int64_t r = dchk(2 * (int64_t)jj + b2, a.n_blk, a.b.dbg) * (2 * kRevPairThreads);
+                cp_async16(&st[b2][0][threadIdx.x], wr + r);
+                cp_async16(&st[b2][1][threadIdx.x], wr + r + kRevPairThreads);
+            }
+        }
+        cp_async_commit();
+    };
+    if (WORDS)
+#pragma unroll
+        for (int i = 0; i < kStages - 1; ++i) fetch(n_chunks - 1 - i);
     const size_t jl = (size_t)dchk(n_chunks - 1, a.n_sub, a.b.dbg);
     float4 n0c = a.sub[jl * T + idx[0]], n1c = a.sub[jl * T + idx[1]];
     for (int j = n_chunks - 1; j >= 0; --j) {
@@ -458,22 +534,40 @@ __device__ __forceinline__ void reverse_chunks2(const AdjArgs &a, const Coef<flo
             n0c = a.sub[jp * T + idx[0]];
             n1c = a.sub[jp * T + idx[1]];
         }
+        if (WORDS) {
+            fetch(j - (kStages - 1));
+            cp_async_wait<kStages - 1>();  // this thread's copies of chunk j have landed
+        }
         if (aligned && len == kSub) {
             float2 Y = make_float2(c0.y, c1.y), V = make_float2(c0.z, c1.z), E = make_float2(c0.w, c1.w);
             const float2 PB = make_float2(phase_base(c0.x), phase_base(c1.x));
             float2 ys[kSub], vs[kSub], es[kSub], szs[kSub];
 #pragma unroll
             for (int b2 = 0; b2 < kSub / 4; ++b2) {
-                const uint32_t m = (uint32_t)(n0 >> 2) + b2;
-                const uint4 w0 = step_block(m, ss[0], a.K), w1 = step_block(m, ss[1], a.K);
                 float2 nr[2], tr[4];
                 float2 cs, sn;
-                box_muller_f32x2(make_uint2(w0.x, w1.x), make_uint2(w0.y, w1.y), k2.bm, nr[0], cs, sn);
-                tr[0] = cs;
-                tr[1] = sn;
-                box_muller_f32x2(make_uint2(w0.z, w1.z), make_uint2(w0.w, w1.w), k2.bm, nr[1], cs, sn);
-                tr[2] = cs;
-                tr[3] = sn;
+                if (WORDS) {
+                    // the radii come as level 1 formed them; the angles are formed here
+                    const uint4 w0 = stage[j % kStages][b2][0][threadIdx.x];
+                    const uint4 w1 = stage[j % kStages][b2][1][threadIdx.x];
+                    nr[0] = make_float2(__uint_as_float(w0.x), __uint_as_float(w1.x));
+                    nr[1] = make_float2(__uint_as_float(w0.z), __uint_as_float(w1.z));
+                    bm_angle_f32x2(make_uint2(w0.y, w1.y), cs, sn);
+                    tr[0] = cs;
+                    tr[1] = sn;
+                    bm_angle_f32x2(make_uint2(w0.w, w1.w), cs, sn);
+                    tr[2] = cs;
+                    tr[3] = sn;
+                } else {
+                    const uint32_t m = (uint32_t)(n0 >> 2) + b2;
+                    const uint4 w0 = step_block(m, ss[0], a.K), w1 = step_block(m, ss[1], a.K);
+                    box_muller_f32x2(make_uint2(w0.x, w1.x), make_uint2(w0.y, w1.y), k2.bm, nr[0], cs, sn);
+                    tr[0] = cs;
+                    tr[1] = sn;
+                    box_muller_f32x2(make_uint2(w0.z, w1.z), make_uint2(w0.w, w1.w), k2.bm, nr[1], cs, sn);
+                    tr[2] = cs;
+                    tr[3] = sn;
+                }
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     const int q = 4 * b2 + i;
@@ -568,6 +662,7 @@ __global__ void __launch_bounds__(kL1Threads) adjoint_level1_kernel(AdjArgs a, i
 
 // Level 1 with two trajectories per thread (trajectories li and li +
 // blockDim.x of the block's 2 blockDim.x), `sub` blocks per tile.
+template <bool WORDS>
 __global__ void __launch_bounds__(kL1Threads) adjoint_level1_pair_kernel(AdjArgs a, int64_t seg, int sub) {
     const Batch &b = a.b;
     const int tile = (int)blockIdx.x / sub;
@@ -587,8 +682,8 @@ __global__ void __launch_bounds__(kL1Threads) adjoint_level1_pair_kernel(AdjArgs
     const StepStream ss[2] = {step_stream((uint64_t)idx[0] + a.nz.traj_base, a.K),
                               step_stream((uint64_t)idx[1] + a.nz.traj_base, a.K)};
     const int64_t slot = dchk(seg, a.ck.n_slots, b.dbg);
-    level1_segment2(a, k, ss, idx, second, s0, s1, a.ck.ck[(size_t)slot * T + idx[0]],
-                    a.ck.ck[(size_t)slot * T + idx[1]]);
+    level1_segment2<WORDS>(a, k, ss, idx, second, s0, s1, a.ck.ck[(size_t)slot * T + idx[0]],
+                           a.ck.ck[(size_t)slot * T + idx[1]]);
 }
 
 __global__ void __launch_bounds__(kRevThreads, ABP_ADJ_MIN_BLOCKS) adjoint_reverse_kernel(AdjArgs a, SegView sv,
@@ -622,8 +717,10 @@ __global__ void __launch_bounds__(kRevThreads, ABP_ADJ_MIN_BLOCKS) adjoint_rever
 
 // The reverse kernel with two trajectories per thread (trajectories li and
 // li + blockDim.x of the block's 2 blockDim.x), `sub` blocks per tile.
+template <bool WORDS>
 __global__ void __launch_bounds__(kRevPairThreads, ABP_ADJ_REV_PAIR_MIN_BLOCKS) adjoint_reverse_pair_kernel(AdjArgs a, SegView sv, int64_t seg,
                                                                                int sub, int64_t window) {
+    __shared__ WordStage stage[WORDS ? kStages : 1];
     const Batch &b = a.b;
     const int tile = (int)blockIdx.x / sub;
     const int li = ((int)blockIdx.x % sub) * 2 * (int)blockDim.x + (int)threadIdx.x;
@@ -649,7 +746,7 @@ __global__ void __launch_bounds__(kRevPairThreads, ABP_ADJ_REV_PAIR_MIN_BLOCKS) 
     float2 acc[6];
 #pragma unroll
     for (int q = 0; q < 6; ++q) acc[q] = make_float2(0.0f, 0.0f);
-    reverse_chunks2(a, k, ss, kx, dtf, idx, s0, s1, lx, lv, le, acc);
+    reverse_chunks2<WORDS>(a, k, ss, kx, dtf, idx, s0, s1, lx, lv, le, acc, stage);
     sv.lam[idx[0]] = make_float4(lx.x, lv.x, le.x, 0.0f);
 #pragma unroll
     for (int q = 0; q < 6; ++q) sv.G[(size_t)q * T + idx[0]] += (double)acc[q].x;
@@ -758,6 +855,67 @@ abp_status set_err(abp_ctx *ctx, abp_status st, const char *msg, cudaError_t e =
     return st;
 }
 
+// Scratch of abp_backward, one allocation: the two sub-checkpoint buffers, the
+// tile partials, the set gradients, the weights, lambda, the per-trajectory sums
+// and, last, the two Philox-block buffers of the hand-off (0 bytes without it).
+// abp_backward_traj reads lambda and the sums of the last call at the same offsets.
+struct AdjLayout {
+    size_t sub1, sub, part, grad, w, lam, g, words1, words, need;
+    size_t off_part, off_grad, off_w, off_lam, off_g, off_words;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Kernel blocks per tile of the paired level-1 and reverse kernels (tiles hold up
+// to kThreads * ppt trajectories, a block two per thread).
+int pair_blocks_per_tile(const abp_ctx *ctx, int threads) {
+    const int cap = kThreads * std::max(ctx->ppt, 1);
+    return (cap + 2 * threads - 1) / (2 * threads);
+}
+
+AdjLayout adj_layout(const abp_ctx *ctx, bool words) {
+    AdjLayout L;
+    const int64_t T = ctx->total_traj, Kc = ctx->cfg.checkpoint_every;
+    const int64_t n_sub = (Kc + kSub - 1) / kSub;
+    L.sub1 = sizeof(float4) * (size_t)n_sub * (size_t)T;
+    L.sub = 2 * align256(L.sub1);  // two buffers, alternating by segment
+    L.part = sizeof(double) * 6 * (size_t)std::max(ctx->n_tiles, 1);
+    L.grad = sizeof(double) * 6 * (size_t)std::max(ctx->n_sets, 1);
+    L.w = sizeof(double) * (size_t)std::max(ctx->n_sets, 1);
+    L.lam = sizeof(float4) * (size_t)std::max<int64_t>(T, 1);
+    L.g = sizeof(double) * 6 * (size_t)std::max<int64_t>(T, 1);
+    const size_t blocks = (size_t)ctx->n_tiles * (size_t)pair_blocks_per_tile(ctx, kL1Threads);
+    L.words1 = words ? sizeof(uint4) * blocks * (size_t)(Kc / 4) * 2 * kL1Threads : 0;
+    L.words = 2 * align256(L.words1);
+    L.off_part = align256(L.sub);
+    L.off_grad = L.off_part + align256(L.part);
+    L.off_w = L.off_grad + align256(L.grad);
+    L.off_lam = L.off_w + align256(L.w);
+    L.off_g = L.off_lam + align256(L.lam);
+    L.off_words = L.off_g + align256(L.g);
+    L.need = L.off_words + L.words;
+    return L;
+}
+
+// Whether abp_backward hands the Philox blocks from level 1 to the reverse sweep:
+// the paired kernels, segments of whole sub-chunks, and both buffers within the
+// budget -- ABP_ADJ_HANDOFF_BYTES if set (0: never), else half the free device
+// memory not already held by the scratch.
+bool use_handoff(const abp_ctx *ctx) {
+    // both kernels must map blocks and threads to trajectories alike
+    if (!ABP_ADJ_L1_PAIRS || !ABP_ADJ_REV_PAIRS || kL1Threads != kRevPairThreads) return false;
+    if (ctx->cfg.checkpoint_every % kSub != 0) return false;
+    const size_t bytes = adj_layout(ctx, true).words;
+    const char *env = getenv("ABP_ADJ_HANDOFF_BYTES");
+    if (env && *env) return (double)bytes <= strtod(env, nullptr);
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return bytes <= (free_b + ctx->d_adj.cap) / 2;
+}
+
 }  // namespace
 }  // namespace abp
 
@@ -781,37 +939,37 @@ extern "C" abp_status abp_backward_windowed(abp_ctx *ctx, const double *dJ_dmean
     if (ctx->g < ctx->max_steps) return set_err(ctx, ABP_ESTATE, "abp_backward before the integration completed");
     if (!ctx->ckpt_complete)
         return set_err(ctx, ABP_ESTATE, "abp_backward after abp_load: the checkpoints do not cover the run from step 0");
-    const int64_t T = ctx->total_traj;
     const int64_t n_sub = (ctx->cfg.checkpoint_every + kSub - 1) / kSub;
-    const size_t sub1_bytes = sizeof(float4) * (size_t)n_sub * (size_t)T;
-    const size_t sub_bytes = 2 * ((sub1_bytes + 255) & ~(size_t)255);  // two buffers, alternating by segment
-    const size_t part_bytes = sizeof(double) * 6 * (size_t)std::max(ctx->n_tiles, 1);
-    const size_t grad_bytes = sizeof(double) * 6 * (size_t)std::max(ctx->n_sets, 1);
-    const size_t w_bytes = sizeof(double) * (size_t)std::max(ctx->n_sets, 1);
-    const size_t lam_bytes = sizeof(float4) * (size_t)std::max<int64_t>(T, 1);
-    const size_t g_bytes = sizeof(double) * 6 * (size_t)std::max<int64_t>(T, 1);
-    const size_t need = sub_bytes + part_bytes + grad_bytes + w_bytes + lam_bytes + g_bytes + 6 * 256;
+    bool words = use_handoff(ctx);
+    AdjLayout L = adj_layout(ctx, words);
     DevBuf &sc = ctx->d_adj;
-    if (!sc.p || sc.cap < need) {
+    if (!sc.p || sc.cap < L.need) {
         sc.release();
-        cudaError_t e = cudaMalloc(&sc.p, need);
+        cudaError_t e = cudaMalloc(&sc.p, L.need);
+        if (e != cudaSuccess && words) {  // no room for the hand-off: draw the blocks twice instead
+            cudaGetLastError();
+            words = false;
+            L = adj_layout(ctx, false);
+            e = cudaMalloc(&sc.p, L.need);
+        }
         if (e != cudaSuccess) {
             sc.p = nullptr;
             cudaGetLastError();
             return set_err(ctx, ABP_ENOMEM, "abp_backward: scratch allocation failed", e);
         }
-        sc.cap = need;
+        sc.cap = L.need;
     }
-    sc.bytes = need;
-    auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    sc.bytes = L.need;
     char *base = (char *)sc.p;
-    float4 *sub[2] = {(float4 *)base, (float4 *)(base + ((sub1_bytes + 255) & ~(size_t)255))};
-    double *partials = (double *)(base + align(sub_bytes));
-    double *gdev = (double *)(base + align(sub_bytes) + align(part_bytes));
-    double *wdev = (double *)(base + align(sub_bytes) + align(part_bytes) + align(grad_bytes));
+    float4 *sub[2] = {(float4 *)base, (float4 *)(base + align256(L.sub1))};
+    uint4 *wbuf[2] = {(uint4 *)(base + L.off_words), (uint4 *)(base + L.off_words + align256(L.words1))};
+    double *partials = (double *)(base + L.off_part);
+    double *gdev = (double *)(base + L.off_grad);
+    double *wdev = (double *)(base + L.off_w);
+    const size_t lam_bytes = L.lam, g_bytes = L.g;
     SegView sv;
-    sv.lam = (float4 *)(base + align(sub_bytes) + align(part_bytes) + align(grad_bytes) + align(w_bytes));
-    sv.G = (double *)((char *)sv.lam + align(lam_bytes));
+    sv.lam = (float4 *)(base + L.off_lam);
+    sv.G = (double *)(base + L.off_g);
     cudaStream_t s = ctx->stream;
     cudaError_t e = cudaSuccess;
     const double *w = nullptr;
@@ -835,6 +993,8 @@ extern "C" abp_status abp_backward_windowed(abp_ctx *ctx, const double *dJ_dmean
         a.nz = ctx->noise();
         a.sub = sub[0];
         a.n_sub = n_sub;
+        a.words = nullptr;
+        a.n_blk = ctx->cfg.checkpoint_every / 4;
         a.w = w;
         a.partials = partials;
         for (int r = 0; r < 10; ++r) {
@@ -863,15 +1023,18 @@ extern "C" abp_status abp_backward_windowed(abp_ctx *ctx, const double *dJ_dmean
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s2, start, 0);
         // blocks per tile: tiles hold up to kThreads * ppt trajectories
         const int cap = kThreads * std::max(ctx->ppt, 1);
-        const int per1 = ABP_ADJ_L1_PAIRS ? 2 * kL1Threads : kL1Threads;
-        const int per2 = ABP_ADJ_REV_PAIRS ? 2 * kRevPairThreads : kRevThreads;
-        const int sub1 = (cap + per1 - 1) / per1, sub2 = (cap + per2 - 1) / per2;
+        const int sub1 = ABP_ADJ_L1_PAIRS ? pair_blocks_per_tile(ctx, kL1Threads) : (cap + kL1Threads - 1) / kL1Threads;
+        const int sub2 = ABP_ADJ_REV_PAIRS ? pair_blocks_per_tile(ctx, kRevPairThreads)
+                                           : (cap + kRevThreads - 1) / kRevThreads;
         auto level1 = [&](int64_t j) {
             AdjArgs aj = a;
             aj.sub = sub[j & 1];
-            if (ABP_ADJ_L1_PAIRS)
-                adjoint_level1_pair_kernel<<<(unsigned)((int64_t)ctx->n_tiles * sub1), kL1Threads, 0, s2>>>(aj, j,
-                                                                                                           sub1);
+            const unsigned g1 = (unsigned)((int64_t)ctx->n_tiles * sub1);
+            if (words) {
+                aj.words = wbuf[j & 1];
+                adjoint_level1_pair_kernel<true><<<g1, kL1Threads, 0, s2>>>(aj, j, sub1);
+            } else if (ABP_ADJ_L1_PAIRS)
+                adjoint_level1_pair_kernel<false><<<g1, kL1Threads, 0, s2>>>(aj, j, sub1);
             else
                 adjoint_level1_kernel<<<(unsigned)((int64_t)ctx->n_tiles * sub1), kL1Threads, 0, s2>>>(aj, j, sub1);
             return cudaEventRecord(l1_done[j & 1], s2);
@@ -885,9 +1048,12 @@ extern "C" abp_status abp_backward_windowed(abp_ctx *ctx, const double *dJ_dmean
             if (e == cudaSuccess) e = cudaStreamWaitEvent(s, l1_done[seg & 1], 0);
             AdjArgs as = a;
             as.sub = sub[seg & 1];
-            if (ABP_ADJ_REV_PAIRS)
-                adjoint_reverse_pair_kernel<<<(unsigned)((int64_t)ctx->n_tiles * sub2), kRevPairThreads, 0, s>>>(
-                    as, sv, seg, sub2, window);
+            const unsigned g2 = (unsigned)((int64_t)ctx->n_tiles * sub2);
+            if (words) {
+                as.words = wbuf[seg & 1];
+                adjoint_reverse_pair_kernel<true><<<g2, kRevPairThreads, 0, s>>>(as, sv, seg, sub2, window);
+            } else if (ABP_ADJ_REV_PAIRS)
+                adjoint_reverse_pair_kernel<false><<<g2, kRevPairThreads, 0, s>>>(as, sv, seg, sub2, window);
             else
                 adjoint_reverse_kernel<<<(unsigned)((int64_t)ctx->n_tiles * sub2), kRevThreads, 0, s>>>(as, sv, seg,
                                                                                                        sub2, window);
@@ -926,23 +1092,19 @@ extern "C" abp_status abp_backward_traj(abp_ctx *ctx, double *dvbar) {
     if (T == 0 || ctx->n_tiles == 0) return ABP_OK;
     // the per-trajectory sums of the last backward call: the same scratch layout as there
     const int64_t n_sub = (ctx->cfg.checkpoint_every + kSub - 1) / kSub;
-    const size_t sub1_bytes = sizeof(float4) * (size_t)n_sub * (size_t)T;
-    const size_t sub_bytes = 2 * ((sub1_bytes + 255) & ~(size_t)255);
-    const size_t part_bytes = sizeof(double) * 6 * (size_t)std::max(ctx->n_tiles, 1);
-    const size_t grad_bytes = sizeof(double) * 6 * (size_t)std::max(ctx->n_sets, 1);
-    const size_t w_bytes = sizeof(double) * (size_t)std::max(ctx->n_sets, 1);
-    const size_t lam_bytes = sizeof(float4) * (size_t)std::max<int64_t>(T, 1);
-    auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const AdjLayout L = adj_layout(ctx, false);  // the hand-off buffers come after the sums
     char *base = (char *)ctx->d_adj.p;
     SegView sv;
-    sv.lam = (float4 *)(base + align(sub_bytes) + align(part_bytes) + align(grad_bytes) + align(w_bytes));
-    sv.G = (double *)((char *)sv.lam + align(lam_bytes));
+    sv.lam = (float4 *)(base + L.off_lam);
+    sv.G = (double *)(base + L.off_g);
     AdjArgs a;
     a.b = ctx->batch();
     a.ck = ctx->ckpt();
     a.nz = ctx->noise();
     a.sub = nullptr;
     a.n_sub = n_sub;
+    a.words = nullptr;
+    a.n_blk = 0;
     a.w = nullptr;
     a.partials = nullptr;
     cudaStream_t s = ctx->stream;

@@ -345,16 +345,25 @@ __device__ __forceinline__ Coef2 make_coef2(const Coef<float> &k) {
 
 // box_muller_f32 of two word pairs (wa.x, wb.x) and (wa.y, wb.y), same
 // operations in the same order.
-__device__ __forceinline__ void box_muller_f32x2(uint2 wa, uint2 wb, float2 c2, float2 &nrs, float2 &cs,
-                                                 float2 &sn) {
+// Its two halves: the scaled radius from wa, and (cos, sin) of the angle from wb.
+__device__ __forceinline__ float2 bm_radius_f32x2(uint2 wa, float2 c2) {
     const float2 u1 =
         __ffma2_rn(make_float2(__uint2float_rn(wa.x), __uint2float_rn(wa.y)), dup2(0x1p-32f), dup2(0x1p-33f));
     const float2 p = __fmul2_rn(make_float2(__log2f(u1.x), __log2f(u1.y)), c2);
-    nrs = make_float2(-sqrt_approx(fabsf(p.x)), -sqrt_approx(fabsf(p.y)));
+    return make_float2(-sqrt_approx(fabsf(p.x)), -sqrt_approx(fabsf(p.y)));
+}
+
+__device__ __forceinline__ void bm_angle_f32x2(uint2 wb, float2 &cs, float2 &sn) {
     const float2 f = make_float2(__uint_as_float(0x3f800000u | (wb.x >> 9)), __uint_as_float(0x3f800000u | (wb.y >> 9)));
     const float2 ang = __ffma2_rn(f, dup2(kTwoPiF), dup2(-1.5f * kTwoPiF));
     __sincosf(ang.x, &sn.x, &cs.x);
     __sincosf(ang.y, &sn.y, &cs.y);
+}
+
+__device__ __forceinline__ void box_muller_f32x2(uint2 wa, uint2 wb, float2 c2, float2 &nrs, float2 &cs,
+                                                 float2 &sn) {
+    nrs = bm_radius_f32x2(wa, c2);
+    bm_angle_f32x2(wb, cs, sn);
 }
 
 // em_step_f32 of two trajectories, same operations in the same order.

@@ -5,7 +5,8 @@ access and records status 3 (reported as ABP_ESTATE) on a violation.
 Bar: a child process runs the same workloads against the release and the checked library --
 ragged batches with one-set and packed tiles, snapshots and split launches under both
 schedules, stochastic Heun, xorshift noise, a warp-specialised narrow launch, the full and
-windowed adjoint with its per-trajectory readout, and the combination of moments on the device --
+windowed adjoint with its per-trajectory readout (with and without the hand-off of Philox blocks
+from level 1 to the reverse sweep), and the combination of moments on the device --
 and no check may fail, and every state, result and gradient must be the
 release library's bits (the checks change no arithmetic)."""
 import os
@@ -59,6 +60,13 @@ with A.Ensemble(w, schedule=1, particles_per_thread=2) as ens:
     out["adjoint/grad"] = ens.backward(host=True).numpy()
     out["adjoint/windowed"] = ens.backward(host=True, window=666).numpy()
     out["adjoint/traj"] = ens.traj_grad(host=True).numpy()
+    ens.synchronize()
+w.checkpoint_every = 256  # whole 8-step sub-chunks: level 1 hands its Philox blocks to the reverse sweep
+with A.Ensemble(w, schedule=1, particles_per_thread=2) as ens:
+    ens.run()
+    out["adjoint256/grad"] = ens.backward(host=True).numpy()
+    out["adjoint256/windowed"] = ens.backward(host=True, window=512).numpy()
+    out["adjoint256/traj"] = ens.traj_grad(host=True).numpy()
     ens.synchronize()
 w.checkpoint_every = 500
 with A.Ensemble(w, schedule=1, particles_per_thread=2) as ens:
