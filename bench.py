@@ -315,6 +315,7 @@ def adjoint_leg(A, stream, small=False, size=None, accuracy=True):
         # windowed adjoint (windows of 2,000 steps, t = 2): bounded where the full one is not
         win = 2000 if w.n_steps[0] >= 2000 else w.n_steps[0]
         g_win = ens.backward(window=win).cpu().numpy()[0] if win % w.checkpoint_every == 0 else None
+        dv_win = ens.traj_grad()[:8192].cpu().numpy() if g_win is not None and accuracy else None
     windowed = None
     if g_win is not None and accuracy:
         # the oracle's windowed tangent on 8,192 trajectories of the same set: its mean and
@@ -330,6 +331,20 @@ def adjoint_leg(A, stream, small=False, size=None, accuracy=True):
                     "oracle_se_over_abs_grad": dict(zip(A.GRAD_PARAMS, map(float, se / np.maximum(np.abs(g_win),
                                                                                                   1e-300)))),
                     "max_abs_diff_over_se": float(z.max()), "oracle_subset_trajectories": sub}
+        # the same trajectories on both sides: the GPU's windowed derivative of each of them against
+        # the oracle's, so the noise of the estimator cancels where the FP32 and FP64 paths stay together
+        d = dv_win[:sub] - r["dvbar"]
+        se_d = d.std(axis=0, ddof=1) / math.sqrt(sub)
+        windowed["paired"] = {"mean_diff": dict(zip(A.GRAD_PARAMS, map(float, d.mean(axis=0)))),
+                              "se_of_mean_diff": dict(zip(A.GRAD_PARAMS, map(float, se_d))),
+                              "se_over_abs_grad": dict(zip(A.GRAD_PARAMS, map(float, se_d / np.maximum(
+                                  np.abs(g_win), 1e-300)))),
+                              "max_abs_mean_diff_over_se": float(np.max(np.abs(d.mean(axis=0)) / np.maximum(se_d,
+                                                                                                          1e-300))),
+                              "fraction_of_trajectories_within_1e-3": float(np.mean(np.all(
+                                  np.abs(d) <= 1e-3 * np.maximum(np.abs(r["dvbar"]),
+                                                                 np.sqrt(np.mean(r["dvbar"] ** 2, axis=0))),
+                                  axis=1)))}
     per_traj = per_trajectory_check(A, stream, w) if accuracy and size is None and not small else None
 
     def check(n_steps, rel_h, K):
