@@ -315,21 +315,25 @@ ABP_API abp_status abp_tiles(const abp_ctx *ctx, int32_t *n_tiles, int32_t *n_pa
  * max_tiles >= the tile count, every tile's first trajectory, trajectory count
  * and set (a packed tile: its first non-empty set).  A negative count or a
  * schedule / particles_per_thread out of range gives ABP_EINVAL.
- * abp_plan_efficiency: the fraction of the launch capacity (resident_blocks
- * blocks of 256 * particles_per_thread trajectories) the batch keeps busy, in
- * particle-steps; the autotuner predicts a candidate's time on a batch as its
- * trial time x the trial batch's fraction / the batch's fraction (plus the
- * state traffic and fixed costs of its launches);  steps_per_launch = the
- * lockstep window or the work queue's item size, 0 = a window of about 2e10
- * particle-steps (lockstep) or the largest of 10^5, 10^4, 10^3 steps that gives
- * every resident block 32 items (work queue). */
+ * abp_plan_efficiency: the fraction of `units` parallel units, each running one
+ * tile of 256 * particles_per_thread trajectories at a time, that the batch keeps
+ * busy, in particle-steps (lockstep: whole waves of tiles per window; work queue:
+ * ceil(items / units) equal items when every tile has the same step count and
+ * the items divide it, else the tile-steps spread over the units plus half an
+ * item; never less than the longest tile).  The autotuner passes the SM count,
+ * since one resident block already draws an SM's full integration rate, and
+ * predicts a candidate's time on a batch as its trial time x the trial batch's
+ * fraction / the batch's fraction (plus the state traffic and fixed costs of its
+ * launches);  steps_per_launch = the lockstep window or the work queue's item
+ * size, 0 = a window of about 2e10 particle-steps (lockstep) or the largest of
+ * 10^5, 10^4, 10^3 steps that gives every unit 32 items (work queue). */
 ABP_API abp_status abp_plan(int32_t n_sets, const int64_t *n_traj, const int64_t *n_steps, int32_t schedule,
                             int32_t particles_per_thread, int32_t checkpoints, int32_t sm_count, int32_t *n_tiles,
                             int32_t *n_packed, int32_t *narrow, int64_t *tile_first, int32_t *tile_count,
                             int32_t *tile_set, int32_t max_tiles);
 ABP_API abp_status abp_plan_efficiency(int32_t n_sets, const int64_t *n_traj, const int64_t *n_steps,
                                        int32_t schedule, int32_t particles_per_thread, int32_t checkpoints,
-                                       int64_t steps_per_launch, int64_t resident_blocks, double *efficiency);
+                                       int64_t steps_per_launch, int64_t units, double *efficiency);
 
 /* Number of kernels this context has enqueued since it was created (host output). */
 ABP_API abp_status abp_kernel_launches(const abp_ctx *ctx, int64_t *launches);

@@ -252,15 +252,15 @@ def abp_plan(n_traj, n_steps, schedule: int, particles_per_thread: int, checkpoi
             "tile_count": list(count[:k]), "tile_set": list(sset[:k])}
 
 
-def abp_plan_efficiency(n_traj, n_steps, schedule: int, particles_per_thread: int, resident_blocks: int,
+def abp_plan_efficiency(n_traj, n_steps, schedule: int, particles_per_thread: int, units: int,
                         checkpoints: bool = False, steps_per_launch: int = 0) -> float:
-    """Busy fraction of a candidate's launch capacity for this batch (the autotuner's model)."""
+    """Busy fraction of `units` parallel units (the autotuner passes the SM count) for this batch."""
     n = len(n_traj)
     M = (C.c_int64 * max(n, 1))(*[int(v) for v in n_traj])
     N = (C.c_int64 * max(n, 1))(*[int(v) for v in n_steps])
     e = C.c_double()
     _check(lib().abp_plan_efficiency(n, M, N, schedule, particles_per_thread, 1 if checkpoints else 0,
-                                     steps_per_launch, resident_blocks, C.byref(e)), what="abp_plan_efficiency")
+                                     steps_per_launch, units, C.byref(e)), what="abp_plan_efficiency")
     return e.value
 
 

@@ -399,8 +399,14 @@ void save_choice(const abp_ctx *ctx, uint64_t bkey, int sched, int ppt, int64_t 
 // tile-steps over `cap` blocks, plus half a work item of tail, bounded below by
 // the longest tile's chain.
 // A tile of kThreads * ppt slots costs the same however full it is.
+// The fraction of `units` parallel units a batch keeps busy, in particle-steps.
+// The autotuner passes the SM count: one resident block already draws its SM's
+// full integration rate (measured: time against tiles per SM is a staircase in
+// ceil(tiles / SMs) for both schedules, with one, two or three blocks per SM), so
+// a batch's last partial round costs whole tiles per SM, not per block.
 double batch_efficiency(int32_t n, const int64_t *n_traj, const int64_t *n_steps, int sched, int ppt,
-                        bool checkpoints, int64_t spl, int64_t cap) {
+                        bool checkpoints, int64_t spl, int64_t units) {
+    const int64_t cap = units;
     const int64_t slots = (int64_t)kThreads * ppt;
     std::vector<std::pair<int64_t, int64_t>> tiles;  // (tile count, steps)
     std::map<int64_t, int64_t> small;               // steps -> trajectories of small sets (lockstep packs them)
@@ -420,10 +426,17 @@ double batch_efficiency(int32_t n, const int64_t *n_traj, const int64_t *n_steps
     if (useful <= 0.0 || cap <= 0) return 1.0;
     double cost = 0.0;  // particle-step capacity spent
     if (sched == 2) {
-        // list scheduling of the work items: makespan about W / cap plus half an item;
-        // items of spl steps (0: the largest of 10^5, 10^4, 10^3 giving 32 items per block)
+        // list scheduling of the work items on the units: when every tile has the same
+        // step count and the items divide it, all items are equal and the makespan is
+        // ceil(items / units) items; otherwise about W / units plus half an item.  Never
+        // less than the longest tile, whose items run one after another.  Items of spl
+        // steps (0: the largest of 10^5, 10^4, 10^3 giving 32 items per unit).
         double tile_steps = 0.0;
-        for (const auto &t : tiles) tile_steps += (double)t.first * (double)t.second;
+        bool equal = true;
+        for (const auto &t : tiles) {
+            tile_steps += (double)t.first * (double)t.second;
+            equal = equal && t.second == tiles[0].second;
+        }
         int64_t item = spl > 0 ? spl : 1000;
         for (int64_t S : {100000, 10000, 1000}) {
             if (spl > 0) break;
@@ -434,7 +447,16 @@ double batch_efficiency(int32_t n, const int64_t *n_traj, const int64_t *n_steps
                 break;
             }
         }
-        const double span = std::max(tile_steps / (double)cap + 0.5 * (double)std::min(item, max_n), (double)max_n);
+        double span;
+        if (equal && (max_n <= item || max_n % item == 0)) {
+            const int64_t len = std::min(item, max_n);
+            int64_t items = 0;
+            for (const auto &t : tiles) items += t.first * (max_n / len);
+            span = (double)((items + cap - 1) / cap) * (double)len;
+        } else {
+            span = tile_steps / (double)cap + 0.5 * (double)std::min(item, max_n);
+        }
+        span = std::max(span, (double)max_n);
         cost = (double)cap * span * (double)slots;
     } else {
         spl = std::max<int64_t>(spl, 1);
@@ -544,14 +566,16 @@ bool plan_tiles(int32_t n_sets, const int64_t *n_traj, const int64_t *n_steps, i
 }
 
 // The autotuner's model of a candidate (schedule, trajectories per thread, steps per
-// launch) on a batch: the candidate's trial time brought to full use of its capacity,
-// scaled to the batch's particle-steps and divided by the fraction of capacity the batch
-// keeps busy (batch_efficiency), plus what its launches move and cost -- every lockstep
+// launch) on a batch: the candidate's trial time brought to full use of the SMs, scaled
+// to the batch's particle-steps and divided by the fraction of the SMs the batch keeps
+// busy (batch_efficiency), plus what its launches move and cost -- every lockstep
 // window loads and stores the state of the trajectories still running, every work item
 // that of its tile (at the device copy rate), and each launch or item pop has a fixed cost.
 // The constants are measured on GB300: copy rate ~6.7 TB/s, a graph-replayed launch a few
 // microseconds, one item's pop, wait and publish about two microseconds of a block.
 constexpr double kHbmBytesPerMs = 6.5e9;
+// Candidates within this fraction of their schedule's best model time are probed too.
+constexpr double kProbeBand = 0.03;
 constexpr double kLaunchMs = 0.03;
 constexpr double kItemMs = 0.002;
 
@@ -582,9 +606,10 @@ double model_ms(const abp_ctx *ctx, const TuneTable &tt, int sched, int ppt, int
     const int64_t cap = candidate_capacity(ctx, sched, ppt);
     const bool ckpt = ctx->cfg.checkpoint_every > 0;
     const int64_t trial_traj = (int64_t)std::max(ctx->sm_count, 1) * kTrialTrajPerSm, trial_steps = kTrialSteps;
+    const int64_t sms = std::max(ctx->sm_count, 1);
     const double eff_trial = batch_efficiency(1, &trial_traj, &trial_steps, sched, ppt, false,
-                                              sched == 1 ? kTrialSteps : kTrialSteps / kTrialRounds, cap);
-    const double eff = batch_efficiency(n, M, N, sched, ppt, ckpt, spl, cap);
+                                              sched == 1 ? kTrialSteps : kTrialSteps / kTrialRounds, sms);
+    const double eff = batch_efficiency(n, M, N, sched, ppt, ckpt, spl, sms);
     double work = 0.0;
     int64_t max_n = 0;
     for (int32_t i = 0; i < n; ++i) {
@@ -937,24 +962,36 @@ TuneChoice choose_configuration(abp_ctx *ctx) {
     }
     const int64_t P = probe_steps(ctx);
     const bool probe = best_of[1] >= 0 && best_of[2] >= 0 && ctx->total_traj > 0 && P > 0;
+    std::vector<char> probed(cands.size(), 0);
     if (probe) {
+        // probed: every candidate within kProbeBand of its schedule's best by the model (the
+        // model cannot see everything a batch does to a kernel, so near-ties are measured);
+        // candidates whose prefix runs the same launches (items or windows capped at the
+        // prefix) share one measurement
         std::vector<int64_t> Np(ctx->n_steps);
         for (int64_t &v : Np) v = std::min(v, P);
-        for (int sch = 1; sch <= 2; ++sch) {
-            Candidate &cd = cands[best_of[sch]];
+        for (int i = 0; i < (int)cands.size(); ++i) {
+            Candidate &cd = cands[i];
+            if (cd.model_ms > cands[best_of[cd.sched]].model_ms * (1.0 + kProbeBand)) continue;
+            probed[i] = 1;
             cd.probe_model = model_ms(ctx, tt, cd.sched, cd.ppt, std::min(cd.spl, P), ctx->n_sets,
                                       ctx->n_traj.data(), Np.data());
-            if (probe_candidate(ctx, cd, P) != ABP_OK) cd.probe_ms = -1.0;
+            for (int j = 0; j < i; ++j)
+                if (probed[j] && cands[j].sched == cd.sched && cands[j].ppt == cd.ppt &&
+                    std::min(cands[j].spl, P) == std::min(cd.spl, P))
+                    cd.probe_ms = cands[j].probe_ms;
+            if (cd.probe_ms < 0.0 && probe_candidate(ctx, cd, P) != ABP_OK) cd.probe_ms = -1.0;
             if (cd.probe_ms > 0.0 && cd.probe_model > 0.0) cd.pred_ms = cd.probe_ms * cd.model_ms / cd.probe_model;
         }
-        // a schedule whose probe failed is not chosen over one that was measured
-        for (int sch = 1; sch <= 2; ++sch)
-            if (cands[best_of[sch]].probe_ms < 0.0 && cands[best_of[3 - sch]].probe_ms > 0.0)
-                cands[best_of[sch]].pred_ms = 1e300;
+        // a candidate whose probe failed is not chosen over one that was measured
+        bool any_measured = false;
+        for (int i = 0; i < (int)cands.size(); ++i) any_measured = any_measured || (probed[i] && cands[i].probe_ms > 0.0);
+        for (int i = 0; i < (int)cands.size(); ++i)
+            if (probed[i] && cands[i].probe_ms < 0.0 && any_measured) cands[i].pred_ms = 1e300;
     }
     int best = -1;
     for (int i = 0; i < (int)cands.size(); ++i) {
-        if (probe && i != best_of[1] && i != best_of[2]) continue;  // the two probed candidates decide
+        if (probe && !probed[i]) continue;  // the probed candidates decide
         if (best < 0 || cands[i].pred_ms < cands[best].pred_ms) best = i;
     }
     tc.sched = cands[best].sched;
@@ -1404,8 +1441,8 @@ abp_status abp_plan(int32_t n_sets, const int64_t *n_traj, const int64_t *n_step
 
 abp_status abp_plan_efficiency(int32_t n_sets, const int64_t *n_traj, const int64_t *n_steps, int32_t schedule,
                                int32_t particles_per_thread, int32_t checkpoints, int64_t steps_per_launch,
-                               int64_t resident_blocks, double *efficiency) {
-    if (!efficiency || !plan_args_ok(n_sets, n_traj, n_steps, schedule, particles_per_thread) || resident_blocks < 1 ||
+                               int64_t units, double *efficiency) {
+    if (!efficiency || !plan_args_ok(n_sets, n_traj, n_steps, schedule, particles_per_thread) || units < 1 ||
         steps_per_launch < 0)
         return ABP_EINVAL;
     int64_t total = 0, max_n = 0;
@@ -1415,7 +1452,7 @@ abp_status abp_plan_efficiency(int32_t n_sets, const int64_t *n_traj, const int6
     }
     const int64_t spl = steps_per_launch > 0 ? steps_per_launch : schedule == 1 ? default_window(total, max_n) : 0;
     *efficiency = batch_efficiency(n_sets, n_traj, n_steps, schedule, particles_per_thread, checkpoints != 0, spl,
-                                   resident_blocks);
+                                   units);
     return ABP_OK;
 }
 

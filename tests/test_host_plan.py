@@ -61,37 +61,51 @@ def test_narrow_width(A):
 
 
 def test_busy_fraction_model(A):
-    # whole waves of full tiles: lockstep keeps everything busy
-    assert A.abp_plan_efficiency([456 * 512 * 3], [10_000], 1, 2, resident_blocks=456) == pytest.approx(1.0)
+    # whole waves of full tiles: lockstep keeps every unit busy
+    assert A.abp_plan_efficiency([456 * 512 * 3], [10_000], 1, 2, units=456) == pytest.approx(1.0)
     # 1.12 waves: the second wave is 12% full
     M = [4096] * 64
-    e = A.abp_plan_efficiency(M, [100_000] * 64, 1, 2, resident_blocks=456)
+    e = A.abp_plan_efficiency(M, [100_000] * 64, 1, 2, units=456)
     assert e == pytest.approx(512 / (2 * 456), rel=1e-9)
-    # the work queue spreads the same tiles over all blocks (half an item of tail)
-    ewq = A.abp_plan_efficiency(M, [100_000] * 64, 2, 2, resident_blocks=456)
-    assert 0.9 < ewq <= 1.0 and ewq > e
+    # the work queue spreads the same tiles over all units: equal items of 10^3 steps (the
+    # largest size giving 32 per unit), ceil(51,200 / 456) = 113 of them on the busiest unit
+    ewq = A.abp_plan_efficiency(M, [100_000] * 64, 2, 2, units=456)
+    assert ewq == pytest.approx(51_200 / (113 * 456), rel=1e-12) and ewq > e
     # a single long set bounds the work queue by its chain
-    e1 = A.abp_plan_efficiency([256], [1000], 2, 1, resident_blocks=100)
+    e1 = A.abp_plan_efficiency([256], [1000], 2, 1, units=100)
     assert e1 == pytest.approx(0.01)
     # one-trajectory work items: packed in lockstep (full tiles), one slot in 256 otherwise
-    items = A.abp_plan_efficiency([1] * 4096, [1000] * 4096, 1, 1, resident_blocks=16)
+    items = A.abp_plan_efficiency([1] * 4096, [1000] * 4096, 1, 1, units=16)
     assert items == pytest.approx(1.0)
-    assert A.abp_plan_efficiency([1] * 4096, [1000] * 4096, 2, 1, resident_blocks=16) < 0.01
+    assert A.abp_plan_efficiency([1] * 4096, [1000] * 4096, 2, 1, units=16) < 0.01
 
 
 def test_trial_batch_busy_fraction(A):
-    # the autotuner's trial batch (4,096 trajectories per SM, 8,192 timed steps) is itself not
-    # fully busy for every candidate: at two trajectories per thread lockstep runs 1,216 tiles
-    # on 456 resident blocks, 2.67 waves, so a third of the last wave idles; the autotuner
-    # multiplies each trial time by this fraction before dividing by the batch's own
+    # the autotuner's trial batch (4,096 trajectories per SM, 8,192 timed steps) against the
+    # units it passes, the SMs (one resident block draws an SM's full rate): 16, 8 or 4 tiles
+    # per SM, whole waves for lockstep at every PPT, and for the work queue in four rounds of
+    # 2,048 steps 4 x 1,216 / 152 = 32 equal items per SM -- no tail anywhere
     T = 152 * 4096
-    lock = {ppt: A.abp_plan_efficiency([T], [8192], 1, ppt, resident_blocks=152 * bps, steps_per_launch=8192)
-            for ppt, bps in ((1, 4), (2, 3), (4, 2))}
-    assert lock[1] == pytest.approx(1.0) and lock[4] == pytest.approx(1.0)
-    assert lock[2] == pytest.approx((1216 / 456) / 3, rel=1e-9)
-    # the work queue, in four rounds of 2,048 steps, loses only its tail
-    wq = A.abp_plan_efficiency([T], [8192], 2, 2, resident_blocks=456, steps_per_launch=2048)
-    assert 0.95 < wq < 1.0
+    for ppt in (1, 2, 4):
+        assert A.abp_plan_efficiency([T], [8192], 1, ppt, units=152, steps_per_launch=8192) == pytest.approx(1.0)
+        assert A.abp_plan_efficiency([T], [8192], 2, ppt, units=152, steps_per_launch=2048) == pytest.approx(1.0)
+    # counted in resident blocks instead (3 per SM at PPT 2), the same batch would lose a third
+    # of its last wave: 1,216 tiles on 456 blocks, 2.67 waves
+    assert A.abp_plan_efficiency([T], [8192], 1, 2, units=456, steps_per_launch=8192) == pytest.approx(
+        (1216 / 456) / 3, rel=1e-9)
+
+
+def test_work_queue_tail_steps_with_whole_items_per_unit(A):
+    # equal items (one set, its step count a multiple of the item size): the makespan is
+    # ceil(items / units) items -- the staircase measured on GB300 with one to three blocks
+    # per SM -- so the busy fraction is items / (units * ceil(items / units))
+    for tiles, units in ((4096, 152), (2048, 152), (1824, 152), (1825, 152)):
+        M = [tiles * 512]
+        e = A.abp_plan_efficiency(M, [3840], 2, 2, units=units, steps_per_launch=3840)
+        assert e == pytest.approx(tiles / (units * math.ceil(tiles / units)), rel=1e-12), tiles
+    # 26.95 items per SM: 0.2% idle; 13.47: 3.8% idle
+    assert A.abp_plan_efficiency([4096 * 512], [3840], 2, 2, units=152, steps_per_launch=3840) > 0.997
+    assert A.abp_plan_efficiency([2048 * 1024], [3840], 2, 4, units=152, steps_per_launch=3840) < 0.97
 
 
 def test_invalid_plans_are_refused(A):
@@ -104,15 +118,16 @@ def test_invalid_plans_are_refused(A):
 
 
 def test_work_queue_tail_follows_the_item_size(A):
-    # the work queue's model: the tile-steps spread over the resident blocks plus half a work
-    # item of tail, at the item size the candidate uses (the autotuner ranks 10^3, 10^4, 10^5)
-    M, N, cap = [4096] * 64, [100_000] * 64, 304
-    tile_steps = 512 * 100_000  # 64 sets x 8 tiles of 512 trajectories (two per thread)
-    useful = 64 * 4096 * 100_000
+    # unequal tiles (sets of different step counts): the tile-steps spread over the units
+    # plus half a work item of tail, at the item size the candidate uses (the autotuner ranks
+    # 10^3, 10^4, 10^5), never less than the longest tile
+    M, N, units = [4096] * 64, [100_000] * 32 + [50_000] * 32, 152
+    tile_steps = 256 * 100_000 + 256 * 50_000  # 64 sets x 8 tiles of 512 trajectories
+    useful = 32 * 4096 * 100_000 + 32 * 4096 * 50_000
     for S in (1000, 10_000, 100_000):
-        e = A.abp_plan_efficiency(M, N, 2, 2, resident_blocks=cap, steps_per_launch=S)
-        span = tile_steps / cap + 0.5 * S
-        assert e == pytest.approx(useful / (cap * span * 512), rel=1e-12), S
-    e1 = A.abp_plan_efficiency(M, N, 2, 2, resident_blocks=cap, steps_per_launch=1000)
-    e5 = A.abp_plan_efficiency(M, N, 2, 2, resident_blocks=cap, steps_per_launch=100_000)
-    assert e1 > 0.99 and e5 < 0.8
+        e = A.abp_plan_efficiency(M, N, 2, 2, units=units, steps_per_launch=S)
+        span = max(tile_steps / units + 0.5 * S, 100_000)
+        assert e == pytest.approx(useful / (units * span * 512), rel=1e-12), S
+    e1 = A.abp_plan_efficiency(M, N, 2, 2, units=units, steps_per_launch=1000)
+    e5 = A.abp_plan_efficiency(M, N, 2, 2, units=units, steps_per_launch=100_000)
+    assert e1 > 0.99 and e5 < 0.9
