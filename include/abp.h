@@ -113,11 +113,12 @@ typedef struct {
                                     environment variable ABP_TUNE_FILE names; empty: none),
                                     predicts every (schedule, particles_per_thread,
                                     steps_per_launch in {10^3, 10^4, 10^5}) candidate's time on
-                                    the batch of abp_set_params from the busy fraction of its
-                                    resident blocks and the state traffic of its launches, then,
-                                    when both schedules are allowed, times the best candidate of
-                                    each on the first steps of the batch itself and keeps the
-                                    faster prediction (abp_tuning_report shows the record) */
+                                    the batch of abp_set_params from the fraction of the SMs
+                                    the batch keeps busy (abp_plan_efficiency) and the state
+                                    traffic of its launches, then, when both schedules are
+                                    allowed, times every candidate within 3% of its schedule's
+                                    best on the first steps of the batch itself and keeps the
+                                    fastest prediction (abp_tuning_report shows the record) */
     int64_t steps_per_launch;    /* lockstep: steps per launch; work queue: steps per work item
                                     (round); 0 = chosen by the autotuner from 10^3, 10^4, 10^5 */
     uint64_t traj_base;          /* added to every global trajectory id: a process that runs
