@@ -184,14 +184,23 @@ def abp_create(cfg: abp_config, stream=None):
 
 
 def abp_set_params(ctx, sets, n_traj, n_steps):
-    n = len(sets)
-    arr = (abp_params * max(n, 1))()
-    for i, s in enumerate(sets):
-        for k in W.PARAM_NAMES:
-            setattr(arr[i], k, float(s[k]))
-    M = (C.c_int64 * max(n, 1))(*[int(m) for m in n_traj])
-    N = (C.c_int64 * max(n, 1))(*[int(v) for v in n_steps])
-    _check(lib().abp_set_params(ctx, n, arr, M, N), ctx)
+    """sets: a sequence of parameter dicts, or a host float64 array [n_sets, 9] in
+    workloads.PARAM_NAMES order (the abp_params layout, passed without a copy)."""
+    if isinstance(sets, np.ndarray):
+        P = np.ascontiguousarray(sets, dtype=np.float64)
+        if P.ndim != 2 or P.shape[1] != len(W.PARAM_NAMES):
+            raise ValueError("parameter array must be [n_sets, %d] float64" % len(W.PARAM_NAMES))
+    else:
+        P = np.array([[s[k] for k in W.PARAM_NAMES] for s in sets], dtype=np.float64).reshape(-1, len(W.PARAM_NAMES))
+    n = P.shape[0]
+    M = np.ascontiguousarray(n_traj, dtype=np.int64)
+    N = np.ascontiguousarray(n_steps, dtype=np.int64)
+    if M.shape != (n,) or N.shape != (n,):
+        raise ValueError("n_traj and n_steps need one entry per parameter set")
+    if n == 0:  # the library reads nothing then; pass valid one-element buffers
+        P, M, N = np.zeros((1, len(W.PARAM_NAMES))), np.zeros(1, np.int64), np.zeros(1, np.int64)
+    _check(lib().abp_set_params(ctx, n, P.ctypes.data_as(C.POINTER(abp_params)), M.ctypes.data_as(C.POINTER(C.c_int64)),
+                                N.ctypes.data_as(C.POINTER(C.c_int64))), ctx)
 
 
 def abp_reset(ctx, seed: int):

@@ -745,8 +745,34 @@ abp_status configure_batch(abp_ctx *ctx, int sched, int ppt, int64_t spl) {
 #undef ALLOC
 
     cudaStream_t s = ctx->stream;
+    // The tables go up from one page-locked staging buffer (each piece at a 16-byte
+    // offset); if it cannot be had, straight from the context's pageable vectors.
+    const size_t stage_need = (sizeof(abp_params) * n_sets + 15) / 16 * 16 + (sizeof(int64_t) * n_sets + 15) / 16 * 16 +
+                              (sizeof(int32_t) * (n_sets + 1) + 15) / 16 * 16 +
+                              (sizeof(int64_t) * ctx->n_tiles + 15) / 16 * 16 +
+                              3 * ((sizeof(int32_t) * ctx->n_tiles + 15) / 16 * 16) +
+                              (sizeof(int64_t) * (n_sets + 1) + 15) / 16 * 16 + (sizeof(int32_t) * n_sets + 15) / 16 * 16;
+    if (ctx->h_stage_cap < stage_need) {
+        if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+        ctx->h_stage = nullptr;
+        ctx->h_stage_cap = 0;
+        if (cudaMallocHost(&ctx->h_stage, stage_need) == cudaSuccess) {
+            ctx->h_stage_cap = stage_need;
+        } else {
+            ctx->h_stage = nullptr;
+            cudaGetLastError();
+        }
+    }
+    size_t stage_off = 0;
     auto up = [&](DevBuf &b, const void *src, size_t n) -> cudaError_t {
-        return n ? cudaMemcpyAsync(b.p, src, n, cudaMemcpyHostToDevice, s) : cudaSuccess;
+        if (!n) return cudaSuccess;
+        if (ctx->h_stage) {
+            char *dst = (char *)ctx->h_stage + stage_off;
+            memcpy(dst, src, n);
+            stage_off += (n + 15) / 16 * 16;
+            src = dst;
+        }
+        return cudaMemcpyAsync(b.p, src, n, cudaMemcpyHostToDevice, s);
     };
     cudaError_t e = up(ctx->d_params, ctx->params.data(), sizeof(abp_params) * n_sets);
     if (e == cudaSuccess) e = up(ctx->d_steps, ctx->n_steps.data(), sizeof(int64_t) * n_sets);
@@ -764,8 +790,8 @@ abp_status configure_batch(abp_ctx *ctx, int sched, int ppt, int64_t spl) {
         e = launch_init(ctx->batch(), ctx->state(), ctx->hist(), ctx->ckpt(), ctx->noise(), s);
         ctx->launches += ctx->n_tiles > 0 ? 1 : 0;
     }
-    // The host arrays above are pageable vectors owned by the context; make the
-    // uploads complete before the context can be modified again.
+    // The staging buffer (or the context's vectors) must not change before the
+    // uploads complete: wait for them.
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         ctx->release_batch();
@@ -823,12 +849,16 @@ std::mutex g_choice_mu;
 std::map<std::pair<int, uint64_t>, std::pair<TuneChoice, std::string>> g_choices;
 
 uint64_t choice_key(const abp_ctx *ctx) {
+    // FNV-1a over 8-byte words (every field hashed is a multiple of 8 bytes)
     uint64_t h = 1469598103934665603ull;
     auto mix = [&](const void *q, size_t n) {
         const unsigned char *c = (const unsigned char *)q;
-        for (size_t i = 0; i < n; ++i) {
-            h ^= c[i];
+        for (size_t i = 0; i + 8 <= n; i += 8) {
+            uint64_t w;
+            memcpy(&w, c + i, 8);
+            h ^= w;
             h *= 1099511628211ull;
+            h ^= h >> 29;
         }
     };
     mix(ctx->params.data(), sizeof(abp_params) * ctx->params.size());

@@ -88,6 +88,11 @@ struct abp_ctx {
 
     // device
     DevBuf d_params, d_steps, d_set_tile_begin, d_tile_first, d_tile_count, d_tile_set, d_set_first, d_set_order;
+    // Page-locked host staging of the batch tables abp_set_params uploads (one
+    // allocation, grown when a batch needs more; copies from pageable memory cost
+    // a fixed fraction of a millisecond each on this platform).
+    void *h_stage = nullptr;
+    size_t h_stage_cap = 0;
     DevBuf d_y, d_yacc, d_ylo, d_v, d_e, d_y0, d_cell, d_xs;
     DevBuf d_hx, d_hv, d_ckpt, d_partials, d_moments, d_status;
     DevBuf d_queue, d_round, d_perm;  // work queue: head + done[n_tiles]; round starts; tile order
@@ -217,6 +222,9 @@ struct abp_ctx {
                           &d_yacc, &d_ylo, &d_v, &d_e, &d_y0, &d_cell, &d_xs, &d_hx, &d_hv, &d_ckpt, &d_partials,
                           &d_moments, &d_adj, &d_live_mom})
             b->release();
+        if (h_stage) cudaFreeHost(h_stage);
+        h_stage = nullptr;
+        h_stage_cap = 0;
         have_batch = false;
         live = false;
     }

@@ -266,6 +266,30 @@ def test_errors_are_reported(abp):
         abp.abp_create(cfg)
 
 
+def test_parameter_matrix_and_dicts_give_the_same_batch(abp):
+    # abp_set_params takes the sets as dicts or as a host [sets, 9] float64 matrix (passed
+    # without a copy): the same batch, the same bits
+    w = ragged_batch(steps=300)
+    out = []
+    for form in ("dicts", "matrix"):
+        with abp.Ensemble(w) as ens:
+            if form == "dicts":
+                abp.abp_set_params(ens.ctx, w.sets, w.n_traj, w.n_steps)
+            else:
+                abp.abp_set_params(ens.ctx, w.param_matrix(), np.asarray(w.n_traj), np.asarray(w.n_steps))
+            ens.integrate(-1)
+            st = ens.state()
+            ens.synchronize()
+            out.append({k: v.cpu().numpy() for k, v in st.items()})
+    for k in out[0]:
+        np.testing.assert_array_equal(out[0][k], out[1][k], err_msg=k)
+    with abp.Ensemble(w) as ens:
+        with pytest.raises(ValueError):
+            abp.abp_set_params(ens.ctx, w.param_matrix()[:, :8], w.n_traj, w.n_steps)
+        with pytest.raises(ValueError):
+            abp.abp_set_params(ens.ctx, w.param_matrix(), w.n_traj[:-1], w.n_steps)
+
+
 @pytest.mark.parametrize("scheme,noise", [(0, 0), (1, 0), (0, 1)])
 def test_paired_steps_match_scalar_steps_bitwise(abp, scheme, noise):
     # One trajectory per thread runs the scalar FP32 step; two and four step trajectory pairs
