@@ -186,13 +186,14 @@ def test_adjoint_at_zero_noise(abp):
         assert ei.value.status == abp.ABP_ESTATE
 
 
-@pytest.mark.parametrize("K,window", [(64, 0), (256, 512), (1000, 0)])
-def test_philox_handoff_gives_the_same_bits(abp, K, window, monkeypatch):
+@pytest.mark.parametrize("K,window,ppt", [(64, 0, 2), (256, 512, 2), (1000, 0, 2), (256, 0, 1), (256, 512, 4)])
+def test_philox_handoff_gives_the_same_bits(abp, K, window, ppt, monkeypatch):
     # checkpoint intervals of whole 8-step sub-chunks let level 1 hand its Philox blocks to the
     # reverse sweep (ABP_ADJ_HANDOFF_BYTES unset: within half the free memory); 0 bytes makes
     # the reverse sweep draw them again.  Ragged sets (odd sizes: a thread with one trajectory;
     # step counts with a partial last chunk and a short last segment): every set gradient and
-    # every trajectory's derivative bit for bit the same
+    # every trajectory's derivative bit for bit the same (1, 2 or 4 trajectories per thread in
+    # the forward: 1, 2 or 4 adjoint blocks per tile, the hand-off laid out by block)
     sets = [W._with(D=0.05), W._with(D=0.2, q=2.0, asym=0.1, gamma0=1.5), W._with(D=0.1, F0=0.3, c=0.3, d=0.7)]
     w = W.Workload(name="handoff", sets=sets, n_traj=[1000, 257, 3], n_steps=[2051, 1900, 1024], dt=1e-3, seed=37,
                    v0_mode=1, checkpoint_every=K)
@@ -202,7 +203,7 @@ def test_philox_handoff_gives_the_same_bits(abp, K, window, monkeypatch):
             monkeypatch.delenv("ABP_ADJ_HANDOFF_BYTES", raising=False)
         else:
             monkeypatch.setenv("ABP_ADJ_HANDOFF_BYTES", env)
-        with abp.Ensemble(w, schedule=1, particles_per_thread=2) as ens:
+        with abp.Ensemble(w, schedule=1, particles_per_thread=ppt) as ens:
             ens.run()
             out[tag] = (ens.backward(host=True, window=window).numpy(), ens.traj_grad(host=True).numpy())
     np.testing.assert_array_equal(out["handoff"][0], out["redraw"][0])
