@@ -785,8 +785,11 @@ def main():
         hx_h = torch.empty((ns, S, w.hist_x_bins), dtype=torch.int32, pin_memory=True)
         n_tiles = sum(math.ceil(m / (256 * tuning["particles_per_thread"])) for m in w.n_traj)
         n_rounds = math.ceil(w.n_steps[0] / spl) if queue else 0
-        # parameters, step counts, tile table and work-queue order, round starts
-        h2d = S * (72 + 8) + 4 * (S + 1) + (16 + 4) * n_tiles + 4 * (n_rounds + 1)
+        # what abp_set_params uploads -- parameters and step counts, set tile ranges, set
+        # offsets and order, the tile table (first trajectory, count, set) and the work-queue
+        # order -- plus the work queue's round starts
+        h2d = S * (72 + 8) + 4 * (S + 1) + 8 * (S + 1) + 4 * S + (8 + 4 + 4 + 4) * n_tiles + (
+            4 * (n_rounds + 1) if queue else 0)
         d2h = mom_h.numel() * 8 + hx_h.numel() * 4
         times = []
         # the inputs as a user holds them on the host: the parameter grid [sets, 9] float64,
