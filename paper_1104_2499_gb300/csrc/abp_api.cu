@@ -48,6 +48,17 @@ abp_status cuda_fail(abp_ctx *ctx, cudaError_t e, const char *what) {
     } while (0)
 
 // Size b for `bytes`, reusing its allocation when the capacity suffices.
+// Resident blocks per SM of the work queue for a batch of n_tiles tiles: the
+// kernel's occupancy, but no more blocks than leave 1.5 tiles to each.  An item
+// waits for its tile's previous round; with about one tile per block the blocks
+// of a round outrun the tiles and idle on those waits (load sweep, 512 tiles:
+// 9.95e11 particle-steps/s on 304 blocks, 9.64e11 on 456).  One block already
+// draws an SM's full rate, so fewer blocks cost little elsewhere.
+int wq_blocks_per_sm(int bps, int64_t n_tiles, int sms) {
+    const int64_t fit = (2 * n_tiles) / (3 * (int64_t)std::max(sms, 1));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(std::max(bps, 1), fit));
+}
+
 abp_status alloc(abp_ctx *ctx, DevBuf &b, size_t bytes, const char *what) {
     if (b.p && b.cap >= bytes) {
         b.bytes = bytes;
@@ -233,7 +244,7 @@ void measure_candidates(abp_ctx *ctx, TuneTable &tt) {
         q.n_items = nt;
         q.hold_tile = -1;
         q.wait_limit_ns = 10000000000LL;
-        const int grid = std::min(std::max(bps, 1) * std::max(ctx->sm_count, 1), nt);
+        const int grid = std::min(wq_blocks_per_sm(bps, nt, ctx->sm_count) * std::max(ctx->sm_count, 1), nt);
         for (int sch = 1; sch <= 2; ++sch) {
             auto window = [&](int64_t g0, int64_t g1) {
                 if (sch == 1) {
@@ -593,6 +604,11 @@ int64_t candidate_capacity(const abp_ctx *ctx, int sched, int ppt) {
     const cudaError_t oe = sched == 1 ? integrate_occupancy(c.state_fp64 != 0, ppt, smem, &bps, mode)
                                       : persistent_occupancy(c.state_fp64 != 0, ppt, smem, &bps, mode);
     if (oe != cudaSuccess) cudaGetLastError();
+    if (sched == 2) {
+        int64_t tiles = 0;
+        for (int32_t i = 0; i < ctx->n_sets; ++i) tiles += (ctx->n_traj[i] + kThreads * ppt - 1) / (kThreads * ppt);
+        bps = wq_blocks_per_sm(bps, tiles, ctx->sm_count);
+    }
     return (int64_t)std::max(bps, 1) * std::max(ctx->sm_count, 1);
 }
 
@@ -709,7 +725,7 @@ abp_status configure_batch(abp_ctx *ctx, int sched, int ppt, int64_t spl) {
         cudaError_t oe =
             persistent_occupancy(c.state_fp64 != 0, ctx->ppt, smem, &bps, c.scheme == 1 ? 1 : c.noise == 1 ? 2 : 0);
         if (oe != cudaSuccess) return cuda_fail(ctx, oe, "occupancy query");
-        ctx->grid = std::max(bps, 1) * std::max(ctx->sm_count, 1);
+        ctx->grid = wq_blocks_per_sm(bps, ctx->n_tiles, ctx->sm_count) * std::max(ctx->sm_count, 1);
     }
     ctx->steps_per_launch = std::max<int64_t>(spl, 1);
 
@@ -838,6 +854,7 @@ struct Candidate {
     int sched, ppt;
     int64_t spl;
     double model_ms;           // model prediction for the whole batch
+    int64_t probe_steps = 0;   // length of its probe prefix
     double probe_ms = -1.0;    // measured time of the probe prefix (-1: not probed)
     double probe_model = 0.0;  // model prediction for the probe prefix
     double pred_ms = 0.0;      // prediction the choice used
@@ -881,6 +898,20 @@ int64_t probe_steps(const abp_ctx *ctx) {
     P = std::min<int64_t>(std::max<int64_t>(P, 256), 16384);
     P = (P + 63) / 64 * 64;
     return std::min(P, ctx->max_steps);
+}
+
+// The probe prefix of one candidate: P steps, but a work-queue candidate is timed
+// over at least four of its own items where that stays within 3e10 particle-steps
+// (FP64 state: 1/64 of it), so that the rounds of a tile follow one another as in
+// the whole run (load sweep, 512 tiles, items of 10^4 steps: over 1.6 rounds the
+// prefix predicted 28.4 ms for a run that takes 26.8).
+int64_t probe_steps_for(const abp_ctx *ctx, int sched, int64_t spl, int64_t P) {
+    if (sched != 2) return P;
+    const double budget = ctx->cfg.state_fp64 ? 3e10 / 64.0 : 3e10;
+    const int64_t fit = (int64_t)(budget / (double)std::max<int64_t>(ctx->total_traj, 1));
+    int64_t Pc = std::max(P, std::min(4 * spl, fit));
+    Pc = (Pc + 63) / 64 * 64;
+    return std::min(Pc, ctx->max_steps);
 }
 
 // Configure the batch for candidate c and time its first P steps on the device
@@ -998,19 +1029,21 @@ TuneChoice choose_configuration(abp_ctx *ctx) {
         // model cannot see everything a batch does to a kernel, so near-ties are measured);
         // candidates whose prefix runs the same launches (items or windows capped at the
         // prefix) share one measurement
-        std::vector<int64_t> Np(ctx->n_steps);
-        for (int64_t &v : Np) v = std::min(v, P);
         for (int i = 0; i < (int)cands.size(); ++i) {
             Candidate &cd = cands[i];
             if (cd.model_ms > cands[best_of[cd.sched]].model_ms * (1.0 + kProbeBand)) continue;
             probed[i] = 1;
-            cd.probe_model = model_ms(ctx, tt, cd.sched, cd.ppt, std::min(cd.spl, P), ctx->n_sets,
+            const int64_t Pc = probe_steps_for(ctx, cd.sched, cd.spl, P);
+            cd.probe_steps = Pc;
+            std::vector<int64_t> Np(ctx->n_steps);
+            for (int64_t &v : Np) v = std::min(v, Pc);
+            cd.probe_model = model_ms(ctx, tt, cd.sched, cd.ppt, std::min(cd.spl, Pc), ctx->n_sets,
                                       ctx->n_traj.data(), Np.data());
             for (int j = 0; j < i; ++j)
                 if (probed[j] && cands[j].sched == cd.sched && cands[j].ppt == cd.ppt &&
-                    std::min(cands[j].spl, P) == std::min(cd.spl, P))
+                    cands[j].probe_steps == Pc && std::min(cands[j].spl, Pc) == std::min(cd.spl, Pc))
                     cd.probe_ms = cands[j].probe_ms;
-            if (cd.probe_ms < 0.0 && probe_candidate(ctx, cd, P) != ABP_OK) cd.probe_ms = -1.0;
+            if (cd.probe_ms < 0.0 && probe_candidate(ctx, cd, Pc) != ABP_OK) cd.probe_ms = -1.0;
             if (cd.probe_ms > 0.0 && cd.probe_model > 0.0) cd.pred_ms = cd.probe_ms * cd.model_ms / cd.probe_model;
         }
         // a candidate whose probe failed is not chosen over one that was measured
@@ -1032,9 +1065,10 @@ TuneChoice choose_configuration(abp_ctx *ctx) {
     for (size_t i = 0; i < cands.size(); ++i) {
         const Candidate &cd = cands[i];
         snprintf(buf, sizeof(buf),
-                 "%s{\"schedule\": %d, \"ppt\": %d, \"steps\": %lld, \"model_ms\": %.4g, \"probe_ms\": %.4g, "
-                 "\"predicted_ms\": %.4g}",
-                 i ? ", " : "", cd.sched, cd.ppt, (long long)cd.spl, cd.model_ms, cd.probe_ms, cd.pred_ms);
+                 "%s{\"schedule\": %d, \"ppt\": %d, \"steps\": %lld, \"model_ms\": %.4g, \"probe_steps\": %lld, "
+                 "\"probe_ms\": %.4g, \"predicted_ms\": %.4g}",
+                 i ? ", " : "", cd.sched, cd.ppt, (long long)cd.spl, cd.model_ms, (long long)cd.probe_steps, cd.probe_ms,
+                 cd.pred_ms);
         rep += buf;
     }
     snprintf(buf, sizeof(buf), "], \"chosen\": {\"schedule\": %d, \"ppt\": %d, \"steps\": %lld}}", tc.sched, tc.ppt,

@@ -554,10 +554,17 @@ __device__ __forceinline__ void run_tile(const Batch &b, const State &st, const 
     Slots<R, PPT> S;
     int64_t idx[PPT];
     bool act[PPT];
+    // Thread t takes trajectories t, t + stride, ... of the tile.  A full tile has
+    // stride kThreads; a partial one (the last tile of a set) ceil(count / PPT), so its
+    // trajectories fill the slots of the first threads and whole warps beyond them stay
+    // idle (their issue slots go to the SM's other blocks) instead of every thread
+    // carrying one real and PPT - 1 empty slots through the paired instructions.  A
+    // trajectory's arithmetic does not depend on its thread or slot: same results.
+    const int stride = PPT > 1 ? (count + PPT - 1) / PPT : kThreads;
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
-        const int li = lane_base + threadIdx.x + q * kThreads;
-        act[q] = li < count;
+        const int li = lane_base + threadIdx.x + q * stride;
+        act[q] = (int)threadIdx.x < stride && li < count;
         idx[q] = dchk(first + (act[q] ? li : count - 1), b.total_traj, b.dbg);
         S.y[q] = __ldcg(&s.y[idx[q]]);
         S.yacc[q] = __ldcg(&s.yacc[idx[q]]);
