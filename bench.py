@@ -35,9 +35,12 @@ N_ALG = 35
 N_ALG_HEUN = 51
 LANES_PER_SM = 128
 # DRAM bytes (read + write) per launch of the integrator on the 2,097,152-trajectory sweep grid,
-# from one ncu capture of that kernel (dram__bytes_read.sum + dram__bytes_write.sum); the traffic
-# is the state load/store, independent of the steps per launch.
-TRAFFIC_PER_LAUNCH = {"integrate_kernel<float,2>": (52523008 + 1700352, 2097152)}
+# from one ncu capture of that kernel (dram__bytes_read.sum + dram__bytes_write.sum).  Lockstep:
+# the state load/store of one window, independent of its length (captured at 2,000 steps).  Work
+# queue: the bench's own launch (10^5 steps in ten rounds of 10^4-step items), captured whole --
+# the later rounds re-read the state from L2, the writes include its write-backs.
+TRAFFIC_PER_LAUNCH = {"integrate_kernel<float,2>": (52520704 + 1661440, 2097152),
+                      "persistent_kernel<float,2>": (52601344 + 20280576, 2097152)}
 
 
 def parse():
@@ -815,7 +818,8 @@ def main():
     achieved = N_ALG * ps_launch / kern_avg / 1e12
     kname = ("persistent_kernel<float,%d>" if queue else "integrate_kernel<float,%d>") % tuning["particles_per_thread"]
     traffic = None
-    if kname in TRAFFIC_PER_LAUNCH and not args.small:
+    # the work-queue figure holds for the launch it was taken from (items of 10^4 steps)
+    if kname in TRAFFIC_PER_LAUNCH and not args.small and (not queue or spl == 10_000):
         b_cap, t_cap = TRAFFIC_PER_LAUNCH[kname]
         traffic = b_cap * w.total_traj / t_cap
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T lane-op/s", "frac": achieved / peak,
