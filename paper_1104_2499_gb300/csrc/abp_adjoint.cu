@@ -652,8 +652,7 @@ __global__ void __launch_bounds__(kL1Threads) adjoint_level1_kernel(AdjArgs a, i
     const int64_t s0 = seg * K;
     if (s0 >= N) return;  // uniform over the block
     const int64_t s1 = min(s0 + K, N);
-    const abp_params p = b.params[set];
-    const Coef<float> k = make_coef<float>(p.q, p.c, p.d, p.gamma0, p.F0, p.D, p.h, p.L, p.asym, a.nz.dt);
+    const Coef<float> k = load_coef<float>(b.coef_f, b.params, set, a.nz.dt);  // the forward's own coefficients
     if (li >= b.tile_count[tile]) return;
     const int64_t idx = dchk(b.tile_first[tile] + li, T, b.dbg);
     const StepStream ss = step_stream((uint64_t)idx + a.nz.traj_base, a.K);
@@ -674,8 +673,7 @@ __global__ void __launch_bounds__(kL1Threads) adjoint_level1_pair_kernel(AdjArgs
     const int64_t s1 = min(s0 + K, N);
     const int count = b.tile_count[tile];
     if (li >= count) return;
-    const abp_params p = b.params[set];
-    const Coef<float> k = make_coef<float>(p.q, p.c, p.d, p.gamma0, p.F0, p.D, p.h, p.L, p.asym, a.nz.dt);
+    const Coef<float> k = load_coef<float>(b.coef_f, b.params, set, a.nz.dt);  // the forward's own coefficients
     const bool second = li + (int)blockDim.x < count;
     const int64_t idx[2] = {dchk(b.tile_first[tile] + li, T, b.dbg),
                             dchk(b.tile_first[tile] + (second ? li + (int)blockDim.x : li), T, b.dbg)};
@@ -698,7 +696,7 @@ __global__ void __launch_bounds__(kRevThreads, ABP_ADJ_MIN_BLOCKS) adjoint_rever
     if (s0 >= N) return;  // uniform over the block
     const int64_t s1 = min(s0 + K, N);
     const abp_params p = b.params[set];
-    const Coef<float> k = make_coef<float>(p.q, p.c, p.d, p.gamma0, p.F0, p.D, p.h, p.L, p.asym, a.nz.dt);
+    const Coef<float> k = load_coef<float>(b.coef_f, b.params, set, a.nz.dt);  // the forward's own coefficients
     const float dtf = (float)a.nz.dt;
     const float kx = (float)(-2.0 * kPi / p.L);  // d phi / dx with the sign of d cos / d phi
     if (li >= b.tile_count[tile]) return;
@@ -732,7 +730,7 @@ __global__ void __launch_bounds__(kRevPairThreads, ABP_ADJ_REV_PAIR_MIN_BLOCKS) 
     const int count = b.tile_count[tile];
     if (li >= count) return;
     const abp_params p = b.params[set];
-    const Coef<float> k = make_coef<float>(p.q, p.c, p.d, p.gamma0, p.F0, p.D, p.h, p.L, p.asym, a.nz.dt);
+    const Coef<float> k = load_coef<float>(b.coef_f, b.params, set, a.nz.dt);  // the forward's own coefficients
     const float dtf = (float)a.nz.dt;
     const float kx = (float)(-2.0 * kPi / p.L);
     const bool second = li + (int)blockDim.x < count;

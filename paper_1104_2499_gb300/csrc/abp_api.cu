@@ -735,6 +735,7 @@ abp_status configure_batch(abp_ctx *ctx, int sched, int ppt, int64_t spl) {
 #define ALLOC(buf, bytes, what) \
     if ((st = alloc(ctx, ctx->buf, (bytes), what)) != ABP_OK) { ctx->release_all(); return st; }
     ALLOC(d_params, sizeof(abp_params) * (size_t)n_sets, "parameters");
+    ALLOC(d_coef, coef_table_bytes(n_sets), "step coefficients");
     ALLOC(d_steps, sizeof(int64_t) * (size_t)n_sets, "step counts");
     ALLOC(d_set_tile_begin, sizeof(int32_t) * ((size_t)n_sets + 1), "set tiles");
     ALLOC(d_tile_first, sizeof(int64_t) * (size_t)ctx->n_tiles, "tile table");
@@ -799,6 +800,8 @@ abp_status configure_batch(abp_ctx *ctx, int sched, int ppt, int64_t spl) {
     if (e == cudaSuccess) e = up(ctx->d_perm, ctx->perm.data(), sizeof(int32_t) * ctx->n_tiles);
     if (e == cudaSuccess) e = up(ctx->d_set_first, ctx->set_first.data(), sizeof(int64_t) * (n_sets + 1));
     if (e == cudaSuccess) e = up(ctx->d_set_order, ctx->set_order.data(), sizeof(int32_t) * n_sets);
+    if (e == cudaSuccess)
+        e = launch_coef((const abp_params *)ctx->d_params.p, n_sets, ctx->cfg.dt, ctx->d_coef.p, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_status.p, 0, sizeof(int32_t), s);
     if (e == cudaSuccess && ctx->d_hx.bytes) e = cudaMemsetAsync(ctx->d_hx.p, 0, ctx->d_hx.bytes, s);
     if (e == cudaSuccess && ctx->d_hv.bytes) e = cudaMemsetAsync(ctx->d_hv.p, 0, ctx->d_hv.bytes, s);

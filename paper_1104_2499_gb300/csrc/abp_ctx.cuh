@@ -88,6 +88,7 @@ struct abp_ctx {
 
     // device
     DevBuf d_params, d_steps, d_set_tile_begin, d_tile_first, d_tile_count, d_tile_set, d_set_first, d_set_order;
+    DevBuf d_coef;  // per-set step coefficients (coef_tables)
     // Page-locked host staging of the batch tables abp_set_params uploads (one
     // allocation, grown when a batch needs more; copies from pageable memory cost
     // a fixed fraction of a millisecond each on this platform).
@@ -130,6 +131,7 @@ struct abp_ctx {
         b.tile_count = (const int32_t *)d_tile_count.p;
         b.tile_set = (const int32_t *)d_tile_set.p;
         b.dbg = (int32_t *)d_status.p;
+        if (d_coef.bytes) abp::coef_tables(d_coef.p, n_sets, &b.coef_f, &b.coef_d);
         return b;
     }
     State state() const {
@@ -218,7 +220,7 @@ struct abp_ctx {
     void release_all() {
         if (live_stream) cudaStreamSynchronize(live_stream);
         drop_graphs();
-        for (DevBuf *b : {&d_queue, &d_round, &d_perm, &d_set_first, &d_set_order, &d_params, &d_steps, &d_set_tile_begin, &d_tile_first, &d_tile_count, &d_tile_set, &d_y,
+        for (DevBuf *b : {&d_queue, &d_round, &d_perm, &d_set_first, &d_set_order, &d_params, &d_coef, &d_steps, &d_set_tile_begin, &d_tile_first, &d_tile_count, &d_tile_set, &d_y,
                           &d_yacc, &d_ylo, &d_v, &d_e, &d_y0, &d_cell, &d_xs, &d_hx, &d_hv, &d_ckpt, &d_partials,
                           &d_moments, &d_adj, &d_live_mom})
             b->release();

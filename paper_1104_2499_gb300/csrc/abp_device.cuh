@@ -11,6 +11,8 @@
 
 #include <cuda_runtime.h>
 
+#include "abp.h"
+
 namespace abp {
 
 // --------------------------------------------------------------------------
@@ -235,6 +237,15 @@ __device__ __forceinline__ Coef<R> make_coef(double q, double c, double d, doubl
     k.dtL = (R)(dt / L);
     k.hdtL = (R)(0.5 * dt / L);
     return k;
+}
+
+// Coefficients of set `set`: from the batch's table when it has one (formed by
+// make_coef in coef_kernel, so the same bits), else formed here from the parameters.
+template <typename R>
+__device__ __forceinline__ Coef<R> load_coef(const void *table, const abp_params *params, int set, double dt) {
+    if (table) return static_cast<const Coef<R> *>(table)[set];
+    const abp_params p = params[set];
+    return make_coef<R>(p.q, p.c, p.d, p.gamma0, p.F0, p.D, p.h, p.L, p.asym, dt);
 }
 
 __device__ __forceinline__ float cos_phase(float y) {

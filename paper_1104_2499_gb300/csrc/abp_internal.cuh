@@ -42,6 +42,9 @@ struct Batch {
     const int32_t *tile_count;     // [n_tiles] trajectories in the tile (>= 1)
     const int32_t *tile_set;       // [n_tiles] the set (packed tile: its first set)
     int32_t *dbg = nullptr;        // status word of the checked build (ABP_DEBUG_CHECKS)
+    // Per-set step coefficients, Coef<float> / Coef<double> [n_sets], formed once per batch
+    // (coef_kernel); NULL: each kernel forms them from params itself (same function).
+    const void *coef_f = nullptr, *coef_d = nullptr;
 };
 
 // Checked build (-DABP_DEBUG_CHECKS=1, the stand-in for a memory checker): an
@@ -207,6 +210,14 @@ struct WaitCtl {
 cudaError_t launch_integrate(const Batch &b, const State &s, const Hist &h, const Ckpt &c, const Noise &nz,
                              int ppt, int64_t g0, int64_t g1, cudaStream_t st, const WaitCtl *wait = nullptr);
 // partials: [n_tiles][4] scratch; moments: [n_sets][8].
+// The per-set coefficient tables of a batch in one device buffer of coef_table_bytes(n)
+// bytes: coef_tables gives the two tables inside it, launch_coef fills them from the
+// device parameter array (the step's FP64 set-up done once per batch instead of at the
+// start of every window, work item and block).
+size_t coef_table_bytes(int32_t n_sets);
+void coef_tables(void *buf, int32_t n_sets, const void **coef_f, const void **coef_d);
+cudaError_t launch_coef(const abp_params *params, int32_t n_sets, double dt, void *buf, cudaStream_t st);
+
 cudaError_t launch_reduce(const Batch &b, const State &s, const Noise &nz, int64_t g, double *partials,
                           double *moments, cudaStream_t st);
 cudaError_t launch_get_state(const Batch &b, const State &s, double dt, int64_t g, double *x, double *x0, double *v,

@@ -548,8 +548,7 @@ __device__ __forceinline__ void run_tile(const Batch &b, const State &st, const 
     const SV<R> s = view<R>(st);
     const int set =
         PACKED ? (int)dchk(find_set(b, first + min(lane_base + (int)threadIdx.x, count - 1)), b.n_sets, b.dbg) : set_t;
-    const abp_params p = b.params[set];
-    const Coef<R> k = make_coef<R>(p.q, p.c, p.d, p.gamma0, p.F0, p.D, p.h, p.L, p.asym, nz.dt);
+    const Coef<R> k = load_coef<R>(sizeof(R) == 4 ? b.coef_f : b.coef_d, b.params, set, nz.dt);
 
     Slots<R, PPT> S;
     int64_t idx[PPT];
@@ -698,8 +697,7 @@ __device__ __forceinline__ void ws_produce(const Batch &b, const State &st, cons
     if (!__any_sync(0xffffffffu, act)) return;  // the consumer warp does not step either
     if (tile == r.hold_tile) return;            // test hook: the consumers' waits run out
     const int set = PACKED ? (int)dchk(find_set(b, first + min(li, count - 1)), b.n_sets, b.dbg) : set_t;
-    const abp_params p = b.params[set];
-    const Coef<float> k = make_coef<float>(p.q, p.c, p.d, p.gamma0, p.F0, p.D, p.h, p.L, p.asym, nz.dt);
+    const Coef<float> k = load_coef<float>(b.coef_f, b.params, set, nz.dt);
     const StepStream ss = step_stream((uint64_t)idx + nz.traj_base, K);
     const int lane = threadIdx.x & 31;
     const int64_t a0 = n_begin / SS, a1 = (n_end - 1) / SS;
@@ -1276,6 +1274,36 @@ cudaError_t integrate_occupancy(bool fp64, int ppt, size_t smem, int *blocks_per
         if (e != cudaSuccess) return e;
     }
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, kThreads, smem);
+}
+
+// One thread per set: its step coefficients in both state types (make_coef, the
+// function every kernel would otherwise call at the start of each tile).
+__global__ void coef_kernel(const abp_params *params, int32_t n, double dt, Coef<float> *cf, Coef<double> *cd) {
+    const int i = (int)(blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+    if (i >= n) return;
+    const abp_params p = params[i];
+    cf[i] = make_coef<float>(p.q, p.c, p.d, p.gamma0, p.F0, p.D, p.h, p.L, p.asym, dt);
+    cd[i] = make_coef<double>(p.q, p.c, p.d, p.gamma0, p.F0, p.D, p.h, p.L, p.asym, dt);
+}
+
+size_t coef_table_bytes(int32_t n_sets) {
+    const size_t n = (size_t)std::max(n_sets, 1);
+    return (sizeof(Coef<float>) * n + 255) / 256 * 256 + sizeof(Coef<double>) * n;
+}
+
+void coef_tables(void *buf, int32_t n_sets, const void **coef_f, const void **coef_d) {
+    const size_t n = (size_t)std::max(n_sets, 1);
+    *coef_f = buf;
+    *coef_d = buf ? (const char *)buf + (sizeof(Coef<float>) * n + 255) / 256 * 256 : nullptr;
+}
+
+cudaError_t launch_coef(const abp_params *params, int32_t n_sets, double dt, void *buf, cudaStream_t st) {
+    if (n_sets <= 0) return cudaSuccess;
+    const void *cf, *cd;
+    coef_tables(buf, n_sets, &cf, &cd);
+    coef_kernel<<<(n_sets + kThreads - 1) / kThreads, kThreads, 0, st>>>(params, n_sets, dt, (Coef<float> *)cf,
+                                                                         (Coef<double> *)cd);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_reduce(const Batch &b, const State &s, const Noise &nz, int64_t g, double *partials,
