@@ -39,8 +39,8 @@ LANES_PER_SM = 128
 # the state load/store of one window, independent of its length (captured at 2,000 steps).  Work
 # queue: the bench's own launch (10^5 steps in ten rounds of 10^4-step items), captured whole --
 # the later rounds re-read the state from L2, the writes include its write-backs.
-TRAFFIC_PER_LAUNCH = {"integrate_kernel<float,2>": (52520704 + 1661440, 2097152),
-                      "persistent_kernel<float,2>": (52601344 + 20280576, 2097152)}
+TRAFFIC_PER_LAUNCH = {"integrate_kernel<float,2>": (52479744 + 1671424, 2097152),
+                      "persistent_kernel<float,2>": (52659712 + 19994112, 2097152)}
 
 
 def parse():
