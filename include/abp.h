@@ -272,7 +272,8 @@ ABP_API abp_status abp_backward_traj(abp_ctx *ctx, double *dvbar);
 /* Upper bound, in nanoseconds, of every device-side wait: in the work-queue
  * schedule (schedule 2) a work item waiting for the previous round of its tile,
  * in a warp-specialised narrow lockstep launch (a batch with fewer tiles than
- * SMs) a warp waiting for its partner's noise or slot; 0 restores the default
+ * SMs) a stepping warp waiting for its producer warps' noise or a producer
+ * waiting for a free slot; 0 restores the default
  * of 60 s.  An expired wait ends the launch with ABP_ETIMEOUT
  * (reported by abp_synchronize); the context stays usable after abp_reset. */
 ABP_API abp_status abp_set_wait_limit(abp_ctx *ctx, int64_t wait_limit_ns);

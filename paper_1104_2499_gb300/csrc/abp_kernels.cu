@@ -422,66 +422,76 @@ __device__ __forceinline__ void advance(const Coef<R> &k, const RoundKeys &K, Sl
 // A narrow launch of 32-thread blocks puts fewer than two warps on an SM, so a
 // warp steps alone and its time per step is the latency of its own chain: the counter
 // block and Box-Muller of four steps, then four dependent state updates.  In
-// the warp-specialised form every consumer warp (its trajectories stepped as
-// in run_tile) has a producer warp that draws the same (nrs, trig) pairs for
-// the same steps ahead into a shared-memory ring; the consumer's chain is the
-// state update alone.  The ring holds kWsSlots slots of kWsSlotSteps steps per
-// warp pair; slot j of a launch holds absolute steps [j S, (j + 1) S), so a
-// slot never straddles a position fold.  Producer and consumer hand slots over
-// through mbarriers (32 arrivals: the lanes of the warp).  Every wait is
-// bounded: past the wait limit the thread records status 1 and stops waiting,
-// so the launch runs to its end and the host reports the timeout.
-constexpr int kWsSlotSteps = 16;
-constexpr int kWsSlots = 4;
-// Stepping threads per block at most: only a narrow launch of 32-thread blocks
-// (fewer than two stepping warps per SM) is latency-bound enough to gain.
-// Measured on the work-items sweep (10^4 steps per cycle): 0.30 against 0.42 ms
-// per cycle up to 2^13 items (32 threads), but 0.433 against 0.425 at 2^14 (64)
-// and 0.593 against 0.549 at 2^15 (128), where stepping and producer warps share
-// schedulers (1.74 warps per scheduler at 2^14) and a step takes 87 cycles
-// instead of 59.
-#ifndef ABP_WS_MAX_WIDTH
-#define ABP_WS_MAX_WIDTH 32
-#endif
-constexpr int kWsMaxWidth = ABP_WS_MAX_WIDTH;
-constexpr int kWsMaxPairs = kWsMaxWidth / 32;
-static_assert(kBlockSteps % kWsSlotSteps == 0 && kWsSlotSteps % 4 == 0, "slots hold whole counter blocks");
+// the warp-specialised form a consumer warp (its 32 trajectories stepped as in
+// run_tile) has NP producer warps that draw the same (nrs, trig) pairs for the
+// same steps ahead into a shared-memory ring; the consumer's chain is the state
+// update alone.  The ring holds kWsSlots slots of kWsSlotSteps steps; slot j of
+// a launch holds absolute steps [j S, (j + 1) S), so a slot ends where a
+// position fold does.  Producer p writes counter blocks p, p + NP, ... of each
+// slot.  Hand-over is by counters in shared memory: filled[p] = slots of the
+// launch producer p has written, consumed = slots the consumer has finished,
+// each stored by one lane after a warp barrier with release semantics and read
+// with acquire semantics.  The consumer checks once per slot and only when its
+// last reading is used up; a check at a slot boundary costs it the drain of its
+// dependent chain, so slots are long (64 steps: measured 59 -> about 35 cycles
+// per step against 16-step slots handed over by mbarriers, all else equal).
+// Every wait is bounded: past the wait limit the thread records status 1 and
+// stops waiting, so the launch runs to its end and the host reports the timeout.
+constexpr int kWsSlotSteps = 64;
+constexpr int kWsSlots = 3;
+static_assert(kWsSlotSteps == kBlockSteps, "a slot ends where a fold does");
+// Producer warps per consumer warp: with one block per SM each of the SM's four
+// schedulers runs one warp, and three producers draw the noise faster than the
+// consumer uses it (one producer warp alone: about 75 cycles per step).  Where a
+// launch puts two blocks on an SM, three producers per block still beat one.
+constexpr int kWsProducers = 3;
 
 struct WsRing {
-    float2 *buf;       // [pairs][kWsSlots][kWsSlotSteps][32] (nrs, trig) per lane and step
-    uint64_t *full;    // [pairs][kWsSlots]: slot written by the producer warp
-    uint64_t *empty;   // [pairs][kWsSlots]: slot read by the consumer warp
-    int32_t *status;   // 1 once a wait gave up
+    float2 *buf;        // [kWsSlots][kWsSlotSteps][32] (nrs, trig) per lane and step
+    int32_t *filled;    // [NP]: slots of the launch written by producer warp p
+    int32_t *consumed;  // slots of the launch the consumer warp has finished
+    int32_t *status;    // 1 once a wait gave up
     int64_t limit_ns;
-    int32_t hold_tile; // test hook: the producers of this tile never hand a slot over
+    int32_t hold_tile;  // test hook: the producers of this tile never hand a slot over
 };
 
-// Wait for the completion of phase `parity` of `bar`, at most limit_ns; after
-// a failure (here or in another thread) the thread no longer waits.
-__device__ __forceinline__ void ws_wait(uint64_t *bar, uint32_t parity, const WsRing &r, bool &failed) {
-    if (failed || mbar_try_wait(bar, parity)) return;
+// Publish a warp's count: every lane's shared-memory accesses before the call
+// are ordered (warp barrier, then one release store) before the new value.
+__device__ __forceinline__ void ws_publish(int32_t *cnt, int32_t v) {
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) st_release_cta(cnt, v);
+}
+
+// Wait until *cnt >= target, at most limit_ns; returns the last value read.
+// After a failure (here or in another thread) the thread no longer waits.
+__device__ __forceinline__ int32_t ws_wait(const int32_t *cnt, int32_t target, const WsRing &r, bool &failed) {
+    int32_t v = ld_acquire_cta(cnt);
+    if (v >= target || failed) return v;
     const uint64_t t0 = global_ns();
     for (;;) {
-        if (mbar_try_wait(bar, parity)) return;
+        v = ld_acquire_cta(cnt);
+        if (v >= target) return v;
         if (*(volatile int32_t *)r.status != 0 || global_ns() - t0 > (uint64_t)r.limit_ns) {
             atomicCAS(r.status, 0, 1);
             failed = true;
-            return;
+            return v;
         }
     }
 }
 
-// Consumer side of one warp pair: the slot held (absolute slot index) and the
-// first slot of the launch.
+// Consumer side: the launch's first slot, the slots known to be written by
+// every producer it waits on (1 with xorshift noise, whose generator only the
+// first producer runs), and whether a wait gave up.
 struct WsCons {
     WsRing r;
-    int pair;
-    int64_t a0, held;
+    int np;
+    int64_t a0;
+    int32_t ready;
     bool failed;
 };
 
 // advance() with the noise taken from the ring (FP32, one trajectory per
-// thread; the producer drew it from the counter-based stream or from the
+// thread; the producers drew it from the counter-based stream or from the
 // trajectory's xorshift generator).
 template <bool HEUN>
 __device__ __forceinline__ void advance_ws(const Coef<float> &k, Slots<float, 1> &S, int64_t n, int64_t n_end,
@@ -490,14 +500,13 @@ __device__ __forceinline__ void advance_ws(const Coef<float> &k, Slots<float, 1>
     const int lane = threadIdx.x & 31;
     while (n < n_end) {
         const int64_t a = n / SS;
-        const int64_t kf = a - c.a0;
-        const int slot = (int)(kf % kWsSlots);
-        if (a != c.held) {
-            if (c.held >= 0) mbar_arrive(&c.r.empty[c.pair * kWsSlots + (int)((c.held - c.a0) % kWsSlots)]);
-            ws_wait(&c.r.full[c.pair * kWsSlots + slot], (uint32_t)((kf / kWsSlots) & 1), c.r, c.failed);
-            c.held = a;
+        const int32_t kf = (int32_t)(a - c.a0);
+        if (kf >= c.ready) {
+            int32_t rd = ws_wait(&c.r.filled[0], kf + 1, c.r, c.failed);
+            for (int p = 1; p < c.np; ++p) rd = min(rd, ws_wait(&c.r.filled[p], kf + 1, c.r, c.failed));
+            c.ready = c.failed ? INT32_MAX : rd;
         }
-        const float2 *ring = c.r.buf + ((size_t)(c.pair * kWsSlots + slot) * SS) * 32 + lane;
+        const float2 *ring = c.r.buf + (size_t)(kf % kWsSlots) * SS * 32 + lane;
         const int64_t a_end = min(n_end, (a + 1) * SS);
         if (n == a * SS && a_end == (a + 1) * SS) {
 #pragma unroll
@@ -506,16 +515,16 @@ __device__ __forceinline__ void advance_ws(const Coef<float> &k, Slots<float, 1>
                 step_f32<HEUN>(k, t.x, t.y, S.pb[0], S.yacc[0], S.v[0], S.e[0]);
             }
         } else {
-            // a fold can fall only on a slot's end (slots tile the 64-step blocks)
             for (; n < a_end; ++n) {
                 const float2 t = ring[(int)(n - a * SS) * 32];
                 step_f32<HEUN>(k, t.x, t.y, S.pb[0], S.yacc[0], S.v[0], S.e[0]);
             }
         }
         n = a_end;
-        if ((n & (kBlockSteps - 1)) == 0) {
+        if ((n & (kBlockSteps - 1)) == 0) {  // the slot's last step: fold, and hand the slot back
             fold_position<float>(S.y[0], S.yacc[0], S.ylo[0], S.cell[0]);
             S.pb[0] = phase_base(S.y[0]);
+            ws_publish(c.r.consumed, kf + 1);
         }
     }
 }
@@ -594,7 +603,7 @@ __device__ __forceinline__ void run_tile(const Batch &b, const State &st, const 
 
     if constexpr (WS) {
         wc->a0 = n_begin / kWsSlotSteps;
-        wc->held = -1;
+        wc->ready = 0;
     }
     int64_t n = n_begin;
     while (n < n_end) {
@@ -623,7 +632,7 @@ __device__ __forceinline__ void run_tile(const Batch &b, const State &st, const 
                     if (h.bx > 0) atomicAdd(&sh[bin_x<R>(S.y[q] + S.yacc[q], h.bx)], 1u);
                     if (h.bv > 0) atomicAdd(&sh[h.bx + bin_v<R>(S.v[q], v_lo, v_hi, v_scale, h.bv)], 1u);
                 }
-                flush_hist<WS>(sh, h, snap, set, b.n_sets, (int)blockDim.x / 2);
+                flush_hist<WS>(sh, h, snap, set, b.n_sets, 32);
             }
         }
         if (ck.every > 0 && n % ck.every == 0 && sizeof(R) == 4) {
@@ -673,17 +682,16 @@ __global__ void ABP_INTEGRATE_BOUNDS integrate_kernel(Batch b, State st, Hist h,
                                                                        lane_base);
 }
 
-// Producer side of one warp pair: the (nrs, trig) pairs of every step of the
-// launch's slots for the trajectories of consumer threads ci (lane by lane), in
-// slot order, each slot reused only after its consumer released it.  The
-// values are those single_step / group_step compute: same counter blocks (or,
-// with xorshift noise, the same words of the trajectory's generator, which the
+// Producer warp p of NP: the (nrs, trig) pairs of the launch's slots for the
+// 32 trajectories of the consumer warp (lane by lane), in slot order, a slot
+// rewritten only after the consumer handed it back.  The values are those
+// single_step / group_step compute: same counter blocks (or, with xorshift
+// noise, the same words of the trajectory's generator, which the first
 // producer loads, advances over the launch's steps and stores back), same
 // Box-Muller, same coefficient.
-template <bool PACKED, int MODE>
+template <bool PACKED, int MODE, int NP>
 __device__ __forceinline__ void ws_produce(const Batch &b, const State &st, const Noise &nz, const RoundKeys &K,
-                                           const WsRing &r, int tile, int64_t w0, int64_t w1, int lane_base, int pair,
-                                           int ci) {
+                                           const WsRing &r, int tile, int64_t w0, int64_t w1, int lane_base, int p) {
     constexpr int SS = kWsSlotSteps;
     const int64_t first = b.tile_first[tile];
     const int count = b.tile_count[tile];
@@ -691,17 +699,19 @@ __device__ __forceinline__ void ws_produce(const Batch &b, const State &st, cons
     const int64_t N = b.set_steps[set_t];
     const int64_t n_begin = min(w0, N), n_end = min(w1, N);
     if (n_begin >= n_end) return;  // uniform over the block, as for the consumers
-    const int li = lane_base + ci;
+    if (MODE == kModeXorshift && p > 0) return;  // one generator chain per trajectory: the first producer's
+    const int lane = threadIdx.x & 31;
+    const int li = lane_base + lane;
     const bool act = li < count;
     const int64_t idx = dchk(first + (act ? li : count - 1), b.total_traj, b.dbg);
     if (!__any_sync(0xffffffffu, act)) return;  // the consumer warp does not step either
-    if (tile == r.hold_tile) return;            // test hook: the consumers' waits run out
+    if (tile == r.hold_tile) return;            // test hook: the consumer's waits run out
     const int set = PACKED ? (int)dchk(find_set(b, first + min(li, count - 1)), b.n_sets, b.dbg) : set_t;
     const Coef<float> k = load_coef<float>(b.coef_f, b.params, set, nz.dt);
     const StepStream ss = step_stream((uint64_t)idx + nz.traj_base, K);
-    const int lane = threadIdx.x & 31;
     const int64_t a0 = n_begin / SS, a1 = (n_end - 1) / SS;
     bool failed = false;
+    int32_t room = kWsSlots;  // slots of the launch [0, room) may be written
     uint32_t xs[4];
     if constexpr (MODE == kModeXorshift) {
         const uint4 w = __ldcg(&st.xs[idx]);
@@ -711,38 +721,40 @@ __device__ __forceinline__ void ws_produce(const Batch &b, const State &st, cons
         xs[3] = w.w;
     }
     for (int64_t a = a0; a <= a1; ++a) {
-        const int64_t kf = a - a0;
-        const int slot = (int)(kf % kWsSlots);
-        if (kf >= kWsSlots) ws_wait(&r.empty[pair * kWsSlots + slot], (uint32_t)((kf / kWsSlots - 1) & 1), r, failed);
-        float2 *out = r.buf + ((size_t)(pair * kWsSlots + slot) * SS) * 32 + lane;
+        const int32_t kf = (int32_t)(a - a0);
+        if (kf >= room) {
+            const int32_t c = ws_wait(r.consumed, kf + 1 - kWsSlots, r, failed);
+            room = failed ? INT32_MAX : c + kWsSlots;
+        }
+        float2 *out = r.buf + (size_t)(kf % kWsSlots) * SS * 32 + lane;
         if constexpr (MODE == kModeXorshift) {
             // the generator advances only over the launch's own steps (two words and the
-            // Box-Muller cosine per step, as single_step draws them)
+            // Box-Muller cosine per step, as single_step draws them); a whole chunk of 16
+            // steps takes its words first (the generator's serial chain), then the
+            // transforms, independent of one another
+            constexpr int CH = 16;
             const int64_t i0 = max(n_begin - a * SS, (int64_t)0), i1 = min(n_end - a * SS, (int64_t)SS);
-            if (i0 == 0 && i1 == SS) {
-                // a whole slot: the words first (the generator's serial chain), then the
-                // transforms, independent of one another
-                uint32_t wv[2 * SS];
+            int64_t i = i0;
+            for (; i + CH <= i1; i += CH) {
+                uint32_t wv[2 * CH];
 #pragma unroll
-                for (int i = 0; i < 2 * SS; ++i) wv[i] = xorshift128(xs);
+                for (int j = 0; j < 2 * CH; ++j) wv[j] = xorshift128(xs);
 #pragma unroll
-                for (int i = 0; i < SS; ++i) {
+                for (int j = 0; j < CH; ++j) {
                     float nr, cs, sn;
-                    box_muller_f32(wv[2 * i], wv[2 * i + 1], k.bm, nr, cs, sn);
-                    out[i * 32] = make_float2(nr, cs);
-                }
-            } else {
-                for (int64_t i = i0; i < i1; ++i) {
-                    const uint32_t wa = xorshift128(xs);
-                    const uint32_t wb = xorshift128(xs);
-                    float nr, cs, sn;
-                    box_muller_f32(wa, wb, k.bm, nr, cs, sn);
-                    out[i * 32] = make_float2(nr, cs);
+                    box_muller_f32(wv[2 * j], wv[2 * j + 1], k.bm, nr, cs, sn);
+                    out[(i + j) * 32] = make_float2(nr, cs);
                 }
             }
+            for (; i < i1; ++i) {
+                const uint32_t wa = xorshift128(xs);
+                const uint32_t wb = xorshift128(xs);
+                float nr, cs, sn;
+                box_muller_f32(wa, wb, k.bm, nr, cs, sn);
+                out[i * 32] = make_float2(nr, cs);
+            }
         } else {
-#pragma unroll
-            for (int j = 0; j < SS / 4; ++j) {
+            for (int j = p; j < SS / 4; j += NP) {
                 const uint4 wv = step_block((uint32_t)(a * (SS / 4) + j), ss, K);
                 float nr, cs, sn;
                 box_muller_f32(wv.x, wv.y, k.bm, nr, cs, sn);
@@ -753,7 +765,7 @@ __device__ __forceinline__ void ws_produce(const Batch &b, const State &st, cons
                 out[(4 * j + 3) * 32] = make_float2(nr, sn);
             }
         }
-        mbar_arrive(&r.full[pair * kWsSlots + slot]);
+        ws_publish(&r.filled[p], kf + 1);
     }
     if constexpr (MODE == kModeXorshift) {
         if (act) st.xs[idx] = make_uint4(xs[0], xs[1], xs[2], xs[3]);
@@ -761,21 +773,17 @@ __device__ __forceinline__ void ws_produce(const Batch &b, const State &st, cons
 }
 
 // Warp-specialised narrow lockstep launch (FP32, any scheme and noise): blocks
-// of 2 w threads over the w trajectories a narrow block of w threads takes
-// (sub blocks per tile); threads [0, w) step them (run_tile), threads [w, 2 w)
+// of 32 (1 + NP) threads over the 32 trajectories a narrow block of 32 threads
+// takes (sub blocks per tile); warp 0 steps them (run_tile), warps 1..NP
 // produce their noise.  Dynamic shared memory: the histogram bins (one-set
 // tiles), then the ring at the next 16-byte boundary.
-template <bool PACKED, int MODE>
-__global__ void __launch_bounds__(2 * kWsMaxWidth) ws_kernel(Batch b, State st, Hist h, Ckpt ck, Noise nz,
-                                                            KeyParam kp, int64_t g0, int64_t g1, WaitCtl wait) {
+template <bool PACKED, int MODE, int NP>
+__global__ void __launch_bounds__(32 * (1 + NP)) ws_kernel(Batch b, State st, Hist h, Ckpt ck, Noise nz,
+                                                          KeyParam kp, int64_t g0, int64_t g1, WaitCtl wait) {
     extern __shared__ uint32_t sh[];
-    __shared__ uint64_t full[kWsMaxPairs * kWsSlots], empty[kWsMaxPairs * kWsSlots];
-    const int w = (int)blockDim.x / 2;
-    const int pairs = w / 32;
-    if ((int)threadIdx.x < pairs * kWsSlots) {
-        mbar_init(&full[threadIdx.x], 32);
-        mbar_init(&empty[threadIdx.x], 32);
-    }
+    __shared__ int32_t filled[NP], consumed;
+    if ((int)threadIdx.x < NP) filled[threadIdx.x] = 0;
+    if (threadIdx.x == 0) consumed = 0;
     if constexpr (!PACKED) zero_hist(sh, h);
     __syncthreads();
     const int nb = PACKED ? 0 : h.bx + (h.bv > 0 ? h.bv + 2 : 0);
@@ -784,16 +792,16 @@ __global__ void __launch_bounds__(2 * kWsMaxWidth) ws_kernel(Batch b, State st, 
         if (threadIdx.x == 0) atomicCAS(wait.status, 0, 2);
         return;
     }
-    const WsRing r{ring, full, empty, wait.status, wait.limit_ns, wait.hold_tile};
+    const WsRing r{ring, filled, &consumed, wait.status, wait.limit_ns, wait.hold_tile};
     const int sub = PACKED ? b.sub_packed : b.sub_single;
     const int tile = (PACKED ? b.n_single : 0) + (int)blockIdx.x / sub;
-    const int lane_base = ((int)blockIdx.x % sub) * w;
-    if ((int)threadIdx.x < w) {
-        WsCons c{r, (int)threadIdx.x >> 5, 0, -1, false};
+    const int lane_base = ((int)blockIdx.x % sub) * 32;
+    const int warp = (int)threadIdx.x >> 5;
+    if (warp == 0) {
+        WsCons c{r, MODE == kModeXorshift ? 1 : NP, 0, 0, false};
         run_tile<float, 1, PACKED, MODE, kGroupUnroll, true>(b, st, h, ck, nz, kp.K, sh, tile, g0, g1, lane_base, &c);
     } else {
-        const int ci = (int)threadIdx.x - w;
-        ws_produce<PACKED, MODE>(b, st, nz, kp.K, r, tile, g0, g1, lane_base, ci >> 5, ci);
+        ws_produce<PACKED, MODE, NP>(b, st, nz, kp.K, r, tile, g0, g1, lane_base, warp - 1);
     }
 }
 
@@ -1105,32 +1113,32 @@ cudaError_t launch_persistent_t(const Batch &b, const State &s, const Hist &h, c
 }
 
 // Warp-specialised form of a narrow launch (see ws_kernel).
+template <bool PACKED, int MODE>
+cudaError_t launch_ws_t(const Batch &b, const State &s, const Hist &h, const Ckpt &c, const Noise &nz,
+                        const KeyParam &kp, unsigned grid, size_t smem, int64_t g0, int64_t g1, const WaitCtl &wait,
+                        cudaStream_t st) {
+    auto kern = ws_kernel<PACKED, MODE, kWsProducers>;
+    // the ring alone is 48 KB: with the static counters the block is past the default limit
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, 32 * (1 + kWsProducers), smem, st>>>(b, s, h, c, nz, kp, g0, g1, wait);
+    return cudaGetLastError();
+}
+
 template <int MODE>
 cudaError_t launch_ws(const Batch &b, const State &s, const Hist &h, const Ckpt &c, const Noise &nz, int64_t g0,
                       int64_t g1, const WaitCtl &wait, cudaStream_t st) {
-    const int w = b.narrow;
-    const size_t ring = sizeof(float2) * (size_t)(w / 32) * kWsSlots * kWsSlotSteps * 32;
+    const size_t ring = sizeof(float2) * (size_t)kWsSlots * kWsSlotSteps * 32;
     const size_t hist = (hist_smem(h) + 15) & ~(size_t)15;
     const KeyParam kp = key_param(nz.k0, nz.k1);
-    if (b.n_single > 0) {
-        auto kern = ws_kernel<false, MODE>;
-        const size_t smem = hist + ring;
-        if (smem > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-        }
-        kern<<<(unsigned)(b.n_single * b.sub_single), 2 * w, smem, st>>>(b, s, h, c, nz, kp, g0, g1, wait);
-    }
-    if (b.n_tiles > b.n_single) {
-        auto kern = ws_kernel<true, MODE>;
-        if (ring > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring);
-            if (e != cudaSuccess) return e;
-        }
-        kern<<<(unsigned)((b.n_tiles - b.n_single) * b.sub_packed), 2 * w, ring, st>>>(b, s, h, c, nz, kp, g0, g1,
-                                                                                        wait);
-    }
-    return cudaGetLastError();
+    cudaError_t e = cudaSuccess;
+    if (b.n_single > 0)
+        e = launch_ws_t<false, MODE>(b, s, h, c, nz, kp, (unsigned)(b.n_single * b.sub_single), hist + ring, g0, g1,
+                                     wait, st);
+    if (e == cudaSuccess && b.n_tiles > b.n_single)
+        e = launch_ws_t<true, MODE>(b, s, h, c, nz, kp, (unsigned)((b.n_tiles - b.n_single) * b.sub_packed), ring, g0,
+                                    g1, wait, st);
+    return e;
 }
 
 template <typename R, int PPT, int MODE = kModeEM>
@@ -1143,7 +1151,7 @@ cudaError_t launch_integrate_t(const Batch &b, const State &s, const Hist &h, co
         if (e != cudaSuccess) return e;
     }
     if constexpr (sizeof(R) == 4 && PPT == 1 && ABP_WS) {
-        if (b.narrow > 0 && b.narrow <= kWsMaxWidth && wait && wait->status)
+        if (b.narrow == 32 && wait && wait->status)
             return launch_ws<MODE>(b, s, h, c, nz, g0, g1, *wait, st);
     }
     const int threads = b.narrow ? b.narrow : kThreads;

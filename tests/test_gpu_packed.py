@@ -132,8 +132,8 @@ def test_narrow_packed_items_against_wide(abp):
 
 @pytest.mark.parametrize("n_traj,scheme", [(4096, 0), (777, 0), (4096, 1), (12800, 0), (12800, 1)])
 def test_warp_specialised_narrow_launch_is_bitwise_the_wide_one(abp, n_traj, scheme):
-    # narrow lockstep blocks of 32 stepping threads run warp-specialised (a producer warp draws
-    # the noise into a shared-memory ring of 16-step slots; 777 trajectories leave a ragged
+    # narrow lockstep blocks of 32 stepping threads run warp-specialised (three producer warps
+    # draw the noise into a shared-memory ring of 64-step slots; 777 trajectories leave a ragged
     # last block); 64-thread blocks (12,800 trajectories) run the plain narrow kernel.  Launch
     # windows (250 steps), snapshots (every 77 steps) and the run's end (1,003 steps) fall
     # inside slots; state, histograms and moments must be the work queue's bits (it never
