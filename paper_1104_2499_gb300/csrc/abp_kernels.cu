@@ -445,6 +445,15 @@ static_assert(kWsSlotSteps == kBlockSteps, "a slot ends where a fold does");
 // consumer uses it (one producer warp alone: about 75 cycles per step).  Where a
 // launch puts two blocks on an SM, three producers per block still beat one.
 constexpr int kWsProducers = 3;
+// Narrow launches planned at most this wide run warp-specialised, as 32-thread
+// stepping blocks.  Measured on the work-items sweep (one-trajectory sets, 10^4
+// steps per cycle): 2^14 items, planned 64 wide (256 blocks), 0.42 ms per cycle
+// on the plain narrow kernel and 0.34 ms warp-specialised (512 blocks of four
+// warps, all resident); at 2^15 (128 wide) the warp-specialised grid would no
+// longer fit on the SMs at once.
+#ifndef ABP_WS_WIDEST
+#define ABP_WS_WIDEST 64
+#endif
 
 struct WsRing {
     float2 *buf;        // [kWsSlots][kWsSlotSteps][32] (nrs, trig) per lane and step
@@ -1125,19 +1134,47 @@ cudaError_t launch_ws_t(const Batch &b, const State &s, const Hist &h, const Ckp
     return cudaGetLastError();
 }
 
+// Whether `grid` blocks of the kernel fit on the GPU at once.
+template <bool PACKED, int MODE>
+cudaError_t ws_resident(unsigned grid, size_t smem, bool &fits) {
+    auto kern = ws_kernel<PACKED, MODE, kWsProducers>;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * (1 + kWsProducers), smem);
+    fits = e == cudaSuccess && (int64_t)grid <= (int64_t)per_sm * sms;
+    return e;
+}
+
+// Runs the launch warp-specialised (taken = true), unless the plan's width is over 32
+// and the 32-thread stepping blocks would not all fit on the GPU at once.
 template <int MODE>
-cudaError_t launch_ws(const Batch &b, const State &s, const Hist &h, const Ckpt &c, const Noise &nz, int64_t g0,
-                      int64_t g1, const WaitCtl &wait, cudaStream_t st) {
+cudaError_t launch_ws(const Batch &b0, const State &s, const Hist &h, const Ckpt &c, const Noise &nz, int64_t g0,
+                      int64_t g1, const WaitCtl &wait, cudaStream_t st, bool &taken) {
+    // 32 stepping threads per block whatever width w the plan chose (w divides the
+    // tiles, so each of its blocks becomes w / 32 blocks): the tiles, and so every
+    // result, stay the same
+    Batch b = b0;
+    b.sub_single = b0.sub_single * (b0.narrow / 32);
+    b.sub_packed = b0.sub_packed * (b0.narrow / 32);
     const size_t ring = sizeof(float2) * (size_t)kWsSlots * kWsSlotSteps * 32;
     const size_t hist = (hist_smem(h) + 15) & ~(size_t)15;
-    const KeyParam kp = key_param(nz.k0, nz.k1);
+    const unsigned grid_s = (unsigned)(b.n_single * b.sub_single);
+    const unsigned grid_p = (unsigned)((b.n_tiles - b.n_single) * b.sub_packed);
     cudaError_t e = cudaSuccess;
-    if (b.n_single > 0)
-        e = launch_ws_t<false, MODE>(b, s, h, c, nz, kp, (unsigned)(b.n_single * b.sub_single), hist + ring, g0, g1,
-                                     wait, st);
-    if (e == cudaSuccess && b.n_tiles > b.n_single)
-        e = launch_ws_t<true, MODE>(b, s, h, c, nz, kp, (unsigned)((b.n_tiles - b.n_single) * b.sub_packed), ring, g0,
-                                    g1, wait, st);
+    taken = true;
+    if (b0.narrow > 32) {
+        bool fits = true;
+        if (grid_s > 0) e = ws_resident<false, MODE>(grid_s, hist + ring, fits);
+        if (e == cudaSuccess && fits && grid_p > 0) e = ws_resident<true, MODE>(grid_p, ring, fits);
+        if (e != cudaSuccess) return e;
+        taken = fits;
+        if (!fits) return cudaSuccess;
+    }
+    const KeyParam kp = key_param(nz.k0, nz.k1);
+    if (grid_s > 0) e = launch_ws_t<false, MODE>(b, s, h, c, nz, kp, grid_s, hist + ring, g0, g1, wait, st);
+    if (e == cudaSuccess && grid_p > 0) e = launch_ws_t<true, MODE>(b, s, h, c, nz, kp, grid_p, ring, g0, g1, wait, st);
     return e;
 }
 
@@ -1151,8 +1188,11 @@ cudaError_t launch_integrate_t(const Batch &b, const State &s, const Hist &h, co
         if (e != cudaSuccess) return e;
     }
     if constexpr (sizeof(R) == 4 && PPT == 1 && ABP_WS) {
-        if (b.narrow == 32 && wait && wait->status)
-            return launch_ws<MODE>(b, s, h, c, nz, g0, g1, *wait, st);
+        if (b.narrow > 0 && b.narrow <= ABP_WS_WIDEST && wait && wait->status) {
+            bool taken = false;
+            const cudaError_t e = launch_ws<MODE>(b, s, h, c, nz, g0, g1, *wait, st, taken);
+            if (e != cudaSuccess || taken) return e;
+        }
     }
     const int threads = b.narrow ? b.narrow : kThreads;
     const int64_t sub_s = b.narrow ? b.sub_single : 1, sub_p = b.narrow ? b.sub_packed : 1;

@@ -130,36 +130,38 @@ def test_narrow_packed_items_against_wide(abp):
         assert torch.equal(ra[k], rb[k]), k
 
 
-@pytest.mark.parametrize("n_traj,scheme", [(4096, 0), (777, 0), (4096, 1), (12800, 0), (12800, 1)])
+@pytest.mark.parametrize("n_traj,scheme", [(4096, 0), (777, 0), (4096, 1), (12800, 0), (12800, 1), (25600, 0)])
 def test_warp_specialised_narrow_launch_is_bitwise_the_wide_one(abp, n_traj, scheme):
     # narrow lockstep blocks of 32 stepping threads run warp-specialised (three producer warps
     # draw the noise into a shared-memory ring of 64-step slots; 777 trajectories leave a ragged
-    # last block); 64-thread blocks (12,800 trajectories) run the plain narrow kernel.  Launch
-    # windows (250 steps), snapshots (every 77 steps) and the run's end (1,003 steps) fall
-    # inside slots; state, histograms and moments must be the work queue's bits (it never
-    # narrows).
+    # last block); a plan of 64-thread blocks (12,800 trajectories) runs as twice as many
+    # warp-specialised 32-thread ones, a plan of 128-thread blocks (25,600) on the plain narrow
+    # kernel.  Launch windows (250 steps), snapshots (every 77 steps) and the run's end (1,003
+    # steps) fall inside slots; state, histograms and moments must be the work queue's bits (it
+    # never narrows).
     w = W.single_set(n_traj=n_traj, n_steps=1003, hist_x_bins=32)
     w.hist_v_bins, w.v_lo, w.v_hi, w.snapshot_every, w.scheme = 16, -2.0, 2.0, 77, scheme
     ra, sa, ta = run(abp, w, schedule=1, particles_per_thread=1, steps_per_launch=250)
     rb, sb, tb = run(abp, w, schedule=2, particles_per_thread=1)
-    assert ta["narrow"] == (64 if n_traj == 12800 else 32) and tb["narrow"] == 0
+    assert ta["narrow"] == {12800: 64, 25600: 128}.get(n_traj, 32) and tb["narrow"] == 0
     for k in sa:
         assert torch.equal(sa[k], sb[k]), k
     for k in ra:
         assert torch.equal(ra[k], rb[k]), k
 
 
-@pytest.mark.parametrize("scheme,noise", [(0, 0), (1, 0), (0, 1)])
-def test_narrow_packed_64_thread_blocks_are_bitwise_the_wide_ones(abp, scheme, noise):
-    # 16,384 one-trajectory work items fill 64 packed tiles, launched as 64-thread narrow blocks
-    # (the plain narrow kernel); histograms of packed sets go to global memory at every
-    # snapshot, and the launch windows and snapshots fall off the counter blocks
-    w = W.force_sweep(n_F=16384, traj_per_set=1, n_steps=650)
+@pytest.mark.parametrize("n_items,scheme,noise", [(16384, 0, 0), (16384, 1, 0), (16384, 0, 1), (32768, 0, 0)])
+def test_narrow_packed_wider_blocks_are_bitwise_the_wide_ones(abp, n_items, scheme, noise):
+    # 16,384 one-trajectory work items fill 64 packed tiles, planned as 64-thread narrow blocks
+    # and run as 32-thread warp-specialised ones; 32,768 fill 128, planned 128 wide (the plain
+    # narrow kernel); histograms of packed sets go to global memory at every snapshot, and the
+    # launch windows and snapshots fall off the counter blocks
+    w = W.force_sweep(n_F=n_items, traj_per_set=1, n_steps=650)
     w.hist_x_bins, w.hist_v_bins, w.v_lo, w.v_hi, w.snapshot_every = 8, 4, -2.0, 2.0, 97
     w.scheme, w.noise = scheme, noise
     ra, sa, ta = run(abp, w, schedule=1, particles_per_thread=1, steps_per_launch=300)
     rb, sb, tb = run(abp, w, schedule=2, particles_per_thread=1)
-    assert ta["packed"] == 64 and ta["narrow"] == 64 and tb["packed"] == 0
+    assert ta["packed"] == n_items // 256 and ta["narrow"] == {16384: 64, 32768: 128}[n_items] and tb["packed"] == 0
     for k in sa:
         assert torch.equal(sa[k], sb[k]), k
     for k in ra:
