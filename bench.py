@@ -69,8 +69,8 @@ def parse():
                     help="N_TRAJ,N_STEPS: time only the forward and backward of the differentiation workload at "
                          "this size (profiling; prints one JSON line without the bench keys)")
     ap.add_argument("--configs", default="default",
-                    help="other workloads timed after the headline, comma-separated: single, uneven, force, heun, "
-                         "xorshift, snapshots_slice, snapshots (the full 64M x 10^6 run, about a minute), precision, "
+                    help="other workloads timed after the headline, comma-separated: single, single_heun, "
+                         "single_xorshift, uneven, force, heun, xorshift, snapshots_slice, snapshots (the full 64M x 10^6 run, about a minute), precision, "
                          "items; 'default' = all but the full snapshots run, 'all' = every one, 'none' = skip; "
                          "reported under 'configs'")
     return ap.parse_args()
@@ -605,15 +605,25 @@ def configs_leg(A, stream, names, lane_peak):
     from paper_1104_2499_gb300 import workloads as W
 
     if names == ["default"]:
-        names = ["single", "uneven", "force", "heun", "xorshift", "snapshots_slice", "precision", "items"]
+        names = ["single", "single_heun", "single_xorshift", "uneven", "force", "heun", "xorshift",
+                 "snapshots_slice", "precision", "items"]
     elif names == ["all"]:
-        names = ["single", "uneven", "force", "heun", "xorshift", "snapshots_slice", "snapshots", "precision",
-                 "items"]
+        names = ["single", "single_heun", "single_xorshift", "uneven", "force", "heun", "xorshift",
+                 "snapshots_slice", "snapshots", "precision", "items"]
     out = {}
     for name in names:
         t0 = time.perf_counter()
         if name == "single":
             out[name] = time_workload(A, stream, W.single_set(), 5, lane_peak)[0]
+        elif name in ("single_heun", "single_xorshift"):
+            # the same set with the stochastic Heun step, or with xorshift noise
+            w = W.single_set()
+            if name == "single_heun":
+                w.scheme = 1
+            else:
+                w.noise = 1
+            w.name += name[len("single"):]
+            out[name] = time_workload(A, stream, w, 5, lane_peak)[0]
         elif name == "uneven":
             w = W.uneven_batch()
             r = time_workload(A, stream, w, 1, lane_peak)[0]
