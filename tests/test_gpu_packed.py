@@ -150,6 +150,21 @@ def test_warp_specialised_narrow_launch_is_bitwise_the_wide_one(abp, n_traj, sch
         assert torch.equal(ra[k], rb[k]), k
 
 
+def test_narrow_plan_whose_split_blocks_do_not_fit_is_bitwise_the_wide_one(abp):
+    # 40 tiles planned 64 wide would become 320 warp-specialised blocks, but with 8,192 + 8,194
+    # histogram bins beside the 48 KB ring at most two fit on an SM (304 at once): the launch
+    # keeps the plain narrow kernel; either way the bits are the work queue's
+    w = W.single_set(n_traj=40 * 256, n_steps=300, hist_x_bins=8192)
+    w.hist_v_bins, w.v_lo, w.v_hi, w.snapshot_every = 8192, -2.0, 2.0, 100
+    ra, sa, ta = run(abp, w, schedule=1, particles_per_thread=1)
+    rb, sb, tb = run(abp, w, schedule=2, particles_per_thread=1)
+    assert ta["tiles"] == 40 and ta["narrow"] == 64 and tb["narrow"] == 0
+    for k in sa:
+        assert torch.equal(sa[k], sb[k]), k
+    for k in ra:
+        assert torch.equal(ra[k], rb[k]), k
+
+
 @pytest.mark.parametrize("n_items,scheme,noise", [(16384, 0, 0), (16384, 1, 0), (16384, 0, 1), (32768, 0, 0)])
 def test_narrow_packed_wider_blocks_are_bitwise_the_wide_ones(abp, n_items, scheme, noise):
     # 16,384 one-trajectory work items fill 64 packed tiles, planned as 64-thread narrow blocks

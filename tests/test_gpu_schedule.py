@@ -88,6 +88,27 @@ def test_graph_replay_is_identical(abp, schedule):
         assert torch.equal(outs[0][k], outs[1][k]) and torch.equal(outs[0][k], outs[2][k]), k
 
 
+@pytest.mark.parametrize("n_traj", [4096, 12800, 25600])
+def test_graph_replay_of_narrow_launches_is_identical(abp, n_traj):
+    # narrow lockstep plans 32, 64 and 128 threads wide (warp-specialised, warp-specialised as
+    # split 32-thread blocks after an occupancy check, plain): direct launch, captured launch and
+    # replayed graph give the same bits
+    w = W.single_set(n_traj=n_traj, n_steps=600, hist_x_bins=64)
+    st = torch.cuda.Stream()
+    outs = []
+    with abp.Ensemble(w, stream=st, schedule=1, particles_per_thread=1, steps_per_launch=1000) as ens:
+        with torch.cuda.stream(st):
+            ens.set_params()
+            assert ens.tiles()["narrow"] == {4096: 32, 12800: 64, 25600: 128}[n_traj]
+            for rep in range(3):
+                ens.reset(w.seed)
+                ens.integrate(-1)
+                outs.append({k: v.clone() for k, v in ens.state().items()})
+        st.synchronize()
+    for k in outs[0]:
+        assert torch.equal(outs[0][k], outs[1][k]) and torch.equal(outs[0][k], outs[2][k]), k
+
+
 def test_autotuner_choices(abp):
     w = W.sweep_grid(n_D=8, n_q=4, traj_per_set=1024, n_steps=20_000)
     with abp.Ensemble(w) as ens:
