@@ -1598,12 +1598,20 @@ abp_status abp_reduce(abp_ctx *ctx, double *moments, uint32_t *hist_x, uint32_t 
     bool synced = false;
     abp_status st;
     if (moments) {
+        // the kernels write every set's row: into a device output directly, else into the
+        // context's buffer, copied to the host
+        const PtrKind k = ptr_kind(moments, ctx->device);
+        if (k == PtrKind::OtherDevice)
+            return fail(ctx, ABP_EINVAL, "an output points to another GPU's memory (the context runs on device %d)",
+                        ctx->device);
+        double *dst = k == PtrKind::Device ? moments : (double *)ctx->d_moments.p;
         cudaError_t e = launch_reduce(ctx->batch(), ctx->state(), ctx->noise(), ctx->g, (double *)ctx->d_partials.p,
-                                      (double *)ctx->d_moments.p, ctx->stream);
+                                      dst, ctx->stream);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "reduction launch");
         ctx->launches += (ctx->n_sets > 0 && ctx->n_single > 0 ? 1 : 0) + (ctx->n_unpacked > 0 ? 1 : 0) +
                          (ctx->n_sets > ctx->n_unpacked ? 1 : 0);
-        if ((st = deliver(ctx, moments, ctx->d_moments.p, sizeof(double) * 8 * ctx->n_sets, &synced)) != ABP_OK)
+        if (k == PtrKind::Host &&
+            (st = deliver(ctx, moments, ctx->d_moments.p, sizeof(double) * 8 * ctx->n_sets, &synced)) != ABP_OK)
             return st;
     }
     if (hist_x && ctx->d_hx.bytes)

@@ -1121,16 +1121,23 @@ cudaError_t launch_persistent_t(const Batch &b, const State &s, const Hist &h, c
     return cudaGetLastError();
 }
 
+// Raise the kernel's dynamic shared-memory limit to `smem` (the ring alone is
+// 48 KB: with the static counters a block is past the default limit).
+template <bool PACKED, int MODE>
+cudaError_t ws_smem_limit(size_t smem) {
+    return cudaFuncSetAttribute(ws_kernel<PACKED, MODE, kWsProducers>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem);
+}
+
 // Warp-specialised form of a narrow launch (see ws_kernel).
 template <bool PACKED, int MODE>
 cudaError_t launch_ws_t(const Batch &b, const State &s, const Hist &h, const Ckpt &c, const Noise &nz,
                         const KeyParam &kp, unsigned grid, size_t smem, int64_t g0, int64_t g1, const WaitCtl &wait,
                         cudaStream_t st) {
-    auto kern = ws_kernel<PACKED, MODE, kWsProducers>;
-    // the ring alone is 48 KB: with the static counters the block is past the default limit
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const cudaError_t e = ws_smem_limit<PACKED, MODE>(smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid, 32 * (1 + kWsProducers), smem, st>>>(b, s, h, c, nz, kp, g0, g1, wait);
+    ws_kernel<PACKED, MODE, kWsProducers><<<grid, 32 * (1 + kWsProducers), smem, st>>>(b, s, h, c, nz, kp, g0, g1,
+                                                                                      wait);
     return cudaGetLastError();
 }
 
@@ -1139,7 +1146,7 @@ template <bool PACKED, int MODE>
 cudaError_t ws_resident(unsigned grid, size_t smem, bool &fits) {
     auto kern = ws_kernel<PACKED, MODE, kWsProducers>;
     int dev = 0, sms = 0, per_sm = 0;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ws_smem_limit<PACKED, MODE>(smem);
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * (1 + kWsProducers), smem);
