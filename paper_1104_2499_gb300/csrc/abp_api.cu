@@ -1295,9 +1295,17 @@ abp_status run_window(abp_ctx *ctx, int64_t g0, int64_t g1) {
         if (n_items == 0) return ABP_OK;
         if (n_items > INT32_MAX / 2) return fail(ctx, ABP_EINVAL, "too many work items; raise steps_per_launch");
     }
-    const bool seen = std::find(ctx->windows_seen.begin(), ctx->windows_seen.end(), std::make_pair(g0, g1)) !=
-                      ctx->windows_seen.end();
-    if (!seen) ctx->windows_seen.emplace_back(g0, g1);
+    // windows are remembered only while a graph may still be captured, and at most 4,096
+    // of them (a caller stepping a few steps at a time meets millions of windows)
+    bool seen = false;
+    if (ctx->graphs.size() < 8) {
+        const std::pair<int64_t, int64_t> win(g0, g1);
+        seen = ctx->windows_seen.count(win) > 0;
+        if (!seen) {
+            if (ctx->windows_seen.size() >= 4096) ctx->windows_seen.clear();
+            ctx->windows_seen.insert(win);
+        }
+    }
     if (s != nullptr && seen && ctx->graphs.size() < 8) {
         abp_ctx::GraphEntry ge{ctx->sched, 0, g0, g1, seg, seed, traj_base, ctx->hold_tile, ctx->wait_limit_ns,
                                (int32_t)n_items, nullptr, nullptr};

@@ -2,6 +2,7 @@
 // runtime translation units (abp_api.cu, abp_adjoint.cu).  Not public.
 #pragma once
 
+#include <set>
 #include <string>
 #include <vector>
 
@@ -74,7 +75,7 @@ struct abp_ctx {
         cudaGraphExec_t exec;
     };
     std::vector<GraphEntry> graphs;
-    std::vector<std::pair<int64_t, int64_t>> windows_seen;
+    std::set<std::pair<int64_t, int64_t>> windows_seen;  // windows run once, not yet captured
     int64_t n_snap = 0;
     int64_t n_ckpt = 0;
     int64_t launches = 0;  // kernels enqueued by this context
