@@ -182,7 +182,11 @@ ABP_API abp_status abp_progress(const abp_ctx *ctx, int64_t *steps_done);
  *   the last two entries counting v < v_lo and v >= v_hi.
  * n_snap = max over sets of (n_steps / snapshot_every), or 1 when
  * snapshot_every == 0; snapshots not reached yet are zero.  The sums are taken
- * in a fixed order, so results are bitwise reproducible. */
+ * in a fixed order, so results are bitwise reproducible.  Asynchronous on the
+ * context's stream when every output is device memory (the reduction kernels
+ * write device moments directly); with a host output the call returns once it
+ * is filled (small page-locked moment outputs are written by the kernels
+ * through their device mapping, others copied). */
 ABP_API abp_status abp_reduce(abp_ctx *ctx, double *moments, uint32_t *hist_x, uint32_t *hist_v);
 
 /* Number of snapshot slots of the current batch (host output): the longest

@@ -173,6 +173,17 @@ inline PtrKind ptr_kind(const void *p, int dev) {
     if (a.type != cudaMemoryTypeDevice) return PtrKind::Host;
     return a.device == dev ? PtrKind::Device : PtrKind::OtherDevice;
 }
+// The device address of page-locked host memory that kernels may write (mapped into
+// the device's address space), else NULL.
+template <typename T>
+inline T *mapped_host(T *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? static_cast<T *>(a.devicePointer) : nullptr;
+}
 inline int current_device() {
     int d = -1;
     if (cudaGetDevice(&d) != cudaSuccess) {

@@ -346,3 +346,22 @@ def test_trajectory_ids_across_the_32_bit_boundary(abp):
             for key, s in (("x", p["L"]), ("v", sv), ("e", p["q"] / p["c"]), ("x0", p["L"])):
                 bound = 1e-4 * np.maximum(np.abs(r[key]), s)
                 assert np.all(np.abs(st[key][sl] - r[key]) <= bound), (first, i, key)
+
+
+@pytest.mark.parametrize("n_sets", [4, 4096])
+def test_moments_are_the_same_bits_in_every_kind_of_output(abp, n_sets):
+    # abp_reduce writes the moments into a device output directly, into a small page-locked
+    # host output through its device mapping, and otherwise (pageable host memory, or 4,096
+    # sets: 256 KB) through its own buffer and a copy; every route gives the same bits
+    w = W.force_sweep(n_F=n_sets, traj_per_set=3, n_steps=200)
+    with abp.Ensemble(w) as ens:
+        ens.run()
+        dev = torch.empty((n_sets, 8), dtype=torch.float64, device="cuda")
+        pinned = torch.empty((n_sets, 8), dtype=torch.float64, pin_memory=True)
+        pageable = torch.empty((n_sets, 8), dtype=torch.float64)
+        for out in (dev, pinned, pageable):
+            abp.abp_reduce(ens.ctx, out, None, None)
+        torch.cuda.synchronize()
+    ref = dev.cpu()
+    assert torch.equal(ref, pinned) and torch.equal(ref, pageable)
+    assert np.isfinite(ref.numpy()[:, 0]).all()
