@@ -4,7 +4,8 @@ access and records status 3 (reported as ABP_ESTATE) on a violation.
 
 Bar: a child process runs the same workloads against the release and the checked library --
 ragged batches with one-set and packed tiles, snapshots and split launches under both
-schedules, stochastic Heun, xorshift noise, a warp-specialised narrow launch, the full and
+schedules, stochastic Heun, xorshift noise, warp-specialised narrow launches (one set of 32-wide
+blocks, and 16,384 packed work items planned 64 wide and split into 32-thread blocks), the full and
 windowed adjoint with its per-trajectory readout (with and without the hand-off of Philox blocks
 from level 1 to the reverse sweep), and the combination of moments on the device --
 and no check may fail, and every state, result and gradient must be the
@@ -43,7 +44,9 @@ runs = [("lockstep", ragged(), dict(schedule=1, particles_per_thread=2, steps_pe
         ("heun", ragged(scheme=1), dict(schedule=1, particles_per_thread=2)),
         ("xorshift", ragged(noise=1), dict(schedule=1, particles_per_thread=1)),
         ("narrow", W.single_set(n_traj=4096, n_steps=1003, hist_x_bins=32),
-         dict(schedule=1, particles_per_thread=1, steps_per_launch=250))]
+         dict(schedule=1, particles_per_thread=1, steps_per_launch=250)),
+        ("narrow64", W.force_sweep(n_F=16384, traj_per_set=1, n_steps=300),
+         dict(schedule=1, particles_per_thread=1, steps_per_launch=130))]
 for tag, w, kw in runs:
     with A.Ensemble(w, **kw) as ens:
         ens.run()
