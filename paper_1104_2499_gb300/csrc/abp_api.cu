@@ -222,6 +222,7 @@ void measure_candidates(abp_ctx *ctx, TuneTable &tt) {
         b.n_single = nt;
         b.set_first = nullptr;
         b.set_order = nullptr;
+        b.slot_set = nullptr;
         b.n_unpacked = 1;
         b.narrow = 0;
         b.sub_single = b.sub_packed = 1;
@@ -494,6 +495,7 @@ double batch_efficiency(int32_t n, const int64_t *n_traj, const int64_t *n_steps
 struct TilePlan {
     std::vector<int64_t> set_first, tile_first;
     std::vector<int32_t> set_packed, set_tile_begin, tile_count, tile_set, set_order;
+    std::vector<int32_t> slot_set;  // [packed tiles][kThreads]: the set of each slot's trajectory
     int32_t n_single = 0, n_unpacked = 0, narrow = 0, sub_single = 1, sub_packed = 1;
 };
 
@@ -542,12 +544,20 @@ bool plan_tiles(int32_t n_sets, const int64_t *n_traj, const int64_t *n_steps, i
         p.set_tile_begin.push_back((int32_t)p.tile_first.size());
     }
     p.n_single = (int32_t)p.tile_first.size();
+    p.slot_set.clear();
     for (const auto &gr : groups) {
         int32_t lead = gr.first;
         while (n_traj[lead] == 0) ++lead;  // the first non-empty set carries the group's step count
         p.tile_first.push_back(p.set_first[gr.first]);
         p.tile_count.push_back((int32_t)(p.set_first[gr.second] - p.set_first[gr.first]));
         p.tile_set.push_back(lead);
+        // slot li holds trajectory tile_first + li (slots past the count repeat the last set)
+        int32_t k = lead;
+        for (int64_t li = 0; li < kThreads; ++li) {
+            const int64_t t = p.set_first[gr.first] + std::min<int64_t>(li, p.tile_count.back() - 1);
+            while (k + 1 < gr.second && p.set_first[k + 1] <= t) ++k;
+            p.slot_set.push_back(k);
+        }
     }
     const int32_t n_tiles = (int32_t)p.tile_first.size();
     p.set_order.clear();
@@ -697,6 +707,7 @@ abp_status configure_batch(abp_ctx *ctx, int sched, int ppt, int64_t spl) {
         ctx->tile_count.swap(plan.tile_count);
         ctx->tile_set.swap(plan.tile_set);
         ctx->set_order.swap(plan.set_order);
+        ctx->slot_set.swap(plan.slot_set);
         ctx->n_single = plan.n_single;
         ctx->n_tiles = (int32_t)ctx->tile_first.size();
         ctx->n_unpacked = plan.n_unpacked;
@@ -759,6 +770,7 @@ abp_status configure_batch(abp_ctx *ctx, int sched, int ppt, int64_t spl) {
     ALLOC(d_perm, sizeof(int32_t) * (size_t)std::max(ctx->n_tiles, 1), "work queue order");
     ALLOC(d_set_first, sizeof(int64_t) * ((size_t)n_sets + 1), "set offsets");
     ALLOC(d_set_order, sizeof(int32_t) * (size_t)std::max(n_sets, 1), "set order");
+    ALLOC(d_slot_set, sizeof(int32_t) * std::max(ctx->slot_set.size(), (size_t)1), "packed slot sets");
 #undef ALLOC
 
     cudaStream_t s = ctx->stream;
@@ -768,7 +780,8 @@ abp_status configure_batch(abp_ctx *ctx, int sched, int ppt, int64_t spl) {
                               (sizeof(int32_t) * (n_sets + 1) + 15) / 16 * 16 +
                               (sizeof(int64_t) * ctx->n_tiles + 15) / 16 * 16 +
                               3 * ((sizeof(int32_t) * ctx->n_tiles + 15) / 16 * 16) +
-                              (sizeof(int64_t) * (n_sets + 1) + 15) / 16 * 16 + (sizeof(int32_t) * n_sets + 15) / 16 * 16;
+                              (sizeof(int64_t) * (n_sets + 1) + 15) / 16 * 16 + (sizeof(int32_t) * n_sets + 15) / 16 * 16 +
+                              (sizeof(int32_t) * ctx->slot_set.size() + 15) / 16 * 16;
     if (ctx->h_stage_cap < stage_need) {
         if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
         ctx->h_stage = nullptr;
@@ -800,6 +813,7 @@ abp_status configure_batch(abp_ctx *ctx, int sched, int ppt, int64_t spl) {
     if (e == cudaSuccess) e = up(ctx->d_perm, ctx->perm.data(), sizeof(int32_t) * ctx->n_tiles);
     if (e == cudaSuccess) e = up(ctx->d_set_first, ctx->set_first.data(), sizeof(int64_t) * (n_sets + 1));
     if (e == cudaSuccess) e = up(ctx->d_set_order, ctx->set_order.data(), sizeof(int32_t) * n_sets);
+    if (e == cudaSuccess) e = up(ctx->d_slot_set, ctx->slot_set.data(), sizeof(int32_t) * ctx->slot_set.size());
     if (e == cudaSuccess)
         e = launch_coef((const abp_params *)ctx->d_params.p, n_sets, ctx->cfg.dt, ctx->d_coef.p, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_status.p, 0, sizeof(int32_t), s);

@@ -81,14 +81,15 @@ struct abp_ctx {
     int64_t launches = 0;  // kernels enqueued by this context
     std::vector<abp_params> params;
     std::vector<int64_t> n_traj, n_steps;
-    std::vector<int32_t> set_tile_begin, tile_count, tile_set, set_packed, set_order;
+    std::vector<int32_t> set_tile_begin, tile_count, tile_set, set_packed, set_order, slot_set;
     std::vector<int64_t> tile_first, set_first;
     int32_t n_single = 0;  // tiles [n_single, n_tiles) are packed
     int32_t n_unpacked = 0;  // sets in one-set tiles
     int32_t narrow = 0, sub_single = 1, sub_packed = 1;  // narrow lockstep launch (small batches)
 
     // device
-    DevBuf d_params, d_steps, d_set_tile_begin, d_tile_first, d_tile_count, d_tile_set, d_set_first, d_set_order;
+    DevBuf d_params, d_steps, d_set_tile_begin, d_tile_first, d_tile_count, d_tile_set, d_set_first, d_set_order,
+        d_slot_set;
     DevBuf d_coef;  // per-set step coefficients (coef_tables)
     // Page-locked host staging of the batch tables abp_set_params uploads (one
     // allocation, grown when a batch needs more; copies from pageable memory cost
@@ -121,6 +122,7 @@ struct abp_ctx {
         b.total_traj = total_traj;
         b.set_first = n_single < n_tiles ? (const int64_t *)d_set_first.p : nullptr;
         b.set_order = n_unpacked < n_sets ? (const int32_t *)d_set_order.p : nullptr;
+        b.slot_set = n_single < n_tiles ? (const int32_t *)d_slot_set.p : nullptr;
         b.n_unpacked = n_unpacked;
         b.narrow = narrow;
         b.sub_single = sub_single;
@@ -221,7 +223,7 @@ struct abp_ctx {
     void release_all() {
         if (live_stream) cudaStreamSynchronize(live_stream);
         drop_graphs();
-        for (DevBuf *b : {&d_queue, &d_round, &d_perm, &d_set_first, &d_set_order, &d_params, &d_coef, &d_steps, &d_set_tile_begin, &d_tile_first, &d_tile_count, &d_tile_set, &d_y,
+        for (DevBuf *b : {&d_queue, &d_round, &d_perm, &d_set_first, &d_set_order, &d_slot_set, &d_params, &d_coef, &d_steps, &d_set_tile_begin, &d_tile_first, &d_tile_count, &d_tile_set, &d_y,
                           &d_yacc, &d_ylo, &d_v, &d_e, &d_y0, &d_cell, &d_xs, &d_hx, &d_hv, &d_ckpt, &d_partials,
                           &d_moments, &d_adj, &d_live_mom})
             b->release();

@@ -30,6 +30,7 @@ struct Batch {
     int64_t total_traj;
     const int64_t *set_first;      // [n_sets + 1] first trajectory of each set (packed batches; else NULL)
     const int32_t *set_order;      // [n_sets] sets in one-set tiles, then sets in packed tiles (NULL: all one-set, in order)
+    const int32_t *slot_set;       // [n_tiles - n_single][kThreads] set of each packed-tile slot (NULL: no packed tiles)
     int32_t n_unpacked;            // sets in one-set tiles (the first n_unpacked entries of set_order)
     // Narrow launch of the lockstep integrator (small batches): blocks of `narrow`
     // threads (0: off), one trajectory per thread, sub_single blocks per one-set

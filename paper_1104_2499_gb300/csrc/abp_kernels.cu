@@ -61,18 +61,12 @@ __device__ __forceinline__ double disp_periods(const SV<R> &s, int64_t t) {
     return (((double)s.cell[t] + (double)s.y[t]) + ((double)s.yacc[t] + (double)s.ylo[t])) - (double)s.y0[t];
 }
 
-// Set of trajectory t in a batch with packed tiles: the last set whose first
-// trajectory is <= t (empty sets share their first index with the next set).
-__device__ __forceinline__ int find_set(const Batch &b, int64_t t) {
-    int lo = 0, hi = b.n_sets - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (b.set_first[mid] <= t)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    return lo;
+// Set of the trajectory in slot li (< kThreads) of packed tile `tile`, from the
+// table the host planner writes (one load instead of a search over the sets).
+__device__ __forceinline__ int packed_set(const Batch &b, int tile, int li) {
+    const int64_t i = dchk((int64_t)(tile - b.n_single) * kThreads + li, (int64_t)(b.n_tiles - b.n_single) * kThreads,
+                           b.dbg);
+    return (int)dchk(b.slot_set[i], b.n_sets, b.dbg);
 }
 
 // ---------------------------------------------------------------- snapshots
@@ -145,7 +139,7 @@ __global__ void __launch_bounds__(kThreads) init_kernel(Batch b, State st, Hist 
     }
     for (int li = threadIdx.x; li < count; li += blockDim.x) {
         const int64_t t = dchk(first + li, b.total_traj, b.dbg);
-        const int my_set = packed ? (int)dchk(find_set(b, t), b.n_sets, b.dbg) : set;
+        const int my_set = packed ? packed_set(b, tile, li) : set;
         const abp_params p = b.params[my_set];
         const uint4 w = noise_block(kInitCounter, (uint64_t)t + nz.traj_base, nz.k0, nz.k1);
         const R y0 = (R)(w.x >> 8) * (R)0x1p-24;
@@ -565,7 +559,7 @@ __device__ __forceinline__ void run_tile(const Batch &b, const State &st, const 
 
     const SV<R> s = view<R>(st);
     const int set =
-        PACKED ? (int)dchk(find_set(b, first + min(lane_base + (int)threadIdx.x, count - 1)), b.n_sets, b.dbg) : set_t;
+        PACKED ? packed_set(b, tile, min(lane_base + (int)threadIdx.x, count - 1)) : set_t;
     const Coef<R> k = load_coef<R>(sizeof(R) == 4 ? b.coef_f : b.coef_d, b.params, set, nz.dt);
 
     Slots<R, PPT> S;
@@ -715,7 +709,7 @@ __device__ __forceinline__ void ws_produce(const Batch &b, const State &st, cons
     const int64_t idx = dchk(first + (act ? li : count - 1), b.total_traj, b.dbg);
     if (!__any_sync(0xffffffffu, act)) return;  // the consumer warp does not step either
     if (tile == r.hold_tile) return;            // test hook: the consumer's waits run out
-    const int set = PACKED ? (int)dchk(find_set(b, first + min(li, count - 1)), b.n_sets, b.dbg) : set_t;
+    const int set = PACKED ? packed_set(b, tile, min(li, count - 1)) : set_t;
     const Coef<float> k = load_coef<float>(b.coef_f, b.params, set, nz.dt);
     const StepStream ss = step_stream((uint64_t)idx + nz.traj_base, K);
     const int64_t a0 = n_begin / SS, a1 = (n_end - 1) / SS;
@@ -1060,7 +1054,7 @@ __global__ void __launch_bounds__(kThreads) get_state_kernel(Batch b, State st, 
     const int count = b.tile_count[tile];
     for (int li = threadIdx.x; li < count; li += blockDim.x) {
         const int64_t t = dchk(first + li, b.total_traj, b.dbg);
-        const int set = (int)dchk(packed ? find_set(b, t) : b.tile_set[tile], b.n_sets, b.dbg);
+        const int set = packed ? packed_set(b, tile, li) : (int)dchk(b.tile_set[tile], b.n_sets, b.dbg);
         const int64_t n = min(g, b.set_steps[set]);
         const double L = b.params[set].L;
         const double x0t = L * (double)s.y0[t];

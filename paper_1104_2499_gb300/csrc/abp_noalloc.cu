@@ -186,6 +186,7 @@ extern "C" abp_status abp_run_set_noalloc(const abp_params *params, const abp_co
     b.n_single = n_tiles;
     b.set_first = nullptr;
     b.set_order = nullptr;
+    b.slot_set = nullptr;
     b.n_unpacked = b.n_sets;
     b.narrow = 0;
     b.sub_single = b.sub_packed = 1;
